@@ -1,0 +1,1057 @@
+/*
+ * cvweno_oracle.c -- plain FP64 CPU oracle for the cell-vertex WENO stabilised
+ * DG residual of Vedral & Kuzmin, "Cell-vertex WENO schemes with shock-capturing
+ * quadrature for high-order finite element discretizations of hyperbolic problems"
+ * (arXiv 2601.16911).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this file: it is
+ * used by the test suite, by the package smoke check and by the benchmark's CPU
+ * baseline leg.  It shares no code, header, table or constant generator with the
+ * CUDA library: its Gauss rule, its Legendre derivatives, its vertex patches and its
+ * semi-norms are all computed here, by deliberately plain (and slow) routes:
+ *
+ *   - Gauss-Legendre nodes by Newton iteration on P_n;
+ *   - Legendre derivatives by differentiating the explicit power sum of P_m;
+ *   - vertex patches by matching corner coordinates (geometric search), never by
+ *     index arithmetic;
+ *   - Sobolev semi-norms by full tensor Gauss quadrature of every derivative of the
+ *     candidate polynomials, the vertex candidates evaluated directly from their
+ *     Taylor form (Sec. 3.2, eq. taylorcand) rather than converted to a basis;
+ *   - face fluxes evaluated once per face and applied to both neighbours.
+ *
+ * Function-by-function citations (Sec./eq. of the paper):
+ *   or_hermite        Sec. 3.2, eq. taylorsol + eq. pointsnorm   (stage a)
+ *   or_vertex_average Sec. 3.2, eq. taylorcand + vertex Jiang-Shu weights (stage b)
+ *   or_sensor         Sec. 3.2, eq. finalweno + cell weights; Sec. 2.2 eq. gamma,
+ *                     eq. snorm, eq. lostab (nu_e)                 (stage c)
+ *   or_sc_weights     Sec. 4, eq. dissrateorig, eq. alphaq, eq. alpha_prelim (stage d)
+ *   or_residual       Sec. 2.1 eq. convop, Sec. 2.2 eq. stab/lostab, eq. sdstab (stage e)
+ *   or_ssprk3         Sec. 2.2 (SSP Runge-Kutta), Sec. 5 (third order SSP-RK)
+ *
+ * Readings of the paper where it is silent or ambiguous (numbered A1..A20, the same
+ * numbers used throughout the project):
+ *   A1  gamma_e = 1 is smooth; DG viscosity is (1-gamma_e) nu_e.
+ *   A2  lambda_e = max |f'(u)| over the cell's volume and own face Gauss nodes
+ *       (Euler: |v| + c), or a given constant (KPP: 1).
+ *   A3  h_e = diam(K_e): dx in 1D, sqrt(dx^2+dy^2) in 2D.
+ *   A4  one exponent q (=1) for all three uses.
+ *   A5  tensor multi-index set 0 <= k_j <= p in the Taylor expansion and both
+ *       semi-norms (exact for Q_p); the 1D case is unaffected.
+ *   A7  a cell with ||u^e||_e <= 1e-30 is flat: gamma_e = 1, alpha_q = 1.
+ *   A8  alpha_q = 1 when the redistribution denominator vanishes.
+ *   A9  redistribute iff gamma_e < C_gamma (= 0.9) and SC is enabled.
+ *   A10 Gauss-Legendre with n = p+1 points per direction for volume and faces.
+ *   A11 DG basis: tensor Legendre (diagonal mass).
+ *   A14 LLF: lambda = max |f'(u)*n| of both traces (or the given constant);
+ *       HLL: Davis wave-speed estimates.
+ *   A15 transmissive boundary: ghost trace = interior trace; boundary vertex
+ *       patches hold only existing cells.
+ *   A18 candidates are not mean-corrected (the sensor uses derivatives only).
+ *   A20 Euler: gamma_e and alpha~_q from the density; f_q per conserved variable,
+ *       so each variable's dissipation rate is preserved.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXP 4
+#define OR_MAXN (OR_MAXP + 1)
+#define OR_MAXND (OR_MAXN * OR_MAXN)
+#define OR_MAXVAR 4
+#define OR_NPROJ 12
+
+enum { OR_DG = 0, OR_CG = 1 };
+enum { OR_PERIODIC = 0, OR_TRANSMISSIVE = 1 };
+enum { OR_BURGERS = 0, OR_KPP = 1, OR_LINADV = 2, OR_EULER = 3 };
+enum {
+  OR_OK = 0,
+  OR_ERR_ARG = 1,
+  OR_ERR_NONFINITE = 3,
+  OR_ERR_POSITIVITY = 4,
+  OR_ERR_UNSUPPORTED = 6,
+  OR_ERR_NOMEM = 7
+};
+enum {
+  IC_CONST = 0,
+  IC_SINE_STEP = 1,
+  IC_CIRCLE = 2,
+  IC_QUADRANTS = 3,
+  IC_FOURIER = 4,
+  IC_POLY = 5,
+  IC_DENSITY_WAVE = 6
+};
+
+typedef struct {
+  int dim, nx, ny, degree, kind, system;
+  int bc[4]; /* x-low, x-high, y-low, y-high */
+  double x0, x1, y0, y1;
+  double eps, r, q, gamma_vertex, c_gamma;
+  int sc_quadrature, sensor_mode; /* sensor_mode: 0 computed, 1 gamma=1, 2 gamma=0 */
+  double lambda_const, gas_gamma, adv_vx, adv_vy;
+} or_desc;
+
+/* ------------------------------------------------------------------------- */
+/* 1D building blocks                                                         */
+/* ------------------------------------------------------------------------- */
+
+static double or_fact(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= (double)i;
+  return f;
+}
+
+static double or_binom(int a, int b) { return or_fact(a) / (or_fact(b) * or_fact(a - b)); }
+
+static double or_ipow(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
+}
+
+/* k-th derivative of the Legendre polynomial P_m at x, from the explicit power sum
+ * P_m(x) = 2^-m sum_j (-1)^j C(m,j) C(2m-2j,m) x^(m-2j), differentiated term by term. */
+static double or_leg_dk(int m, int k, double x) {
+  double s = 0.0;
+  for (int j = 0; 2 * j <= m; ++j) {
+    int e = m - 2 * j;
+    if (e < k) continue;
+    double c = ((j & 1) ? -1.0 : 1.0) * or_binom(m, j) * or_binom(2 * m - 2 * j, m) / or_ipow(2.0, m);
+    s += c * or_fact(e) / or_fact(e - k) * or_ipow(x, e - k);
+  }
+  return s;
+}
+
+/* n-point Gauss-Legendre rule on [-1,1] by Newton iteration on P_n (ascending nodes). */
+static void or_gauss(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* mesh: geometry, Gauss rule and geometric vertex patches                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  or_desc d;
+  int dim, p, n, nd, nvar, nx, ny, ncell, ncorner, nq;
+  double dx, dy, h, jac;  /* jac = |K_e| / |reference cell| */
+  double gx[OR_MAXN], gw[OR_MAXN];
+  int nvert;
+  int *vcount, *vcell, *vcorner; /* [nvert][4] */
+  int* cvert;                     /* [ncell][ncorner] */
+} or_mesh;
+
+typedef struct {
+  double X, Y;
+  int e, c;
+} or_corner_rec;
+
+static double g_sort_tol;
+
+static int or_cmp_corner(const void* a, const void* b) {
+  const or_corner_rec* p = (const or_corner_rec*)a;
+  const or_corner_rec* s = (const or_corner_rec*)b;
+  if (fabs(p->Y - s->Y) > g_sort_tol) return p->Y < s->Y ? -1 : 1;
+  if (fabs(p->X - s->X) > g_sort_tol) return p->X < s->X ? -1 : 1;
+  if (p->e != s->e) return p->e < s->e ? -1 : 1;
+  return 0;
+}
+
+static void or_mesh_free(or_mesh* m) {
+  free(m->vcount);
+  free(m->vcell);
+  free(m->vcorner);
+  free(m->cvert);
+  memset(m, 0, sizeof(*m));
+}
+
+static int or_nvar(const or_desc* d) { return d->system == OR_EULER ? 4 : 1; }
+
+static int or_mesh_init(const or_desc* d, or_mesh* m) {
+  memset(m, 0, sizeof(*m));
+  if (d->dim != 1 && d->dim != 2) return OR_ERR_ARG;
+  if (d->degree < 1 || d->degree > OR_MAXP) return OR_ERR_UNSUPPORTED;
+  if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return OR_ERR_ARG;
+  if (d->kind != OR_DG) return OR_ERR_UNSUPPORTED;
+  if (d->system == OR_EULER && d->dim != 2) return OR_ERR_UNSUPPORTED;
+  if (d->system == OR_KPP && d->dim != 2) return OR_ERR_UNSUPPORTED;
+  if ((d->bc[0] == OR_PERIODIC) != (d->bc[1] == OR_PERIODIC)) return OR_ERR_ARG;
+  if (d->dim == 2 && (d->bc[2] == OR_PERIODIC) != (d->bc[3] == OR_PERIODIC)) return OR_ERR_ARG;
+  m->d = *d;
+  m->dim = d->dim;
+  m->p = d->degree;
+  m->n = d->degree + 1;
+  m->nd = d->dim == 2 ? m->n * m->n : m->n;
+  m->nq = m->nd;
+  m->nvar = or_nvar(d);
+  m->nx = d->nx;
+  m->ny = d->dim == 2 ? d->ny : 1;
+  m->ncell = m->nx * m->ny;
+  m->ncorner = d->dim == 2 ? 4 : 2;
+  m->dx = (d->x1 - d->x0) / m->nx;
+  m->dy = d->dim == 2 ? (d->y1 - d->y0) / m->ny : 1.0;
+  m->h = d->dim == 2 ? sqrt(m->dx * m->dx + m->dy * m->dy) : m->dx;
+  m->jac = d->dim == 2 ? 0.25 * m->dx * m->dy : 0.5 * m->dx;
+  or_gauss(m->n, m->gx, m->gw);
+
+  /* geometric search: every cell corner becomes a record at its physical position
+   * (periodic sides identified); records at the same position form one patch. */
+  int nrec = m->ncell * m->ncorner;
+  or_corner_rec* rec = (or_corner_rec*)malloc(sizeof(or_corner_rec) * nrec);
+  m->cvert = (int*)malloc(sizeof(int) * nrec);
+  if (!rec || !m->cvert) { free(rec); or_mesh_free(m); return OR_ERR_NOMEM; }
+  double lx = d->x1 - d->x0, ly = d->dim == 2 ? d->y1 - d->y0 : 1.0;
+  g_sort_tol = 1e-9 * (lx > ly ? lx : ly);
+  int r = 0;
+  for (int e = 0; e < m->ncell; ++e) {
+    int i = e % m->nx, j = e / m->nx;
+    for (int c = 0; c < m->ncorner; ++c) {
+      double X = d->x0 + (i + (c & 1)) * m->dx;
+      double Y = d->dim == 2 ? d->y0 + (j + (c >> 1)) * m->dy : 0.0;
+      if (d->bc[0] == OR_PERIODIC && fabs(X - d->x1) <= g_sort_tol) X = d->x0;
+      if (d->dim == 2 && d->bc[2] == OR_PERIODIC && fabs(Y - d->y1) <= g_sort_tol) Y = d->y0;
+      rec[r].X = X;
+      rec[r].Y = Y;
+      rec[r].e = e;
+      rec[r].c = c;
+      ++r;
+    }
+  }
+  qsort(rec, nrec, sizeof(or_corner_rec), or_cmp_corner);
+  int nv = 0;
+  for (int t = 0; t < nrec; ++t)
+    if (t == 0 || fabs(rec[t].X - rec[t - 1].X) > g_sort_tol || fabs(rec[t].Y - rec[t - 1].Y) > g_sort_tol) ++nv;
+  m->nvert = nv;
+  m->vcount = (int*)calloc(nv, sizeof(int));
+  m->vcell = (int*)malloc(sizeof(int) * nv * 4);
+  m->vcorner = (int*)malloc(sizeof(int) * nv * 4);
+  if (!m->vcount || !m->vcell || !m->vcorner) { free(rec); or_mesh_free(m); return OR_ERR_NOMEM; }
+  for (int t = 0; t < nv * 4; ++t) m->vcell[t] = m->vcorner[t] = -1;
+  int v = -1;
+  for (int t = 0; t < nrec; ++t) {
+    if (t == 0 || fabs(rec[t].X - rec[t - 1].X) > g_sort_tol || fabs(rec[t].Y - rec[t - 1].Y) > g_sort_tol) ++v;
+    int s = m->vcount[v]++;
+    if (s >= 4) { free(rec); or_mesh_free(m); return OR_ERR_ARG; }
+    m->vcell[4 * v + s] = rec[t].e;
+    m->vcorner[4 * v + s] = rec[t].c;
+    m->cvert[rec[t].e * m->ncorner + rec[t].c] = v;
+  }
+  free(rec);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* basis (tensor Legendre, reading A11) and its physical derivatives          */
+/* ------------------------------------------------------------------------- */
+
+/* D^k phi_m at reference point (xi, eta) in physical units. */
+static double or_dphi(const or_mesh* m, int mi, int kx, int ky, double xi, double eta) {
+  int mx = mi % m->n, my = mi / m->n;
+  double v = or_ipow(2.0 / m->dx, kx) * or_leg_dk(mx, kx, xi);
+  if (m->dim == 2) v *= or_ipow(2.0 / m->dy, ky) * or_leg_dk(my, ky, eta);
+  return v;
+}
+
+/* D^k u^e at (xi, eta) for one variable's coefficient block c[nd]. */
+static double or_du(const or_mesh* m, const double* c, int kx, int ky, double xi, double eta) {
+  double s = 0.0;
+  for (int mi = 0; mi < m->nd; ++mi) s += c[mi] * or_dphi(m, mi, kx, ky, xi, eta);
+  return s;
+}
+
+/* multi-index set K (tensor set, reading A5): index t -> (kx, ky) */
+static int or_nk(const or_mesh* m) { return m->nd; }
+static void or_kidx(const or_mesh* m, int t, int* kx, int* ky) {
+  *kx = t % m->n;
+  *ky = m->dim == 2 ? t / m->n : 0;
+}
+
+/* volume Gauss point t -> reference coordinates and weight (including |J|) */
+static void or_qpoint(const or_mesh* m, int t, double* xi, double* eta, double* W) {
+  int qx = t % m->n, qy = m->dim == 2 ? t / m->n : 0;
+  *xi = m->gx[qx];
+  *eta = m->dim == 2 ? m->gx[qy] : 0.0;
+  *W = m->gw[qx] * (m->dim == 2 ? m->gw[qy] : 1.0) * m->jac;
+}
+
+static const double* or_cell(const or_mesh* m, const double* u, int var, int e) {
+  return u + ((size_t)var * m->ncell + e) * m->nd;
+}
+
+/* ------------------------------------------------------------------------- */
+/* fluxes                                                                     */
+/* ------------------------------------------------------------------------- */
+
+static void or_flux(const or_mesh* m, const double* U, double* Fx, double* Fy) {
+  const or_desc* d = &m->d;
+  switch (d->system) {
+    case OR_BURGERS:
+      Fx[0] = 0.5 * U[0] * U[0];
+      Fy[0] = 0.5 * U[0] * U[0];
+      break;
+    case OR_KPP:
+      Fx[0] = sin(U[0]);
+      Fy[0] = cos(U[0]);
+      break;
+    case OR_LINADV:
+      Fx[0] = d->adv_vx * U[0];
+      Fy[0] = d->adv_vy * U[0];
+      break;
+    default: {
+      double g = d->gas_gamma, rho = U[0], vx = U[1] / rho, vy = U[2] / rho;
+      double p = (g - 1.0) * (U[3] - 0.5 * rho * (vx * vx + vy * vy));
+      Fx[0] = U[1];
+      Fx[1] = U[1] * vx + p;
+      Fx[2] = U[2] * vx;
+      Fx[3] = (U[3] + p) * vx;
+      Fy[0] = U[2];
+      Fy[1] = U[1] * vy;
+      Fy[2] = U[2] * vy + p;
+      Fy[3] = (U[3] + p) * vy;
+    }
+  }
+}
+
+/* |f'(u) . n| for scalar laws; n = (nx, ny) */
+static double or_normal_speed(const or_mesh* m, double u, double nx, double ny) {
+  const or_desc* d = &m->d;
+  switch (d->system) {
+    case OR_BURGERS: return fabs(u * (nx + (m->dim == 2 ? ny : 0.0)));
+    case OR_KPP: return fabs(cos(u) * nx - sin(u) * ny);
+    default: return fabs(d->adv_vx * nx + (m->dim == 2 ? d->adv_vy * ny : 0.0));
+  }
+}
+
+/* max wave speed |f'(U)| (Euclidean) or |v|+c; also checks Euler positivity */
+static int or_wave_speed(const or_mesh* m, const double* U, double* s) {
+  const or_desc* d = &m->d;
+  switch (d->system) {
+    case OR_BURGERS: *s = fabs(U[0]) * (m->dim == 2 ? sqrt(2.0) : 1.0); return OR_OK;
+    case OR_KPP: *s = 1.0; return OR_OK;
+    case OR_LINADV:
+      *s = m->dim == 2 ? sqrt(d->adv_vx * d->adv_vx + d->adv_vy * d->adv_vy) : fabs(d->adv_vx);
+      return OR_OK;
+    default: {
+      double g = d->gas_gamma, rho = U[0];
+      if (!(rho > 0.0)) return OR_ERR_POSITIVITY;
+      double vx = U[1] / rho, vy = U[2] / rho;
+      double p = (g - 1.0) * (U[3] - 0.5 * rho * (vx * vx + vy * vy));
+      if (!(p > 0.0)) return OR_ERR_POSITIVITY;
+      *s = sqrt(vx * vx + vy * vy) + sqrt(g * p / rho);
+      return OR_OK;
+    }
+  }
+}
+
+/* numerical flux F*(UL, UR) . n for the normal n = (nx, ny), reading A14 */
+static int or_numflux(const or_mesh* m, const double* UL, const double* UR, double nx, double ny, double* F) {
+  const or_desc* d = &m->d;
+  double FxL[OR_MAXVAR], FyL[OR_MAXVAR], FxR[OR_MAXVAR], FyR[OR_MAXVAR];
+  or_flux(m, UL, FxL, FyL);
+  or_flux(m, UR, FxR, FyR);
+  if (m->dim == 1) { ny = 0.0; }
+  if (d->system != OR_EULER) {
+    double lam = d->lambda_const > 0.0 ? d->lambda_const
+                                       : fmax(or_normal_speed(m, UL[0], nx, ny), or_normal_speed(m, UR[0], nx, ny));
+    double fl = FxL[0] * nx + FyL[0] * ny, fr = FxR[0] * nx + FyR[0] * ny;
+    F[0] = 0.5 * (fl + fr) - 0.5 * lam * (UR[0] - UL[0]);
+    return OR_OK;
+  }
+  double g = d->gas_gamma;
+  double rl = UL[0], rr = UR[0];
+  if (!(rl > 0.0) || !(rr > 0.0)) return OR_ERR_POSITIVITY;
+  double vnl = (UL[1] * nx + UL[2] * ny) / rl, vnr = (UR[1] * nx + UR[2] * ny) / rr;
+  double pl = (g - 1.0) * (UL[3] - 0.5 * (UL[1] * UL[1] + UL[2] * UL[2]) / rl);
+  double pr = (g - 1.0) * (UR[3] - 0.5 * (UR[1] * UR[1] + UR[2] * UR[2]) / rr);
+  if (!(pl > 0.0) || !(pr > 0.0)) return OR_ERR_POSITIVITY;
+  double cl = sqrt(g * pl / rl), cr = sqrt(g * pr / rr);
+  double sl = fmin(vnl - cl, vnr - cr), sr = fmax(vnl + cl, vnr + cr);
+  for (int c = 0; c < 4; ++c) {
+    double fl = FxL[c] * nx + FyL[c] * ny, fr = FxR[c] * nx + FyR[c] * ny;
+    if (sl >= 0.0)
+      F[c] = fl;
+    else if (sr <= 0.0)
+      F[c] = fr;
+    else
+      F[c] = (sr * fl - sl * fr + sl * sr * (UR[c] - UL[c])) / (sr - sl);
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* stage (a): Hermite (Taylor) data at cell vertices                          */
+/* ------------------------------------------------------------------------- */
+
+/* T[e][c][k] = D^k u^e(x_c) for the sensor variable (variable 0) and
+ * beta[e][c] = ||u^e||_{x_c}^q with the pointwise semi-norm of eq. pointsnorm. */
+static void or_hermite_m(const or_mesh* m, const double* u, double* T, double* beta) {
+  int nk = or_nk(m);
+  for (int e = 0; e < m->ncell; ++e) {
+    const double* c0 = or_cell(m, u, 0, e);
+    for (int c = 0; c < m->ncorner; ++c) {
+      double xi = (c & 1) ? 1.0 : -1.0, eta = (c >> 1) ? 1.0 : -1.0;
+      double s2 = 0.0;
+      for (int t = 0; t < nk; ++t) {
+        int kx, ky;
+        or_kidx(m, t, &kx, &ky);
+        double v = or_du(m, c0, kx, ky, xi, eta);
+        T[((size_t)e * m->ncorner + c) * nk + t] = v;
+        if (kx + ky > 0) s2 += or_ipow(m->h, 2 * (kx + ky)) * v * v;
+      }
+      beta[(size_t)e * m->ncorner + c] = pow(sqrt(s2), m->d.q);
+    }
+  }
+}
+
+/* stage (b): vertex-averaged Taylor data T*[v][k] with equal linear weights */
+static void or_vertex_average_m(const or_mesh* m, const double* T, const double* beta, double* Tstar) {
+  int nk = or_nk(m);
+  for (int v = 0; v < m->nvert; ++v) {
+    double wsum = 0.0;
+    double acc[OR_MAXND];
+    for (int t = 0; t < nk; ++t) acc[t] = 0.0;
+    for (int s = 0; s < m->vcount[v]; ++s) {
+      int e = m->vcell[4 * v + s], c = m->vcorner[4 * v + s];
+      double w = 1.0 / pow(m->d.eps + beta[(size_t)e * m->ncorner + c], m->d.r);
+      wsum += w;
+      for (int t = 0; t < nk; ++t) acc[t] += w * T[((size_t)e * m->ncorner + c) * nk + t];
+    }
+    for (int t = 0; t < nk; ++t) Tstar[(size_t)v * nk + t] = acc[t] / wsum;
+  }
+}
+
+/* D^j of the vertex candidate sum_k T*_k (x-x_i)^k / k! at the physical offset (ox, oy) */
+static double or_taylor_dj(const or_mesh* m, const double* Ts, int jx, int jy, double ox, double oy) {
+  int nk = or_nk(m);
+  double s = 0.0;
+  for (int t = 0; t < nk; ++t) {
+    int kx, ky;
+    or_kidx(m, t, &kx, &ky);
+    if (kx < jx || ky < jy) continue;
+    double term = Ts[t] * or_ipow(ox, kx - jx) / or_fact(kx - jx);
+    if (m->dim == 2) term *= or_ipow(oy, ky - jy) / or_fact(ky - jy);
+    s += term;
+  }
+  return s;
+}
+
+/* physical offset of reference point (xi, eta) from corner c of the same cell */
+static void or_offset_from_corner(const or_mesh* m, int c, double xi, double eta, double* ox, double* oy) {
+  double cxi = (c & 1) ? 1.0 : -1.0, ceta = (c >> 1) ? 1.0 : -1.0;
+  *ox = 0.5 * m->dx * (xi - cxi);
+  *oy = m->dim == 2 ? 0.5 * m->dy * (eta - ceta) : 0.0;
+}
+
+/* cell wave speed lambda_e (reading A2) over volume and own face Gauss nodes */
+static int or_cell_lambda(const or_mesh* m, const double* u, int e, double* lam) {
+  if (m->d.system != OR_EULER && m->d.lambda_const > 0.0) { *lam = m->d.lambda_const; return OR_OK; }
+  double best = 0.0;
+  int npt = m->nq + (m->dim == 2 ? 4 * m->n : 2);
+  for (int t = 0; t < npt; ++t) {
+    double xi, eta, W;
+    if (t < m->nq) {
+      or_qpoint(m, t, &xi, &eta, &W);
+    } else {
+      int f = (t - m->nq) / (m->dim == 2 ? m->n : 1), s = (t - m->nq) % (m->dim == 2 ? m->n : 1);
+      if (f < 2) { xi = f == 0 ? -1.0 : 1.0; eta = m->dim == 2 ? m->gx[s] : 0.0; }
+      else { eta = f == 2 ? -1.0 : 1.0; xi = m->gx[s]; }
+    }
+    double U[OR_MAXVAR], sp;
+    for (int v = 0; v < m->nvar; ++v) U[v] = or_du(m, or_cell(m, u, v, e), 0, 0, xi, eta);
+    int st = or_wave_speed(m, U, &sp);
+    if (st) return st;
+    if (sp > best) best = sp;
+  }
+  *lam = best;
+  return OR_OK;
+}
+
+/* stage (c): cell-vertex WENO reconstruction, smoothness sensor and viscosity.
+ * norm0[e] returns ||u^e||_e (needed by stage d). */
+static int or_sensor_m(const or_mesh* m, const double* u, const double* Tstar, double* gamma, double* nu,
+                       double* norm0, double* lamv) {
+  const or_desc* d = &m->d;
+  int nk = or_nk(m), nq = m->nq, ncand = m->ncorner + 1;
+  double* Dv = (double*)malloc(sizeof(double) * ncand * nk * nq);
+  if (!Dv) return OR_ERR_NOMEM;
+  for (int e = 0; e < m->ncell; ++e) {
+    const double* c0 = or_cell(m, u, 0, e);
+    double N2[OR_MAXN + 1] = {0};
+    /* derivatives of every candidate at every volume Gauss point */
+    for (int t = 0; t < nk; ++t) {
+      int jx, jy;
+      or_kidx(m, t, &jx, &jy);
+      if (jx + jy == 0) continue;
+      double sc = or_ipow(m->h, 2 * (jx + jy) - m->dim);
+      for (int qi = 0; qi < nq; ++qi) {
+        double xi, eta, W;
+        or_qpoint(m, qi, &xi, &eta, &W);
+        double v0 = or_du(m, c0, jx, jy, xi, eta);
+        Dv[(0 * nk + t) * nq + qi] = v0;
+        N2[0] += sc * W * v0 * v0;
+        for (int l = 1; l < ncand; ++l) {
+          int c = l - 1, vtx = m->cvert[e * m->ncorner + c];
+          double ox, oy;
+          or_offset_from_corner(m, c, xi, eta, &ox, &oy);
+          double vl = or_taylor_dj(m, Tstar + (size_t)vtx * nk, jx, jy, ox, oy);
+          Dv[(l * nk + t) * nq + qi] = vl;
+          N2[l] += sc * W * vl * vl;
+        }
+      }
+    }
+    double om[OR_MAXN + 1], osum = 0.0;
+    for (int l = 0; l < ncand; ++l) {
+      double lin = l == 0 ? 1.0 - (ncand - 1) * d->gamma_vertex : d->gamma_vertex;
+      double b = pow(sqrt(N2[l]), d->q);
+      om[l] = lin / pow(d->eps + b, d->r);
+      osum += om[l];
+    }
+    for (int l = 0; l < ncand; ++l) om[l] /= osum;
+    double diff2 = 0.0;
+    for (int t = 0; t < nk; ++t) {
+      int jx, jy;
+      or_kidx(m, t, &jx, &jy);
+      if (jx + jy == 0) continue;
+      double sc = or_ipow(m->h, 2 * (jx + jy) - m->dim);
+      for (int qi = 0; qi < nq; ++qi) {
+        double xi, eta, W;
+        or_qpoint(m, qi, &xi, &eta, &W);
+        double ustar = 0.0;
+        for (int l = 0; l < ncand; ++l) ustar += om[l] * Dv[(l * nk + t) * nq + qi];
+        double df = Dv[(0 * nk + t) * nq + qi] - ustar;
+        diff2 += sc * W * df * df;
+      }
+    }
+    double nrm = sqrt(N2[0]);
+    double g;
+    if (d->sensor_mode == 1)
+      g = 1.0;
+    else if (d->sensor_mode == 2)
+      g = 0.0;
+    else if (nrm <= 1e-30)
+      g = 1.0;
+    else
+      g = 1.0 - pow(fmin(1.0, sqrt(diff2) / nrm), d->q);
+    double lam;
+    int st = or_cell_lambda(m, u, e, &lam);
+    if (st) { free(Dv); return st; }
+    gamma[e] = g;
+    nu[e] = lam * m->h / (2.0 * m->p);
+    if (norm0) norm0[e] = nrm;
+    if (lamv) lamv[e] = lam;
+  }
+  free(Dv);
+  return OR_OK;
+}
+
+/* stage (d): nonlinear quadrature weights alpha[e][var][q] and the troubled flag */
+static void or_sc_weights_m(const or_mesh* m, const double* u, const double* gamma, const double* norm0,
+                            const int* override_troubled, double* alpha, int* troubled) {
+  const or_desc* d = &m->d;
+  int nq = m->nq, nk = or_nk(m);
+  for (int e = 0; e < m->ncell; ++e) {
+    int tr = d->sc_quadrature && gamma[e] < d->c_gamma && norm0[e] > 1e-30;
+    if (override_troubled && override_troubled[e] >= 0) tr = override_troubled[e] && norm0[e] > 1e-30;
+    troubled[e] = tr;
+    for (int v = 0; v < m->nvar; ++v)
+      for (int qi = 0; qi < nq; ++qi) alpha[((size_t)e * m->nvar + v) * nq + qi] = 1.0;
+    if (!tr) continue;
+    double at[OR_MAXND], W[OR_MAXND];
+    const double* c0 = or_cell(m, u, 0, e);
+    for (int qi = 0; qi < nq; ++qi) {
+      double xi, eta;
+      or_qpoint(m, qi, &xi, &eta, &W[qi]);
+      double s2 = 0.0;
+      for (int t = 0; t < nk; ++t) {
+        int kx, ky;
+        or_kidx(m, t, &kx, &ky);
+        if (kx + ky == 0) continue;
+        double v = or_du(m, c0, kx, ky, xi, eta);
+        s2 += or_ipow(m->h, 2 * (kx + ky)) * v * v;
+      }
+      at[qi] = sqrt(s2) / norm0[e]; /* eq. alpha_prelim */
+    }
+    for (int v = 0; v < m->nvar; ++v) {
+      const double* cv = or_cell(m, u, v, e);
+      double f[OR_MAXND], s1 = 0.0, s2 = 0.0;
+      for (int qi = 0; qi < nq; ++qi) {
+        double xi, eta, Wq;
+        or_qpoint(m, qi, &xi, &eta, &Wq);
+        double gx = or_du(m, cv, 1, 0, xi, eta);
+        double gy = m->dim == 2 ? or_du(m, cv, 0, 1, xi, eta) : 0.0;
+        f[qi] = (1.0 - gamma[e]) * (gx * gx + gy * gy); /* DG f_q */
+        s1 += W[qi] * f[qi];
+        s2 += W[qi] * at[qi] * f[qi];
+      }
+      if (s2 > 0.0)
+        for (int qi = 0; qi < nq; ++qi) alpha[((size_t)e * m->nvar + v) * nq + qi] = at[qi] * s1 / s2; /* eq. alphaq */
+    }
+  }
+}
+
+/* trace of all variables of cell e at reference point (xi, eta) */
+static void or_trace(const or_mesh* m, const double* u, int e, double xi, double eta, double* U) {
+  for (int v = 0; v < m->nvar; ++v) U[v] = or_du(m, or_cell(m, u, v, e), 0, 0, xi, eta);
+}
+
+/* stage (e): r = int grad phi . f(u) - sum faces int phi F* . n - s_h(u, phi);
+ * dudt = M^{-1} r, M computed by the same Gauss rule. */
+static int or_residual_m(const or_mesh* m, const double* u, const double* gamma, const double* nu,
+                         const double* alpha, double* dudt) {
+  int nd = m->nd, nq = m->nq, nv = m->nvar;
+  size_t ntot = (size_t)nv * m->ncell * nd;
+  for (size_t t = 0; t < ntot; ++t) dudt[t] = 0.0;
+  /* volume terms */
+  for (int e = 0; e < m->ncell; ++e) {
+    double mu = (1.0 - gamma[e]) * nu[e];
+    for (int qi = 0; qi < nq; ++qi) {
+      double xi, eta, W;
+      or_qpoint(m, qi, &xi, &eta, &W);
+      double U[OR_MAXVAR], Fx[OR_MAXVAR], Fy[OR_MAXVAR], Gx[OR_MAXVAR], Gy[OR_MAXVAR];
+      for (int v = 0; v < nv; ++v) {
+        const double* cv = or_cell(m, u, v, e);
+        U[v] = or_du(m, cv, 0, 0, xi, eta);
+        Gx[v] = or_du(m, cv, 1, 0, xi, eta);
+        Gy[v] = m->dim == 2 ? or_du(m, cv, 0, 1, xi, eta) : 0.0;
+      }
+      or_flux(m, U, Fx, Fy);
+      for (int v = 0; v < nv; ++v) {
+        double a = alpha[((size_t)e * nv + v) * nq + qi];
+        double* r = dudt + ((size_t)v * m->ncell + e) * nd;
+        for (int mi = 0; mi < nd; ++mi) {
+          double px = or_dphi(m, mi, 1, 0, xi, eta);
+          double py = m->dim == 2 ? or_dphi(m, mi, 0, 1, xi, eta) : 0.0;
+          r[mi] += W * (px * Fx[v] + (m->dim == 2 ? py * Fy[v] : 0.0));
+          r[mi] -= mu * a * W * (px * Gx[v] + py * Gy[v]);
+        }
+      }
+    }
+  }
+  /* faces: direction 0 = x-faces, 1 = y-faces */
+  for (int dirn = 0; dirn < m->dim; ++dirn) {
+    int na = dirn == 0 ? m->nx : m->ny; /* cells along the normal */
+    int nb = dirn == 0 ? m->ny : m->nx; /* cells along the face */
+    int per = m->d.bc[2 * dirn] == OR_PERIODIC;
+    int nface = per ? na : na + 1;
+    int nfp = m->dim == 2 ? m->n : 1;
+    double fw = m->dim == 2 ? (dirn == 0 ? 0.5 * m->dy : 0.5 * m->dx) : 1.0;
+    double nxn = dirn == 0 ? 1.0 : 0.0, nyn = dirn == 0 ? 0.0 : 1.0;
+    for (int b = 0; b < nb; ++b) {
+      for (int a = 0; a < nface; ++a) {
+        int aL = a - 1, aR = a;
+        if (per) { aL = (a - 1 + na) % na; }
+        int eL = -1, eR = -1;
+        if (aL >= 0) eL = dirn == 0 ? aL + m->nx * b : b + m->nx * aL;
+        if (aR < na) eR = dirn == 0 ? aR + m->nx * b : b + m->nx * aR;
+        for (int s = 0; s < nfp; ++s) {
+          double tcoord = m->dim == 2 ? m->gx[s] : 0.0;
+          double wq = m->dim == 2 ? m->gw[s] : 1.0;
+          double xiL = dirn == 0 ? 1.0 : tcoord, etaL = dirn == 0 ? tcoord : 1.0;
+          double xiR = dirn == 0 ? -1.0 : tcoord, etaR = dirn == 0 ? tcoord : -1.0;
+          double UL[OR_MAXVAR] = {0}, UR[OR_MAXVAR] = {0}, F[OR_MAXVAR];
+          if (eL >= 0) or_trace(m, u, eL, xiL, etaL, UL);
+          if (eR >= 0) or_trace(m, u, eR, xiR, etaR, UR);
+          if (eL < 0) memcpy(UL, UR, sizeof(UL));
+          if (eR < 0) memcpy(UR, UL, sizeof(UR));
+          int st = or_numflux(m, UL, UR, nxn, nyn, F);
+          if (st) return st;
+          for (int v = 0; v < nv; ++v) {
+            for (int mi = 0; mi < nd; ++mi) {
+              if (eL >= 0)
+                dudt[((size_t)v * m->ncell + eL) * nd + mi] -= fw * wq * or_dphi(m, mi, 0, 0, xiL, etaL) * F[v];
+              if (eR >= 0)
+                dudt[((size_t)v * m->ncell + eR) * nd + mi] += fw * wq * or_dphi(m, mi, 0, 0, xiR, etaR) * F[v];
+            }
+          }
+        }
+      }
+    }
+  }
+  /* mass matrix: diagonal for the Legendre basis, computed by quadrature */
+  for (int mi = 0; mi < nd; ++mi) {
+    double M = 0.0;
+    for (int qi = 0; qi < nq; ++qi) {
+      double xi, eta, W;
+      or_qpoint(m, qi, &xi, &eta, &W);
+      double ph = or_dphi(m, mi, 0, 0, xi, eta);
+      M += W * ph * ph;
+    }
+    for (int v = 0; v < nv; ++v)
+      for (int e = 0; e < m->ncell; ++e) dudt[((size_t)v * m->ncell + e) * nd + mi] /= M;
+  }
+  for (size_t t = 0; t < ntot; ++t)
+    if (!isfinite(dudt[t])) return OR_ERR_NONFINITE;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* exported entry points                                                      */
+/* ------------------------------------------------------------------------- */
+
+int or_mesh_counts(const or_desc* d, int* ncell, int* ndof, int* nvar, int* nvert, int* nq) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  if (ncell) *ncell = m.ncell;
+  if (ndof) *ndof = m.nd;
+  if (nvar) *nvar = m.nvar;
+  if (nvert) *nvert = m.nvert;
+  if (nq) *nq = m.nq;
+  or_mesh_free(&m);
+  return OR_OK;
+}
+
+/* geometric vertex patches: count[v], cell[v][4], corner[v][4] (-1 padded), and the
+ * vertex of each cell corner cvert[e][c]. */
+int or_vertex_patches(const or_desc* d, int* count, int* cell, int* corner, int* cvert) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  memcpy(count, m.vcount, sizeof(int) * m.nvert);
+  memcpy(cell, m.vcell, sizeof(int) * m.nvert * 4);
+  memcpy(corner, m.vcorner, sizeof(int) * m.nvert * 4);
+  memcpy(cvert, m.cvert, sizeof(int) * m.ncell * m.ncorner);
+  or_mesh_free(&m);
+  return OR_OK;
+}
+
+int or_gauss_rule(int n, double* x, double* w) {
+  if (n < 1 || n > 64) return OR_ERR_ARG;
+  or_gauss(n, x, w);
+  return OR_OK;
+}
+
+double or_legendre_dk(int m, int k, double x) { return or_leg_dk(m, k, x); }
+
+int or_hermite(const or_desc* d, const double* u, double* T, double* beta) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  or_hermite_m(&m, u, T, beta);
+  or_mesh_free(&m);
+  return OR_OK;
+}
+
+int or_vertex_average(const or_desc* d, const double* u, double* Tstar) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  size_t nT = (size_t)m.ncell * m.ncorner * m.nd;
+  double* T = (double*)malloc(sizeof(double) * nT);
+  double* beta = (double*)malloc(sizeof(double) * m.ncell * m.ncorner);
+  if (!T || !beta) { free(T); free(beta); or_mesh_free(&m); return OR_ERR_NOMEM; }
+  or_hermite_m(&m, u, T, beta);
+  or_vertex_average_m(&m, T, beta, Tstar);
+  free(T);
+  free(beta);
+  or_mesh_free(&m);
+  return OR_OK;
+}
+
+/* Full stage: sensor, SC weights and residual.  Any output pointer may be NULL.
+ * override_troubled (may be NULL): per cell -1 = decide, 0/1 = force the SC decision. */
+int or_residual(const or_desc* d, const double* u, const int* override_troubled, double* dudt, double* gamma_out,
+                double* nu_out, double* alpha_out, int* troubled_out) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  size_t nT = (size_t)m.ncell * m.ncorner * m.nd;
+  double* T = (double*)malloc(sizeof(double) * nT);
+  double* beta = (double*)malloc(sizeof(double) * m.ncell * m.ncorner);
+  double* Tstar = (double*)malloc(sizeof(double) * (size_t)m.nvert * m.nd);
+  double* gamma = (double*)malloc(sizeof(double) * m.ncell);
+  double* nu = (double*)malloc(sizeof(double) * m.ncell);
+  double* norm0 = (double*)malloc(sizeof(double) * m.ncell);
+  double* alpha = (double*)malloc(sizeof(double) * (size_t)m.ncell * m.nvar * m.nq);
+  int* troubled = (int*)malloc(sizeof(int) * m.ncell);
+  double* r = dudt ? NULL : (double*)malloc(sizeof(double) * (size_t)m.nvar * m.ncell * m.nd);
+  if (!T || !beta || !Tstar || !gamma || !nu || !norm0 || !alpha || !troubled || (!dudt && !r)) {
+    st = OR_ERR_NOMEM;
+    goto done;
+  }
+  or_hermite_m(&m, u, T, beta);
+  or_vertex_average_m(&m, T, beta, Tstar);
+  st = or_sensor_m(&m, u, Tstar, gamma, nu, norm0, NULL);
+  if (st) goto done;
+  or_sc_weights_m(&m, u, gamma, norm0, override_troubled, alpha, troubled);
+  st = or_residual_m(&m, u, gamma, nu, alpha, dudt ? dudt : r);
+  if (gamma_out) memcpy(gamma_out, gamma, sizeof(double) * m.ncell);
+  if (nu_out) memcpy(nu_out, nu, sizeof(double) * m.ncell);
+  if (alpha_out) memcpy(alpha_out, alpha, sizeof(double) * (size_t)m.ncell * m.nvar * m.nq);
+  if (troubled_out) memcpy(troubled_out, troubled, sizeof(int) * m.ncell);
+done:
+  free(T);
+  free(beta);
+  free(Tstar);
+  free(gamma);
+  free(nu);
+  free(norm0);
+  free(alpha);
+  free(troubled);
+  free(r);
+  or_mesh_free(&m);
+  return st;
+}
+
+/* Stage (e) alone with caller-given gamma_e, nu_e and alpha_q (for per-stage tests). */
+int or_residual_given(const or_desc* d, const double* u, const double* gamma, const double* nu, const double* alpha,
+                      double* dudt) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  st = or_residual_m(&m, u, gamma, nu, alpha, dudt);
+  or_mesh_free(&m);
+  return st;
+}
+
+/* Stage (d) alone: SC weights for caller-given gamma_e. */
+int or_sc_weights(const or_desc* d, const double* u, const double* gamma, double* alpha, int* troubled) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  double* norm0 = (double*)calloc(m.ncell, sizeof(double));
+  int* tr = troubled ? troubled : (int*)malloc(sizeof(int) * m.ncell);
+  if (!norm0 || !tr) { st = OR_ERR_NOMEM; goto done; }
+  /* ||u^e||_e by quadrature, eq. snorm */
+  for (int e = 0; e < m.ncell; ++e) {
+    const double* c0 = or_cell(&m, u, 0, e);
+    double s = 0.0;
+    for (int t = 0; t < or_nk(&m); ++t) {
+      int jx, jy;
+      or_kidx(&m, t, &jx, &jy);
+      if (jx + jy == 0) continue;
+      double sc = or_ipow(m.h, 2 * (jx + jy) - m.dim);
+      for (int qi = 0; qi < m.nq; ++qi) {
+        double xi, eta, W;
+        or_qpoint(&m, qi, &xi, &eta, &W);
+        double v = or_du(&m, c0, jx, jy, xi, eta);
+        s += sc * W * v * v;
+      }
+    }
+    norm0[e] = sqrt(s);
+  }
+  or_sc_weights_m(&m, u, gamma, norm0, NULL, alpha, tr);
+done:
+  free(norm0);
+  if (!troubled) free(tr);
+  or_mesh_free(&m);
+  return st;
+}
+
+/* max over cells of lambda_e (reading A2), for the CFL time step */
+int or_max_wavespeed(const or_desc* d, const double* u, double* lam_max) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  double best = 0.0;
+  for (int e = 0; e < m.ncell; ++e) {
+    double lam;
+    st = or_cell_lambda(&m, u, e, &lam);
+    if (st) break;
+    if (lam > best) best = lam;
+  }
+  *lam_max = best;
+  or_mesh_free(&m);
+  return st;
+}
+
+/* SSP-RK3 in Shu-Osher form, nsteps steps of size dt (in place). */
+int or_ssprk3(const or_desc* d, double* u, double dt, int nsteps) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  size_t N = (size_t)m.nvar * m.ncell * m.nd;
+  or_mesh_free(&m);
+  double* L = (double*)malloc(sizeof(double) * N);
+  double* u1 = (double*)malloc(sizeof(double) * N);
+  double* u2 = (double*)malloc(sizeof(double) * N);
+  if (!L || !u1 || !u2) { free(L); free(u1); free(u2); return OR_ERR_NOMEM; }
+  for (int s = 0; s < nsteps && !st; ++s) {
+    st = or_residual(d, u, NULL, L, NULL, NULL, NULL, NULL);
+    if (st) break;
+    for (size_t t = 0; t < N; ++t) u1[t] = u[t] + dt * L[t];
+    st = or_residual(d, u1, NULL, L, NULL, NULL, NULL, NULL);
+    if (st) break;
+    for (size_t t = 0; t < N; ++t) u2[t] = 0.75 * u[t] + 0.25 * (u1[t] + dt * L[t]);
+    st = or_residual(d, u2, NULL, L, NULL, NULL, NULL, NULL);
+    if (st) break;
+    for (size_t t = 0; t < N; ++t) u[t] = u[t] / 3.0 + 2.0 / 3.0 * (u2[t] + dt * L[t]);
+  }
+  free(L);
+  free(u1);
+  free(u2);
+  return st;
+}
+
+/* integral of every variable over the domain: sum_e int_{K_e} u_h (by quadrature) */
+int or_mass_total(const or_desc* d, const double* u, double* totals) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  for (int v = 0; v < m.nvar; ++v) {
+    double s = 0.0;
+    for (int e = 0; e < m.ncell; ++e)
+      for (int qi = 0; qi < m.nq; ++qi) {
+        double xi, eta, W;
+        or_qpoint(&m, qi, &xi, &eta, &W);
+        s += W * or_du(&m, or_cell(&m, u, v, e), 0, 0, xi, eta);
+      }
+    totals[v] = s;
+  }
+  or_mesh_free(&m);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* initial data: analytic fields and their L2 projection (reading A17)        */
+/* ------------------------------------------------------------------------- */
+
+static void or_prim_to_cons(double g, double rho, double vx, double vy, double p, double* U) {
+  U[0] = rho;
+  U[1] = rho * vx;
+  U[2] = rho * vy;
+  U[3] = p / (g - 1.0) + 0.5 * rho * (vx * vx + vy * vy);
+}
+
+/* analytic initial datum at (x, y); params layout documented in the Python wrapper */
+static void or_ic_eval(const or_desc* d, int type, const double* P, double x, double y, double* U) {
+  switch (type) {
+    case IC_CONST:
+      for (int v = 0; v < 4; ++v) U[v] = P[v];
+      break;
+    case IC_SINE_STEP: /* A sin(2 pi k (x - x0)/Lx) + B H(x - s) */
+      U[0] = P[0] * sin(2.0 * M_PI * P[1] * (x - d->x0) / (d->x1 - d->x0)) + (x >= P[3] ? P[2] : 0.0);
+      break;
+    case IC_CIRCLE: { /* center (P0,P1), radius P2, inside P3, outside P4 */
+      double rx = x - P[0], ry = y - P[1];
+      U[0] = (rx * rx + ry * ry <= P[2] * P[2]) ? P[3] : P[4];
+      break;
+    }
+    case IC_QUADRANTS: { /* split (P0,P1); quadrant qx + 2 qy has primitives P[2+4q .. 5+4q] */
+      int qd = (x >= P[0] ? 1 : 0) + 2 * (y >= P[1] ? 1 : 0);
+      const double* s = P + 2 + 4 * qd;
+      or_prim_to_cons(d->gas_gamma, s[0], s[1], s[2], s[3], U);
+      break;
+    }
+    case IC_FOURIER: { /* P0 = number of modes M; mode j: a, kx, ky, phase at P[1+4j..] */
+      int M = (int)P[0];
+      double s = 0.0, lx = d->x1 - d->x0, ly = d->dim == 2 ? d->y1 - d->y0 : 1.0;
+      for (int j = 0; j < M; ++j) {
+        const double* md = P + 1 + 4 * j;
+        s += md[0] * sin(2.0 * M_PI * (md[1] * (x - d->x0) / lx + md[2] * (y - d->y0) / ly) + md[3]);
+      }
+      U[0] = s;
+      break;
+    }
+    case IC_POLY: { /* sum_{i,j<=4} P[i + 5 j] x^i y^j */
+      double s = 0.0;
+      for (int j = 0; j < 5; ++j)
+        for (int i = 0; i < 5; ++i) s += P[i + 5 * j] * or_ipow(x, i) * or_ipow(y, j);
+      U[0] = s;
+      break;
+    }
+    case IC_DENSITY_WAVE: { /* rho = 1 + A sin(2 pi (kx x/Lx + ky y/Ly)), v = (P3,P4), p = P5 */
+      double lx = d->x1 - d->x0, ly = d->y1 - d->y0;
+      double rho = 1.0 + P[0] * sin(2.0 * M_PI * (P[1] * (x - d->x0) / lx + P[2] * (y - d->y0) / ly));
+      or_prim_to_cons(d->gas_gamma, rho, P[3], P[4], P[5], U);
+      break;
+    }
+    default:
+      U[0] = U[1] = U[2] = U[3] = 0.0;
+  }
+}
+
+int or_ic_point(const or_desc* d, int type, const double* params, double x, double y, double* U) {
+  or_ic_eval(d, type, params, x, y, U);
+  return OR_OK;
+}
+
+/* L2 projection onto the DG space with a 12-point Gauss rule per direction. */
+int or_project(const or_desc* d, int type, const double* params, double* u) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  double px[OR_NPROJ], pw[OR_NPROJ];
+  or_gauss(OR_NPROJ, px, pw);
+  int npy = m.dim == 2 ? OR_NPROJ : 1;
+  for (int e = 0; e < m.ncell; ++e) {
+    int i = e % m.nx, j = e / m.nx;
+    double xc = d->x0 + (i + 0.5) * m.dx;
+    double yc = m.dim == 2 ? d->y0 + (j + 0.5) * m.dy : 0.0;
+    double acc[OR_MAXVAR][OR_MAXND], mass[OR_MAXND];
+    memset(acc, 0, sizeof(acc));
+    memset(mass, 0, sizeof(mass));
+    for (int b = 0; b < npy; ++b)
+      for (int a = 0; a < OR_NPROJ; ++a) {
+        double xi = px[a], eta = m.dim == 2 ? px[b] : 0.0;
+        double W = pw[a] * (m.dim == 2 ? pw[b] : 1.0);
+        double U[4];
+        or_ic_eval(d, type, params, xc + 0.5 * m.dx * xi, yc + 0.5 * m.dy * eta, U);
+        for (int mi = 0; mi < m.nd; ++mi) {
+          double ph = or_dphi(&m, mi, 0, 0, xi, eta);
+          mass[mi] += W * ph * ph;
+          for (int v = 0; v < m.nvar; ++v) acc[v][mi] += W * ph * U[v];
+        }
+      }
+    for (int v = 0; v < m.nvar; ++v)
+      for (int mi = 0; mi < m.nd; ++mi) u[((size_t)v * m.ncell + e) * m.nd + mi] = acc[v][mi] / mass[mi];
+  }
+  or_mesh_free(&m);
+  return OR_OK;
+}
+
+/* values of variable var at the nq1d^dim Gauss points of every cell, with the
+ * physical coordinates and weights of those points (for L1 norms). */
+int or_eval_points(const or_desc* d, const double* u, int var, int nq1d, double* vals, double* xs, double* ys,
+                   double* ws) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  if (nq1d < 1 || nq1d > 32 || var < 0 || var >= m.nvar) { or_mesh_free(&m); return OR_ERR_ARG; }
+  double px[32], pw[32];
+  or_gauss(nq1d, px, pw);
+  int npy = m.dim == 2 ? nq1d : 1;
+  size_t t = 0;
+  for (int e = 0; e < m.ncell; ++e) {
+    int i = e % m.nx, j = e / m.nx;
+    double xc = d->x0 + (i + 0.5) * m.dx;
+    double yc = m.dim == 2 ? d->y0 + (j + 0.5) * m.dy : 0.0;
+    for (int b = 0; b < npy; ++b)
+      for (int a = 0; a < nq1d; ++a, ++t) {
+        double xi = px[a], eta = m.dim == 2 ? px[b] : 0.0;
+        if (vals) vals[t] = or_du(&m, or_cell(&m, u, var, e), 0, 0, xi, eta);
+        if (xs) xs[t] = xc + 0.5 * m.dx * xi;
+        if (ys) ys[t] = yc + 0.5 * m.dy * eta;
+        if (ws) ws[t] = pw[a] * (m.dim == 2 ? pw[b] : 1.0) * m.jac;
+      }
+  }
+  or_mesh_free(&m);
+  return OR_OK;
+}
