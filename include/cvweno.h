@@ -1,0 +1,190 @@
+/*
+ * cvweno.h -- C ABI of the GB300 (sm_103a) cell-vertex WENO stabilised DG solver.
+ *
+ * The library computes, on one GPU, the per-stage stabilised residual of
+ * Vedral & Kuzmin, "Cell-vertex WENO schemes with shock-capturing quadrature for
+ * high-order finite element discretizations of hyperbolic problems" (arXiv
+ * 2601.16911), for du/dt + div f(u) = 0 (Sec. 2, eq. pde) on uniform 1D meshes and
+ * uniform structured quadrilateral meshes, DG with tensor Legendre Q_p, p = 1..4:
+ *
+ *   (a) Hermite (Taylor) data of every cell at its vertices   Sec. 3.2, eq. taylorsol,
+ *                                                              eq. pointsnorm
+ *   (b) vertex-averaged HWENO candidates                       Sec. 3.2, eq. taylorcand
+ *   (c) cell-vertex WENO reconstruction, sensor gamma_e and
+ *       viscosity nu_e                                         Sec. 3.2 eq. finalweno,
+ *                                                              Sec. 2.2 eq. gamma, snorm,
+ *                                                              lostab
+ *   (d) shock-capturing quadrature weights alpha_q             Sec. 4, eq. alphaq,
+ *                                                              eq. alpha_prelim
+ *   (e) volume + face residual with the dissipation added      Sec. 2.1 eq. convop,
+ *       (LLF for scalar laws, HLL for Euler), M^{-1}, SSP-RK3  Sec. 2.2 eq. stab, sdstab
+ *
+ * Conventions (all entry points):
+ *   - Every float pointer is a CALLER-OWNED DEVICE pointer, contiguous, laid out
+ *     u[var][cell][k] with cell = i + nx*j and k = kx + (p+1)*ky (tensor Legendre
+ *     mode, 1D: k = kx).  The library never frees caller memory.
+ *   - Host pointers are marked "host".  Streams are cudaStream_t passed as void*;
+ *     NULL means the legacy default stream.  Work is stream-ordered; an entry point
+ *     only synchronises where it says so.
+ *   - Errors are returned as cvweno_status; nothing is thrown across the ABI.
+ *     Kernels report non-finite values and non-positive density/pressure through a
+ *     device status word that cvweno_status_check() (and every synchronising
+ *     entry point) reads and clears.
+ *   - A mesh owns its tables and scratch (two stage buffers of the state size).
+ *     Calls on one mesh must not overlap on different streams.
+ */
+#ifndef CVWENO_H
+#define CVWENO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cvweno_mesh_s* cvweno_mesh;
+
+typedef enum {
+  CVWENO_OK = 0,
+  CVWENO_ERR_ARG = 1,          /* invalid argument (NULL pointer, bad size, bad combination) */
+  CVWENO_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  CVWENO_ERR_NONFINITE = 3,    /* a kernel produced a NaN/Inf */
+  CVWENO_ERR_POSITIVITY = 4,   /* Euler: non-positive density or pressure at a node */
+  CVWENO_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  CVWENO_ERR_UNSUPPORTED = 6,  /* valid but not implemented (degree, kind, system) */
+  CVWENO_ERR_NOMEM = 7         /* device or host allocation failed */
+} cvweno_status;
+
+enum { CVWENO_DG = 0, CVWENO_CG = 1 };
+enum { CVWENO_PERIODIC = 0, CVWENO_TRANSMISSIVE = 1 };
+/* flux f: BURGERS 1D u^2/2, 2D (u^2/2, u^2/2); KPP (sin u, cos u) (Sec. 5.3);
+ * LINADV (vx u, vy u); EULER ideal gas (rho, rho v, rho E) (Sec. 5.4) */
+enum { CVWENO_BURGERS = 0, CVWENO_KPP = 1, CVWENO_LINADV = 2, CVWENO_EULER = 3 };
+/* sensor_mode: COMPUTED = eq. gamma; SMOOTH forces gamma_e = 1; TROUBLED forces 0 */
+enum { CVWENO_SENSOR_COMPUTED = 0, CVWENO_SENSOR_SMOOTH = 1, CVWENO_SENSOR_TROUBLED = 2 };
+/* analytic initial data for cvweno_project; parameter layouts in cvweno_project */
+enum {
+  CVWENO_IC_CONST = 0,
+  CVWENO_IC_SINE_STEP = 1,
+  CVWENO_IC_CIRCLE = 2,
+  CVWENO_IC_QUADRANTS = 3,
+  CVWENO_IC_FOURIER = 4,
+  CVWENO_IC_POLY = 5,
+  CVWENO_IC_DENSITY_WAVE = 6
+};
+
+/* Method parameters.  Defaults (cvweno_default_params) are the paper's:
+ * eps = 1e-6, r = 2 (Sec. 3.2, Jiang-Shu), q = 1 (Sec. 5), vertex linear weight
+ * 1e-3 (Sec. 3.2), C_gamma = 0.9 (Sec. 5), SC quadrature on, gas gamma = 1.4. */
+typedef struct {
+  double eps;           /* Jiang-Shu epsilon */
+  double r;             /* Jiang-Shu power; must be an integer in [1, 8] */
+  double q;             /* exponent q of eq. gamma and of both indicators, >= 1 */
+  double gamma_vertex;  /* linear weight of each vertex candidate; cell gets 1 - v_e * this */
+  double c_gamma;       /* SC quadrature cutoff: redistribute iff gamma_e < c_gamma */
+  int sc_quadrature;    /* 1: shock-capturing quadrature (Sec. 4) on; 0: off */
+  int sensor_mode;      /* CVWENO_SENSOR_* */
+  double lambda_const;  /* > 0: fixed wave speed for nu_e and LLF (KPP: 1); <= 0: computed */
+  double gas_gamma;     /* Euler heat capacity ratio */
+  double adv_vx, adv_vy;/* LINADV velocity */
+} cvweno_params;
+
+typedef struct {
+  int dim;              /* 1 or 2 */
+  int nx, ny;           /* cells per direction (ny ignored in 1D) */
+  int degree;           /* p in 1..4 */
+  int kind;             /* CVWENO_DG (CG returns CVWENO_ERR_UNSUPPORTED) */
+  int system;           /* CVWENO_BURGERS | KPP | LINADV | EULER (KPP, EULER: 2D only) */
+  int bc[4];            /* x-low, x-high, y-low, y-high: PERIODIC or TRANSMISSIVE;
+                           periodic sides must come in pairs */
+  double x0, x1, y0, y1;/* box [x0,x1] x [y0,y1] (y ignored in 1D) */
+  cvweno_params params;
+} cvweno_mesh_desc;
+
+/* Fill *p with the paper's parameter values (see cvweno_params). */
+void cvweno_default_params(cvweno_params* p);
+
+/* Build the mesh: host tables (vertex patches, colouring), basis tabulations in
+ * FP64 rounded once to FP32, device scratch.  desc and out are host pointers.
+ * Returns ERR_ARG for inconsistent sizes/sides, ERR_UNSUPPORTED for CG, degree > 4,
+ * 1D Euler/KPP or a non-integer r.  Makes the current device the mesh's device. */
+cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* desc, cvweno_mesh* out);
+
+/* Free everything the mesh owns (synchronises its device).  NULL is accepted. */
+cvweno_status cvweno_mesh_destroy(cvweno_mesh m);
+
+/* Sizes (host out-pointers, each may be NULL): cells, DOFs per cell per variable
+ * ((p+1)^dim), conserved variables (1 or 4), vertices (periodic sides identify
+ * their vertices), quadrature points per cell ((p+1)^dim Gauss-Legendre). */
+cvweno_status cvweno_mesh_info(cvweno_mesh m, int64_t* ncells, int64_t* ndof_per_var, int* nvars,
+                               int64_t* nverts, int* nquad);
+
+/* Host copies of the integer mesh tables (host arrays, each may be NULL):
+ *   cell_vertices[ncells][2^dim]  vertex of corner c = cx + 2 cy of each cell
+ *   vertex_cells[nverts][2^dim]   cells around each vertex in the fixed slot order
+ *                                 SW, SE, NW, NE (1D: W, E); -1 where a transmissive
+ *                                 side leaves a slot empty
+ *   colour[ncells]                a colouring in which no two cells sharing a vertex
+ *                                 have the same colour (at most 9 colours) */
+cvweno_status cvweno_mesh_tables(cvweno_mesh m, int32_t* cell_vertices, int32_t* vertex_cells, int32_t* colour);
+
+/* L2 projection of an analytic initial datum onto the DG space (12-point Gauss rule
+ * per direction), written to u (device, state layout).  ic_params: host array of 64
+ * doubles:
+ *   CONST: conserved state [0..3]; SINE_STEP: A sin(2 pi k (x-x0)/Lx) + B H(x - s) with
+ *   (A, k, B, s); CIRCLE: (cx, cy, R, inside, outside); QUADRANTS (Euler): split (xs, ys)
+ *   then (rho, vx, vy, p) of quadrant qx + 2 qy; FOURIER: M then M x (a, kx, ky, phase)
+ *   of sum a sin(2 pi (kx (x-x0)/Lx + ky (y-y0)/Ly) + phase); POLY: params[i + 5 j] is
+ *   the coefficient of x^i y^j (i, j <= 4); DENSITY_WAVE (Euler):
+ *   rho = 1 + A sin(2 pi (kx (x-x0)/Lx + ky (y-y0)/Ly)), velocity (vx, vy), pressure p0
+ *   with (A, kx, ky, vx, vy, p0). */
+cvweno_status cvweno_project(cvweno_mesh m, int ic_type, const double* ic_params, float* u, void* stream);
+
+/* Stages (a)+(b) only, for inspection: T*[nverts][(p+1)^dim] (device), the vertex
+ * candidate's physical derivatives D^k u*_i(x_i), k = kx + (p+1) ky (eq. taylorcand). */
+cvweno_status cvweno_vertex_data(cvweno_mesh m, const float* u, float* tstar, void* stream);
+
+/* Stages (a)-(c): smoothness sensor gamma_e (eq. gamma) and viscosity
+ * nu_e = lambda_e h_e / (2p) (eq. lostab), both [ncells] device arrays. */
+cvweno_status cvweno_sensor(cvweno_mesh m, const float* u, float* gamma, float* nu, void* stream);
+
+/* Stages (a)-(e): dudt = M^{-1} r (device, state layout).  Optional device outputs
+ * (NULL to skip): gamma[ncells], nu[ncells], alpha[ncells][nvars][nquad] (the SC
+ * weights, 1 where not redistributed; q = qx + (p+1) qy), troubled[ncells] (1 where
+ * SC redistributed).  troubled_override (device int32[ncells] or NULL): -1 = decide,
+ * 0/1 = force the SC decision of that cell (used to compare decisions taken in
+ * another precision). */
+cvweno_status cvweno_residual_ex(cvweno_mesh m, const float* u, const int32_t* troubled_override, float* dudt,
+                                 float* gamma, float* nu, float* alpha, int32_t* troubled, void* stream);
+
+/* Stages (a)-(e): dudt = M^{-1} r (device, state layout). */
+cvweno_status cvweno_residual(cvweno_mesh m, const float* u, float* dudt, void* stream);
+
+/* One SSP-RK3 step (Shu-Osher form) in place on u (device).  dt > 0: that step size,
+ * no synchronisation.  dt <= 0: dt = cfl * min(dx, dy) / (dim * max lambda_e), which
+ * reads the FP64 maximum back (synchronises) and also checks the status word.
+ * dt_used (host, may be NULL) receives the step size. */
+cvweno_status cvweno_step(cvweno_mesh m, float* u, double dt, double cfl, double* dt_used, void* stream);
+
+/* nsteps SSP-RK3 steps of fixed size dt > 0, enqueued without synchronisation. */
+cvweno_status cvweno_advance(cvweno_mesh m, float* u, double dt, int nsteps, void* stream);
+
+/* FP64 totals sum_e int_{K_e} u_h of every conserved variable into totals[nvars]
+ * (host).  Synchronises. */
+cvweno_status cvweno_mass_total(cvweno_mesh m, const float* u, double* totals, void* stream);
+
+/* FP64 maximum over cells of lambda_e (the CFL wave speed) into *lam (host).
+ * Synchronises and checks the status word. */
+cvweno_status cvweno_max_wavespeed(cvweno_mesh m, const float* u, double* lam, void* stream);
+
+/* Synchronise the stream, read and clear the mesh's device status word. */
+cvweno_status cvweno_status_check(cvweno_mesh m, void* stream);
+
+/* Static description of a status code. */
+const char* cvweno_status_string(cvweno_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CVWENO_H */

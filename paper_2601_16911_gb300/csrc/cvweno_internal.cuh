@@ -1,0 +1,114 @@
+// Internal declarations of the GB300 cell-vertex WENO library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cvweno.h"
+
+namespace cvw {
+
+constexpr int kMaxP = 4;
+
+// Status bits raised by kernels in the mesh's device status word.
+enum : int { kStatNonfinite = 1, kStatPositivity = 2 };
+
+// Reference-cell tabulations of one (dim, p) pair, FP64 on the host rounded once to
+// FP32, passed to the kernels by value (__grid_constant__), so that every warp reads
+// them through the constant bank with uniform addresses.
+//   E[k][m]     = P_m^(k)(+1); the value at -1 is (-1)^(m+k) E[k][m]
+//   B[q][m]     = P_m(xi_q), Bd[q][m] = P_m'(xi_q) at the n Gauss-Legendre nodes xi_q
+//   Bk[k][q][m] = P_m^(k)(xi_q) (pointwise semi-norm at quadrature nodes, stage d)
+//   w[q]        Gauss weights on [-1,1]
+//   sigma[k]    weights of the pointwise semi-norm in reference derivatives:
+//               ||u||_x^2 = sum_{k != 0} sigma_k (d_ref^k u)^2  (eq. pointsnorm)
+//   R[i][j]     upper-triangular Cholesky factor of the element semi-norm Gram matrix
+//               on Legendre modes 1..ND-1: ||u||_e = |R c[1:]|     (eq. snorm)
+//   A[l][i][j]  R times the Taylor->Legendre map of corner l, on derivative orders
+//               1..ND-1: ||u*_vertex||_e-vector = A[l] t*[1:]       (Sec. 3.2 remark)
+//   tscale[k]   (2/dx)^kx (2/dy)^ky: reference -> physical derivative
+template <int DIM, int P>
+struct DgTables {
+  static constexpr int N = P + 1;
+  static constexpr int ND = DIM == 2 ? N * N : N;
+  static constexpr int NS = ND - 1;
+  static constexpr int NC = 1 << DIM;
+  float E[N][N];
+  float B[N][N];
+  float Bd[N][N];
+  float Bk[N][N][N];
+  float w[N];
+  float sigma[ND];
+  float tscale[ND];
+  float R[NS][NS];
+  float A[NC][NS][NS];
+};
+
+// Run-time arguments of one stage launch.
+struct StageArgs {
+  const float* u_in;   // state the residual is evaluated on
+  const float* u_n;    // RK: state at the start of the step (may alias u_out)
+  float* u_out;        // RK result or dudt
+  float* gamma_out;    // optional [ncell]
+  float* nu_out;       // optional [ncell]
+  float* alpha_out;    // optional [ncell][nvar][nq]
+  int32_t* troubled_out;          // optional [ncell]
+  const int32_t* troubled_override;  // optional [ncell]
+  float* tstar_out;    // optional [nvert][ND] (physical derivatives)
+  float* lambda_out;   // optional [ncell] wave speed lambda_e
+  int* status;         // device status word
+  int nx, ny;          // cells
+  int perx, pery;      // periodic flags
+  int vx;              // vertices per row (nx if periodic in x, nx+1 otherwise)
+  int mode;            // kMode* flags
+  float rk_a, rk_b, dt;  // u_out = rk_a u_n + rk_b (u_in + dt L(u_in))
+  float two_dx, two_dy;  // 2/dx, 2/dy
+  float nu_scale;        // h_e / (2p)
+  float eps, gamma_vertex, c_gamma, q, lambda_const;
+  int r;
+  int sc, sensor_mode;
+  float adv_vx, adv_vy;
+  float gas_gamma;
+};
+
+enum : int {
+  kModeResidual = 1,   // write dudt to u_out
+  kModeRK = 2,         // write rk_a u_n + rk_b (u_in + dt L) to u_out
+  kModeSensorOnly = 4, // stop after stage (c) (gamma, nu, lambda outputs)
+};
+
+}  // namespace cvw
+
+struct cvweno_mesh_s {
+  cvweno_mesh_desc desc;
+  int device;
+  int dim, p, n, nd, nvar, nq, ncorner;
+  int nx, ny, vx, vy;
+  int64_t ncell, nvert, nstate;
+  double dx, dy, h;
+  // host tables
+  int32_t* cell_vertices;  // [ncell][ncorner]
+  int32_t* vertex_cells;   // [nvert][ncorner]
+  int32_t* colour;         // [ncell]
+  // reference tabulations, one per (dim, p) -- only the matching one is filled
+  void* tables;            // host copy of DgTables<dim, p>
+  size_t tables_bytes;
+  // device scratch
+  float* d_u1;
+  float* d_u2;
+  float* d_lambda;         // [ncell]
+  double* d_red;           // reduction scratch
+  int* d_status;
+  int* h_status;           // pinned
+  double* h_red;           // pinned
+};
+
+namespace cvw {
+// tables.cpp
+cvweno_status build_tables(cvweno_mesh m);
+void gauss_rule(int n, double* x, double* w);         // Gauss-Legendre on [-1,1], ascending
+void legendre_values(double x, int mmax, double* out);  // P_0..P_mmax at x
+// dg_scalar.cu / dg_euler.cu
+cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
+}  // namespace cvw

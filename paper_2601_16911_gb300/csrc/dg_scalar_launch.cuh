@@ -1,0 +1,26 @@
+// Host-side launcher of the fused scalar stage kernel.
+#pragma once
+
+#include "dg_scalar_kernel.cuh"
+
+namespace cvw {
+
+template <int DIM, int P, int SYS, int TX, int TY>
+cudaError_t launch_scalar(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
+  using Tb = DgTables<DIM, P>;
+  constexpr int HX = TX + 2, HY = DIM == 2 ? TY + 2 : 1;
+  constexpr int VXT = TX + 1, VYT = DIM == 2 ? TY + 1 : 1;
+  constexpr size_t smem = sizeof(float) * Tb::ND * (size_t)(HX * HY + VXT * VYT);
+  static_assert(smem <= 200 * 1024, "tile too large for shared memory");
+  auto kern = dg_scalar_stage<DIM, P, SYS, TX, TY>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (m->tables_bytes != sizeof(Tb)) return cudaErrorInvalidValue;
+  dim3 grid((a.nx + TX - 1) / TX, DIM == 2 ? (a.ny + TY - 1) / TY : 1);
+  kern<<<grid, TX * TY, smem, s>>>(a, *static_cast<const Tb*>(m->tables));
+  return cudaGetLastError();
+}
+
+}  // namespace cvw

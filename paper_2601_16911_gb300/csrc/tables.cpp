@@ -1,0 +1,269 @@
+// Host-side construction of the mesh tables and reference-cell tabulations.
+//
+// All tabulations are computed in FP64 and rounded once to FP32.  The routes are the
+// library's own: Gauss-Legendre nodes and weights by the Golub-Welsch eigenproblem
+// of the Legendre Jacobi matrix (cyclic Jacobi rotations), Legendre derivatives by
+// the recurrence D^k P_{m+1} = D^k P_{m-1} + (2m+1) D^{k-1} P_m, the Taylor->Legendre
+// corner maps by exact quadrature of the Taylor monomials, and the element semi-norm
+// (eq. snorm) as a Gram matrix reduced by Cholesky factorisation.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "cvweno_internal.cuh"
+
+namespace cvw {
+namespace {
+
+// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi rotations.
+// a (n x n, row-major) is destroyed; eigenvalues to lam, eigenvectors as columns of v.
+void jacobi_eigen(int n, std::vector<double>& a, std::vector<double>& lam, std::vector<double>& v) {
+  v.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) v[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
+    if (off < 1e-300) break;
+    for (int pi = 0; pi < n; ++pi) {
+      for (int qi = pi + 1; qi < n; ++qi) {
+        double apq = a[pi * n + qi];
+        if (fabs(apq) < 1e-300) continue;
+        double theta = (a[qi * n + qi] - a[pi * n + pi]) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          double akp = a[k * n + pi], akq = a[k * n + qi];
+          a[k * n + pi] = c * akp - s * akq;
+          a[k * n + qi] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          double apk = a[pi * n + k], aqk = a[qi * n + k];
+          a[pi * n + k] = c * apk - s * aqk;
+          a[qi * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = v[k * n + pi], vkq = v[k * n + qi];
+          v[k * n + pi] = c * vkp - s * vkq;
+          v[k * n + qi] = s * vkp + c * vkq;
+        }
+      }
+    }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = a[i * n + i];
+}
+
+// Golub-Welsch: nodes = eigenvalues of the symmetric Jacobi matrix of the Legendre
+// recurrence, weights = 2 * (first eigenvector component)^2.  Ascending nodes.
+void gauss_golub_welsch(int n, double* x, double* w) {
+  std::vector<double> J(n * n, 0.0), lam, V;
+  for (int k = 1; k < n; ++k) {
+    double b = k / sqrt(4.0 * k * k - 1.0);
+    J[(k - 1) * n + k] = J[k * n + k - 1] = b;
+  }
+  jacobi_eigen(n, J, lam, V);
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (lam[idx[j]] < lam[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+  for (int i = 0; i < n; ++i) {
+    x[i] = lam[idx[i]];
+    double v0 = V[0 * n + idx[i]];
+    w[i] = 2.0 * v0 * v0;
+  }
+  // symmetrise (the rule is symmetric about 0)
+  for (int i = 0; i < n / 2; ++i) {
+    double xm = 0.5 * (x[n - 1 - i] - x[i]), wm = 0.5 * (w[i] + w[n - 1 - i]);
+    x[i] = -xm;
+    x[n - 1 - i] = xm;
+    w[i] = w[n - 1 - i] = wm;
+  }
+  if (n % 2) x[n / 2] = 0.0;
+}
+
+// D^k P_m(x) for m <= mmax, k <= kmax: out[k][m] (row stride mmax+1).
+void legendre_derivs(double x, int mmax, int kmax, double* out) {
+  int S = mmax + 1;
+  for (int k = 0; k <= kmax; ++k)
+    for (int m = 0; m <= mmax; ++m) out[k * S + m] = 0.0;
+  out[0] = 1.0;
+  if (mmax >= 1) out[1] = x;
+  for (int m = 1; m < mmax; ++m) out[m + 1] = ((2.0 * m + 1.0) * x * out[m] - m * out[m - 1]) / (m + 1.0);
+  for (int k = 1; k <= kmax; ++k) {
+    if (mmax >= 1) out[k * S + 1] = (k == 1) ? 1.0 : 0.0;
+    for (int m = 1; m < mmax; ++m)
+      out[k * S + m + 1] = out[k * S + m - 1] + (2.0 * m + 1.0) * out[(k - 1) * S + m];
+  }
+}
+
+double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+
+template <int DIM, int P>
+cvweno_status fill(cvweno_mesh m) {
+  using T = DgTables<DIM, P>;
+  constexpr int N = T::N, ND = T::ND, NS = T::NS, NC = T::NC;
+  T* t = (T*)calloc(1, sizeof(T));
+  if (!t) return CVWENO_ERR_NOMEM;
+  const double dx = m->dx, dy = m->dy, h = m->h;
+  double gx[N], gw[N];
+  gauss_golub_welsch(N, gx, gw);
+  double tab[N * N];
+  // E at +1
+  legendre_derivs(1.0, P, P, tab);
+  for (int k = 0; k < N; ++k)
+    for (int mm = 0; mm < N; ++mm) t->E[k][mm] = (float)tab[k * N + mm];
+  for (int q = 0; q < N; ++q) {
+    legendre_derivs(gx[q], P, P, tab);
+    for (int mm = 0; mm < N; ++mm) {
+      t->B[q][mm] = (float)tab[mm];
+      t->Bd[q][mm] = (float)tab[N + mm];
+      for (int k = 0; k < N; ++k) t->Bk[k][q][mm] = (float)tab[k * N + mm];
+    }
+    t->w[q] = (float)gw[q];
+  }
+  // pointwise semi-norm weights and reference->physical scales
+  for (int k = 0; k < ND; ++k) {
+    int kx = k % N, ky = DIM == 2 ? k / N : 0;
+    double sx = pow(2.0 * h / dx, 2 * kx), sy = DIM == 2 ? pow(2.0 * h / dy, 2 * ky) : 1.0;
+    t->sigma[k] = (k == 0) ? 0.0f : (float)(sx * sy);
+    t->tscale[k] = (float)(pow(2.0 / dx, kx) * (DIM == 2 ? pow(2.0 / dy, ky) : 1.0));
+  }
+  // 1D Gram blocks g_k[a][b] = int_{-1}^{1} D^k P_a D^k P_b, by an 8-point rule (exact)
+  const int NG = 8;
+  double qx[NG], qw[NG];
+  gauss_golub_welsch(NG, qx, qw);
+  std::vector<double> g((size_t)N * N * N, 0.0);  // [k][a][b]
+  double tq[N * N];
+  for (int q = 0; q < NG; ++q) {
+    legendre_derivs(qx[q], P, P, tq);
+    for (int k = 0; k < N; ++k)
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) g[(k * N + a) * N + b] += qw[q] * tq[k * N + a] * tq[k * N + b];
+  }
+  // element semi-norm Gram matrix on modes (eq. snorm), physical scaling folded in
+  const double jac = DIM == 2 ? 0.25 * dx * dy : 0.5 * dx;
+  std::vector<double> G((size_t)ND * ND, 0.0);
+  for (int k = 1; k < ND; ++k) {
+    int kx = k % N, ky = DIM == 2 ? k / N : 0;
+    double rho = pow(h, 2 * (kx + ky) - DIM) * pow(2.0 / dx, 2 * kx) * (DIM == 2 ? pow(2.0 / dy, 2 * ky) : 1.0) * jac;
+    for (int a = 0; a < ND; ++a)
+      for (int b = 0; b < ND; ++b) {
+        int ax = a % N, ay = DIM == 2 ? a / N : 0, bx = b % N, by = DIM == 2 ? b / N : 0;
+        double v = g[(kx * N + ax) * N + bx];
+        if (DIM == 2) v *= g[(ky * N + ay) * N + by];
+        G[a * ND + b] += rho * v;
+      }
+  }
+  // Cholesky G[1:,1:] = R^T R, R upper triangular
+  std::vector<double> R((size_t)NS * NS, 0.0);
+  for (int j = 0; j < NS; ++j) {
+    double s = G[(j + 1) * ND + (j + 1)];
+    for (int k = 0; k < j; ++k) s -= R[k * NS + j] * R[k * NS + j];
+    if (!(s > 0.0)) { free(t); return CVWENO_ERR_ARG; }
+    R[j * NS + j] = sqrt(s);
+    for (int i = j + 1; i < NS; ++i) {
+      double v = G[(j + 1) * ND + (i + 1)];
+      for (int k = 0; k < j; ++k) v -= R[k * NS + j] * R[k * NS + i];
+      R[j * NS + i] = v / R[j * NS + j];
+    }
+  }
+  for (int i = 0; i < NS; ++i)
+    for (int j = 0; j < NS; ++j) t->R[i][j] = (float)R[i * NS + j];
+  // Taylor->Legendre at corner s = -1, +1:  Gs[m][k] = (2m+1)/2 int P_m (xi - s)^k / k!
+  double Gs[2][N][N];
+  for (int si = 0; si < 2; ++si) {
+    double s = si ? 1.0 : -1.0;
+    for (int a = 0; a < N; ++a)
+      for (int k = 0; k < N; ++k) {
+        double acc = 0.0;
+        for (int q = 0; q < NG; ++q) {
+          legendre_derivs(qx[q], P, 0, tq);
+          acc += qw[q] * tq[a] * pow(qx[q] - s, k) / factorial(k);
+        }
+        Gs[si][a][k] = 0.5 * (2 * a + 1) * acc;
+      }
+  }
+  for (int l = 0; l < NC; ++l) {
+    int sxi = l & 1, syi = (l >> 1) & 1;
+    // C[a][k] for a, k in 1..ND-1, then A = R C
+    std::vector<double> C((size_t)NS * NS);
+    for (int a = 1; a < ND; ++a)
+      for (int k = 1; k < ND; ++k) {
+        int ax = a % N, ay = DIM == 2 ? a / N : 0, kx = k % N, ky = DIM == 2 ? k / N : 0;
+        double v = Gs[sxi][ax][kx];
+        if (DIM == 2) v *= Gs[syi][ay][ky];
+        C[(a - 1) * NS + (k - 1)] = v;
+      }
+    for (int i = 0; i < NS; ++i)
+      for (int j = 0; j < NS; ++j) {
+        double acc = 0.0;
+        for (int k = i; k < NS; ++k) acc += R[i * NS + k] * C[k * NS + j];
+        t->A[l][i][j] = (float)acc;
+      }
+  }
+  m->tables = t;
+  m->tables_bytes = sizeof(T);
+  return CVWENO_OK;
+}
+
+}  // namespace
+
+void gauss_rule(int n, double* x, double* w) { gauss_golub_welsch(n, x, w); }
+
+void legendre_values(double x, int mmax, double* out) { legendre_derivs(x, mmax, 0, out); }
+
+cvweno_status build_tables(cvweno_mesh m) {
+  // integer mesh tables
+  const int nx = m->nx, ny = m->ny, nc = m->ncorner;
+  const int perx = m->desc.bc[0] == CVWENO_PERIODIC, pery = m->dim == 2 && m->desc.bc[2] == CVWENO_PERIODIC;
+  m->cell_vertices = (int32_t*)malloc(sizeof(int32_t) * m->ncell * nc);
+  m->vertex_cells = (int32_t*)malloc(sizeof(int32_t) * m->nvert * nc);
+  m->colour = (int32_t*)malloc(sizeof(int32_t) * m->ncell);
+  if (!m->cell_vertices || !m->vertex_cells || !m->colour) return CVWENO_ERR_NOMEM;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      int64_t e = i + (int64_t)nx * j;
+      for (int c = 0; c < nc; ++c) {
+        int I = i + (c & 1), J = j + ((c >> 1) & 1);
+        if (perx && I == nx) I = 0;
+        if (pery && J == ny) J = 0;
+        m->cell_vertices[e * nc + c] = (int32_t)(I + (int64_t)m->vx * J);
+      }
+      int cx = (perx && (nx & 1) && i == nx - 1) ? 2 : (i & 1);
+      int cy = m->dim == 2 ? ((pery && (ny & 1) && j == ny - 1) ? 2 : (j & 1)) : 0;
+      m->colour[e] = cx + 3 * cy;
+    }
+  for (int J = 0; J < m->vy; ++J)
+    for (int I = 0; I < m->vx; ++I) {
+      int64_t v = I + (int64_t)m->vx * J;
+      for (int s = 0; s < nc; ++s) {
+        int ci = I - 1 + (s & 1), cj = m->dim == 2 ? J - 1 + ((s >> 1) & 1) : 0;
+        if (perx) ci = (ci + nx) % nx;
+        if (pery) cj = (cj + ny) % ny;
+        bool ok = ci >= 0 && ci < nx && cj >= 0 && cj < ny;
+        m->vertex_cells[v * nc + s] = ok ? (int32_t)(ci + (int64_t)nx * cj) : -1;
+      }
+    }
+  // reference tabulations
+  switch (m->dim * 10 + m->p) {
+    case 11: return fill<1, 1>(m);
+    case 12: return fill<1, 2>(m);
+    case 13: return fill<1, 3>(m);
+    case 14: return fill<1, 4>(m);
+    case 21: return fill<2, 1>(m);
+    case 22: return fill<2, 2>(m);
+    case 23: return fill<2, 3>(m);
+    case 24: return fill<2, 4>(m);
+    default: return CVWENO_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace cvw

@@ -1,0 +1,325 @@
+"""Thin ctypes binding of the CUDA library (``include/cvweno.h``).
+
+Argument marshalling only: every function below calls the C entry point of the same
+name; all arithmetic runs in the library's sm_103a kernels.  Device arrays are torch
+CUDA tensors (their data pointers are passed), streams are torch CUDA streams (the
+current stream by default).  There is no CPU fallback: ``load()`` raises when the
+library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_POSITIVITY, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM = range(8)
+DG, CG = 0, 1
+PERIODIC, TRANSMISSIVE = 0, 1
+BURGERS, KPP, LINADV, EULER = 0, 1, 2, 3
+SENSOR_COMPUTED, SENSOR_SMOOTH, SENSOR_TROUBLED = 0, 1, 2
+
+
+class CvwenoError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = load().cvweno_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+class cvweno_params(ctypes.Structure):
+    _fields_ = [
+        ("eps", ctypes.c_double), ("r", ctypes.c_double), ("q", ctypes.c_double),
+        ("gamma_vertex", ctypes.c_double), ("c_gamma", ctypes.c_double),
+        ("sc_quadrature", ctypes.c_int), ("sensor_mode", ctypes.c_int),
+        ("lambda_const", ctypes.c_double), ("gas_gamma", ctypes.c_double),
+        ("adv_vx", ctypes.c_double), ("adv_vy", ctypes.c_double),
+    ]
+
+
+class cvweno_mesh_desc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("degree", ctypes.c_int),
+        ("kind", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int * 4),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("params", cvweno_params),
+    ]
+
+
+_VP = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_IP = ctypes.POINTER(ctypes.c_int)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_DP = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    "cvweno_default_params": (None, [ctypes.POINTER(cvweno_params)]),
+    "cvweno_mesh_create": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), ctypes.POINTER(_VP)]),
+    "cvweno_mesh_destroy": (ctypes.c_int, [_VP]),
+    "cvweno_mesh_info": (ctypes.c_int, [_VP, _I64P, _I64P, _IP, _I64P, _IP]),
+    "cvweno_mesh_tables": (ctypes.c_int, [_VP, _I32P, _I32P, _I32P]),
+    "cvweno_project": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _VP, _VP]),
+    "cvweno_vertex_data": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "cvweno_sensor": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "cvweno_residual_ex": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "cvweno_residual": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "cvweno_step": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double, _DP, _VP]),
+    "cvweno_advance": (ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_int, _VP]),
+    "cvweno_mass_total": (ctypes.c_int, [_VP, _VP, _DP, _VP]),
+    "cvweno_max_wavespeed": (ctypes.c_int, [_VP, _VP, _DP, _VP]),
+    "cvweno_status_check": (ctypes.c_int, [_VP, _VP]),
+    "cvweno_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libcvweno.so (optionally building it first).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if build_if_missing and _build.is_stale():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is not built; run paper_2601_16911_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(code, where):
+    if code != OK:
+        raise CvwenoError(code, where)
+
+
+def default_params() -> cvweno_params:
+    p = cvweno_params()
+    load().cvweno_default_params(ctypes.byref(p))
+    return p
+
+
+def make_desc(d: dict) -> cvweno_mesh_desc:
+    """Build the C mesh description from a problem dict (see inputs.mesh)."""
+    c = cvweno_mesh_desc()
+    c.dim, c.nx, c.ny, c.degree = int(d["dim"]), int(d["nx"]), int(d.get("ny", 1)), int(d["degree"])
+    c.kind, c.system = int(d.get("kind", DG)), int(d["system"])
+    for i in range(4):
+        c.bc[i] = int(d["bc"][i])
+    c.x0, c.x1, c.y0, c.y1 = float(d["x0"]), float(d["x1"]), float(d.get("y0", 0.0)), float(d.get("y1", 1.0))
+    p = default_params()
+    for f, _ in cvweno_params._fields_:
+        if f in d:
+            setattr(p, f, type(getattr(p, f))(d[f]))
+    c.params = p
+    return c
+
+
+class Mesh:
+    """Owning handle of a cvweno_mesh; methods mirror the C entry points."""
+
+    def __init__(self, d: dict):
+        lib = load()
+        self.desc = dict(d)
+        self._h = _VP()
+        _check(lib.cvweno_mesh_create(ctypes.byref(make_desc(d)), ctypes.byref(self._h)), "cvweno_mesh_create")
+        nc, nd, nverts = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        nv, nq = ctypes.c_int(), ctypes.c_int()
+        _check(lib.cvweno_mesh_info(self._h, ctypes.byref(nc), ctypes.byref(nd), ctypes.byref(nv),
+                                    ctypes.byref(nverts), ctypes.byref(nq)), "cvweno_mesh_info")
+        self.ncells, self.ndof, self.nvars, self.nverts, self.nquad = nc.value, nd.value, nv.value, nverts.value, nq.value
+        self.state_shape = (self.nvars, self.ncells, self.ndof)
+
+    def close(self):
+        if self._h:
+            load().cvweno_mesh_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def empty_state(self, device="cuda"):
+        return torch.empty(self.state_shape, dtype=torch.float32, device=device)
+
+    def tables(self):
+        import numpy as np
+        ncorner = 4 if self.desc["dim"] == 2 else 2
+        cv = np.zeros((self.ncells, ncorner), np.int32)
+        vc = np.zeros((self.nverts, ncorner), np.int32)
+        col = np.zeros(self.ncells, np.int32)
+        _check(load().cvweno_mesh_tables(self._h, cv.ctypes.data_as(_I32P), vc.ctypes.data_as(_I32P),
+                                         col.ctypes.data_as(_I32P)), "cvweno_mesh_tables")
+        return cv, vc, col
+
+    def project(self, ic_type: int, params, out=None, stream=None):
+        prm = (ctypes.c_double * 64)()
+        for i, v in enumerate(params):
+            prm[i] = float(v)
+        u = out if out is not None else self.empty_state()
+        _check(load().cvweno_project(self._h, int(ic_type), prm, _ptr(u), _stream(stream)), "cvweno_project")
+        return u
+
+    def vertex_data(self, u, stream=None):
+        ts = torch.empty((self.nverts, self.ndof), dtype=torch.float32, device=u.device)
+        _check(load().cvweno_vertex_data(self._h, _ptr(u), _ptr(ts), _stream(stream)), "cvweno_vertex_data")
+        return ts
+
+    def sensor(self, u, stream=None):
+        g = torch.empty(self.ncells, dtype=torch.float32, device=u.device)
+        nu = torch.empty_like(g)
+        _check(load().cvweno_sensor(self._h, _ptr(u), _ptr(g), _ptr(nu), _stream(stream)), "cvweno_sensor")
+        return g, nu
+
+    def residual(self, u, out=None, stream=None):
+        r = out if out is not None else torch.empty_like(u)
+        _check(load().cvweno_residual(self._h, _ptr(u), _ptr(r), _stream(stream)), "cvweno_residual")
+        return r
+
+    def residual_ex(self, u, troubled_override=None, stream=None):
+        dev = u.device
+        out = dict(
+            dudt=torch.empty_like(u),
+            gamma=torch.empty(self.ncells, dtype=torch.float32, device=dev),
+            nu=torch.empty(self.ncells, dtype=torch.float32, device=dev),
+            alpha=torch.empty((self.ncells, self.nvars, self.nquad), dtype=torch.float32, device=dev),
+            troubled=torch.empty(self.ncells, dtype=torch.int32, device=dev),
+        )
+        _check(load().cvweno_residual_ex(self._h, _ptr(u), _ptr(troubled_override), _ptr(out["dudt"]),
+                                         _ptr(out["gamma"]), _ptr(out["nu"]), _ptr(out["alpha"]),
+                                         _ptr(out["troubled"]), _stream(stream)), "cvweno_residual_ex")
+        return out
+
+    def step(self, u, dt: float = 0.0, cfl: float = 0.0, stream=None) -> float:
+        used = ctypes.c_double()
+        _check(load().cvweno_step(self._h, _ptr(u), float(dt), float(cfl), ctypes.byref(used), _stream(stream)),
+               "cvweno_step")
+        return used.value
+
+    def advance(self, u, dt: float, nsteps: int, stream=None):
+        _check(load().cvweno_advance(self._h, _ptr(u), float(dt), int(nsteps), _stream(stream)), "cvweno_advance")
+
+    def mass_total(self, u, stream=None):
+        t = (ctypes.c_double * self.nvars)()
+        _check(load().cvweno_mass_total(self._h, _ptr(u), t, _stream(stream)), "cvweno_mass_total")
+        return [t[i] for i in range(self.nvars)]
+
+    def max_wavespeed(self, u, stream=None) -> float:
+        lam = ctypes.c_double()
+        _check(load().cvweno_max_wavespeed(self._h, _ptr(u), ctypes.byref(lam), _stream(stream)),
+               "cvweno_max_wavespeed")
+        return lam.value
+
+    def status_check(self, stream=None):
+        _check(load().cvweno_status_check(self._h, _stream(stream)), "cvweno_status_check")
+
+
+# ---- the C entry points under their own names (argument marshalling only) ----------------
+
+def _h(mesh):
+    return mesh.handle if isinstance(mesh, Mesh) else mesh
+
+
+def cvweno_mesh_create(desc: dict) -> Mesh:
+    return Mesh(desc)
+
+
+def cvweno_mesh_destroy(mesh: Mesh):
+    mesh.close()
+
+
+def cvweno_mesh_info(mesh: Mesh) -> dict:
+    return dict(ncells=mesh.ncells, ndof_per_var=mesh.ndof, nvars=mesh.nvars, nverts=mesh.nverts, nquad=mesh.nquad)
+
+
+def cvweno_mesh_tables(mesh: Mesh):
+    return mesh.tables()
+
+
+def cvweno_project(mesh: Mesh, ic_type: int, params, u, stream=None):
+    return mesh.project(ic_type, params, out=u, stream=stream)
+
+
+def cvweno_vertex_data(mesh: Mesh, u, tstar, stream=None):
+    _check(load().cvweno_vertex_data(_h(mesh), _ptr(u), _ptr(tstar), _stream(stream)), "cvweno_vertex_data")
+
+
+def cvweno_sensor(mesh: Mesh, u, gamma, nu, stream=None):
+    _check(load().cvweno_sensor(_h(mesh), _ptr(u), _ptr(gamma), _ptr(nu), _stream(stream)), "cvweno_sensor")
+
+
+def cvweno_residual_ex(mesh: Mesh, u, troubled_override, dudt, gamma=None, nu=None, alpha=None, troubled=None,
+                       stream=None):
+    _check(load().cvweno_residual_ex(_h(mesh), _ptr(u), _ptr(troubled_override), _ptr(dudt), _ptr(gamma), _ptr(nu),
+                                     _ptr(alpha), _ptr(troubled), _stream(stream)), "cvweno_residual_ex")
+
+
+def cvweno_residual(mesh: Mesh, u, dudt, stream=None):
+    _check(load().cvweno_residual(_h(mesh), _ptr(u), _ptr(dudt), _stream(stream)), "cvweno_residual")
+
+
+def cvweno_step(mesh: Mesh, u, dt: float = 0.0, cfl: float = 0.0, stream=None) -> float:
+    return mesh.step(u, dt, cfl, stream)
+
+
+def cvweno_advance(mesh: Mesh, u, dt: float, nsteps: int, stream=None):
+    mesh.advance(u, dt, nsteps, stream)
+
+
+def cvweno_mass_total(mesh: Mesh, u, stream=None):
+    return mesh.mass_total(u, stream)
+
+
+def cvweno_max_wavespeed(mesh: Mesh, u, stream=None) -> float:
+    return mesh.max_wavespeed(u, stream)
+
+
+def cvweno_status_check(mesh: Mesh, stream=None):
+    mesh.status_check(stream)
+
+
+def cvweno_status_string(code: int) -> str:
+    return load().cvweno_status_string(int(code)).decode()
+
+
+def cvweno_default_params() -> cvweno_params:
+    return default_params()
