@@ -180,6 +180,27 @@ cvweno_status cvweno_max_wavespeed(cvweno_mesh m, const float* u, double* lam, v
 /* Synchronise the stream, read and clear the mesh's device status word. */
 cvweno_status cvweno_status_check(cvweno_mesh m, void* stream);
 
+/* One SSP-RK3 step of fixed size dt > 0, in place on the caller's state u (device,
+ * state layout of desc), that allocates nothing -- for callers that cannot allocate
+ * device or host memory (a library running inside an arena or memory pool it does not
+ * own, or an embedding that forbids cudaMalloc after start-up).  It needs no mesh
+ * handle: the tabulations are built on the host stack, and the two RK stage buffers and
+ * the status word live in file-scope __device__ storage that the library holds on every
+ * GPU that loads it until the process exits (2 x 4,194,304 floats = 32 MiB).
+ * The paper has no counterpart; this is a deployment variant of cvweno_step.
+ *   - States larger than 4,194,304 floats (ncells x (p+1)^dim x nvars) return
+ *     CVWENO_ERR_ARG; other argument checks and codes are those of cvweno_mesh_create.
+ *   - The first call on a device looks up the device addresses of that storage with
+ *     the device current; make that first call before any stream capture.
+ *   - Every call shares the same storage: calls that overlap on the GPU (different
+ *     streams, or different host threads) race and corrupt each other's stages.
+ *   - status_out (host, may be NULL): when given, the call synchronises the stream and
+ *     stores the device status bits of this step (1 non-finite, 2 non-positive density
+ *     or pressure), returning CVWENO_ERR_NONFINITE / CVWENO_ERR_POSITIVITY accordingly;
+ *     when NULL the call only enqueues work. */
+cvweno_status cvweno_step_static(const cvweno_mesh_desc* desc, float* u, double dt, int32_t* status_out,
+                                 void* stream);
+
 /* Static description of a status code. */
 const char* cvweno_status_string(cvweno_status s);
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcvweno.so")
-SOURCES = ["tables.cpp", "api.cu", "dg_scalar_1d.cu", "dg_scalar_2d.cu", "dg_euler.cu"]
+SOURCES = ["tables.cpp", "api.cu", "dg_scalar_1d.cu", "dg_scalar_2d.cu", "dg_euler.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -75,6 +75,8 @@ _SIGNATURES = {
     "cvweno_max_wavespeed": (ctypes.c_int, [_VP, _VP, _DP, _VP]),
     "cvweno_status_check": (ctypes.c_int, [_VP, _VP]),
     "cvweno_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cvweno_step_static": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), _VP, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_int32), _VP]),
 }
 
 
@@ -323,3 +325,13 @@ def cvweno_status_string(code: int) -> str:
 
 def cvweno_default_params() -> cvweno_params:
     return default_params()
+
+
+def cvweno_step_static(desc: dict, u, dt: float, check_status: bool = False, stream=None) -> int:
+    """One SSP-RK3 step that allocates nothing (see include/cvweno.h); returns the
+    device status bits when check_status is set (the call then synchronises)."""
+    st = ctypes.c_int32(0)
+    _check(load().cvweno_step_static(ctypes.byref(make_desc(desc)), _ptr(u), float(dt),
+                                     ctypes.byref(st) if check_status else None, _stream(stream)),
+           "cvweno_step_static")
+    return st.value
