@@ -49,6 +49,15 @@
  *   A18 candidates are not mean-corrected (the sensor uses derivatives only).
  *   A20 Euler: gamma_e and alpha~_q from the density; f_q per conserved variable,
  *       so each variable's dissipation rate is preserved.
+ *   A12 CG mass: lumped (row-sum) mass and two defect-correction sweeps
+ *       du <- du + ML^{-1}(r - M_C du).
+ *   A13 CG P_h: lumped-mass L2 projection (P_h g)_j = sum_e int phi_j g / sum_e int phi_j.
+ *   A24 CG SC weights: f_q = |grad u|^2 - gamma_e grad u . P_h grad u can be negative;
+ *       alpha_q = 1 unless sum w f > 0 and sum w alpha~ f > 0.
+ *   A25 CG initial data: interpolation at the GLL nodes (periodic meshes only).
+ * CG is parity-unpinned against the paper's exact values (A12, A13 are readings); its
+ * pins are conservation, the sweeps' convergence to the consistent-mass solve, the
+ * shared sensor's pins and the design order / Table bur2 magnitudes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -154,6 +163,52 @@ static void or_gauss(int n, double* x, double* w) {
   }
 }
 
+/* Gauss-Lobatto-Legendre nodes (ascending; the endpoints and the roots of P_p') and
+ * weights 2 / (p (p+1) P_p(x)^2), by Newton iteration on P_p'. */
+static void or_gll(int p, double* x, double* w) {
+  x[0] = -1.0;
+  x[p] = 1.0;
+  for (int i = 1; i < p; ++i) {
+    double z = -cos(M_PI * i / p);
+    for (int it = 0; it < 200; ++it) {
+      double dz = or_leg_dk(p, 1, z) / or_leg_dk(p, 2, z);
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+  }
+  for (int i = 0; i <= p; ++i) {
+    double P = or_leg_dk(p, 0, x[i]);
+    w[i] = 2.0 / (p * (p + 1.0) * P * P);
+  }
+}
+
+/* monomial coefficients of the Lagrange polynomials on the nodes x[0..p], by
+ * multiplying out prod_{b != a} (xi - x_b) / (x_a - x_b) */
+static void or_lagrange_monomials(int p, const double* x, double lag[OR_MAXN][OR_MAXN]) {
+  for (int a = 0; a <= p; ++a) {
+    double c[OR_MAXN + 1] = {0};
+    c[0] = 1.0;
+    int deg = 0;
+    double den = 1.0;
+    for (int b = 0; b <= p; ++b) {
+      if (b == a) continue;
+      for (int e = deg + 1; e >= 1; --e) c[e] = c[e - 1] - x[b] * c[e];
+      c[0] = -x[b] * c[0];
+      ++deg;
+      den *= x[a] - x[b];
+    }
+    for (int e = 0; e <= p; ++e) lag[a][e] = c[e] / den;
+  }
+}
+
+/* k-th derivative of Lagrange polynomial a at xi */
+static double or_lag_dk(const double lag[OR_MAXN][OR_MAXN], int p, int a, int k, double xi) {
+  double s = 0.0;
+  for (int e = k; e <= p; ++e) s += lag[a][e] * or_fact(e) / or_fact(e - k) * or_ipow(xi, e - k);
+  return s;
+}
+
 /* ------------------------------------------------------------------------- */
 /* mesh: geometry, Gauss rule and geometric vertex patches                    */
 /* ------------------------------------------------------------------------- */
@@ -166,6 +221,10 @@ typedef struct {
   int nvert;
   int *vcount, *vcell, *vcorner; /* [nvert][4] */
   int* cvert;                     /* [ncell][ncorner] */
+  /* CG: GLL nodes and the monomial coefficients of their Lagrange polynomials */
+  int kind, nnx, nny, nnode;
+  double gll[OR_MAXN], gllw[OR_MAXN];
+  double lag[OR_MAXN][OR_MAXN]; /* lag[a][e]: coefficient of xi^e in l_a(xi) */
 } or_mesh;
 
 typedef struct {
@@ -199,7 +258,10 @@ static int or_mesh_init(const or_desc* d, or_mesh* m) {
   if (d->dim != 1 && d->dim != 2) return OR_ERR_ARG;
   if (d->degree < 1 || d->degree > OR_MAXP) return OR_ERR_UNSUPPORTED;
   if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return OR_ERR_ARG;
-  if (d->kind != OR_DG) return OR_ERR_UNSUPPORTED;
+  if (d->kind != OR_DG && d->kind != OR_CG) return OR_ERR_UNSUPPORTED;
+  if (d->kind == OR_CG && (d->system == OR_EULER || d->bc[0] != OR_PERIODIC ||
+                           (d->dim == 2 && d->bc[2] != OR_PERIODIC)))
+    return OR_ERR_UNSUPPORTED;
   if (d->system == OR_EULER && d->dim != 2) return OR_ERR_UNSUPPORTED;
   if (d->system == OR_KPP && d->dim != 2) return OR_ERR_UNSUPPORTED;
   if ((d->bc[0] == OR_PERIODIC) != (d->bc[1] == OR_PERIODIC)) return OR_ERR_ARG;
@@ -220,6 +282,14 @@ static int or_mesh_init(const or_desc* d, or_mesh* m) {
   m->h = d->dim == 2 ? sqrt(m->dx * m->dx + m->dy * m->dy) : m->dx;
   m->jac = d->dim == 2 ? 0.25 * m->dx * m->dy : 0.5 * m->dx;
   or_gauss(m->n, m->gx, m->gw);
+  m->kind = d->kind;
+  if (d->kind == OR_CG) {
+    m->nnx = m->p * m->nx;
+    m->nny = d->dim == 2 ? m->p * m->ny : 1;
+    m->nnode = m->nnx * m->nny;
+    or_gll(m->p, m->gll, m->gllw);
+    or_lagrange_monomials(m->p, m->gll, m->lag);
+  }
 
   /* geometric search: every cell corner becomes a record at its physical position
    * (periodic sides identified); records at the same position form one patch. */
@@ -274,9 +344,30 @@ static int or_mesh_init(const or_desc* d, or_mesh* m) {
 /* D^k phi_m at reference point (xi, eta) in physical units. */
 static double or_dphi(const or_mesh* m, int mi, int kx, int ky, double xi, double eta) {
   int mx = mi % m->n, my = mi / m->n;
+  if (m->kind == OR_CG) { /* GLL-node Lagrange basis, local node (mx, my) */
+    double v = or_ipow(2.0 / m->dx, kx) * or_lag_dk(m->lag, m->p, mx, kx, xi);
+    if (m->dim == 2) v *= or_ipow(2.0 / m->dy, ky) * or_lag_dk(m->lag, m->p, my, ky, eta);
+    return v;
+  }
   double v = or_ipow(2.0 / m->dx, kx) * or_leg_dk(mx, kx, xi);
   if (m->dim == 2) v *= or_ipow(2.0 / m->dy, ky) * or_leg_dk(my, ky, eta);
   return v;
+}
+
+/* CG: global node of local node (a, b) of cell e (periodic lattice of p nx x p ny) */
+static int or_cg_node(const or_mesh* m, int e, int a, int b) {
+  int i = e % m->nx, j = e / m->nx;
+  int I = (m->p * i + a) % m->nnx, J = m->dim == 2 ? (m->p * j + b) % m->nny : 0;
+  return I + m->nnx * J;
+}
+
+/* CG: cell-local copies uc[var][cell][a + n b] of the nodal state u[var][node] */
+static void or_cg_gather(const or_mesh* m, const double* u, double* uc) {
+  for (int v = 0; v < m->nvar; ++v)
+    for (int e = 0; e < m->ncell; ++e)
+      for (int mi = 0; mi < m->nd; ++mi)
+        uc[((size_t)v * m->ncell + e) * m->nd + mi] =
+            u[(size_t)v * m->nnode + or_cg_node(m, e, mi % m->n, mi / m->n)];
 }
 
 /* D^k u^e at (xi, eta) for one variable's coefficient block c[nd]. */
@@ -711,9 +802,175 @@ static int or_residual_m(const or_mesh* m, const double* u, const double* gamma,
   return OR_OK;
 }
 
+
+/* ------------------------------------------------------------------------- */
+/* CG variant (Sec. 2.2 CG remark; readings A12, A13, A24)                    */
+/* ------------------------------------------------------------------------- */
+
+/* Lumped mass ML_j = sum_e int phi_j (Gauss rule, exact). */
+static void or_cg_lumped_mass(const or_mesh* m, double* ML) {
+  for (int j = 0; j < m->nnode; ++j) ML[j] = 0.0;
+  for (int e = 0; e < m->ncell; ++e)
+    for (int mi = 0; mi < m->nd; ++mi) {
+      double s = 0.0;
+      for (int qi = 0; qi < m->nq; ++qi) {
+        double xi, eta, W;
+        or_qpoint(m, qi, &xi, &eta, &W);
+        s += W * or_dphi(m, mi, 0, 0, xi, eta);
+      }
+      ML[or_cg_node(m, e, mi % m->n, mi / m->n)] += s;
+    }
+}
+
+/* y = M_C x with the consistent mass M_C,ij = sum_e int phi_i phi_j (Gauss rule). */
+static void or_cg_consistent_mass(const or_mesh* m, const double* x, double* y) {
+  for (int j = 0; j < m->nnode; ++j) y[j] = 0.0;
+  for (int e = 0; e < m->ncell; ++e)
+    for (int qi = 0; qi < m->nq; ++qi) {
+      double xi, eta, W;
+      or_qpoint(m, qi, &xi, &eta, &W);
+      double xq = 0.0;
+      for (int mj = 0; mj < m->nd; ++mj) xq += x[or_cg_node(m, e, mj % m->n, mj / m->n)] * or_dphi(m, mj, 0, 0, xi, eta);
+      for (int mi = 0; mi < m->nd; ++mi)
+        y[or_cg_node(m, e, mi % m->n, mi / m->n)] += W * or_dphi(m, mi, 0, 0, xi, eta) * xq;
+    }
+}
+
+/* CG stage: P_h grad u by the lumped-mass L2 projection (A13), the SC weights with
+ * f_q = |grad u|^2 - gamma_e grad u . P_h grad u (Sec. 4; A24: alpha = 1 unless both
+ * sums are positive), the residual
+ *   r_j = sum_e int grad phi_j . f(u) - nu_e sum_q alpha_q w_q grad phi_j . (grad u - gamma_e P_h grad u)
+ * (Sec. 2.2, CG form of eq. stab) and dudt = M^{-1} r by the lumped mass and two
+ * defect-correction sweeps (A12). */
+static int or_cg_residual_m(const or_mesh* m, const double* uc, const double* gamma, const double* nu,
+                            const double* norm0, const int* override_troubled, double* alpha, int* troubled,
+                            double* dudt) {
+  const or_desc* d = &m->d;
+  int nq = m->nq, nd = m->nd, nn = m->nnode;
+  double* ML = (double*)malloc(sizeof(double) * nn);
+  double* Ph = (double*)calloc((size_t)2 * nn, sizeof(double));
+  double* r = (double*)calloc(nn, sizeof(double));
+  double* tmp = (double*)malloc(sizeof(double) * nn);
+  if (!ML || !Ph || !r || !tmp) { free(ML); free(Ph); free(r); free(tmp); return OR_ERR_NOMEM; }
+  or_cg_lumped_mass(m, ML);
+  /* P_h grad u: (sum_e int phi_j d_c u) / ML_j */
+  for (int e = 0; e < m->ncell; ++e) {
+    const double* c = uc + (size_t)e * nd;
+    for (int qi = 0; qi < nq; ++qi) {
+      double xi, eta, W;
+      or_qpoint(m, qi, &xi, &eta, &W);
+      double gx = or_du(m, c, 1, 0, xi, eta), gy = m->dim == 2 ? or_du(m, c, 0, 1, xi, eta) : 0.0;
+      for (int mi = 0; mi < nd; ++mi) {
+        int jn = or_cg_node(m, e, mi % m->n, mi / m->n);
+        double ph = or_dphi(m, mi, 0, 0, xi, eta);
+        Ph[jn] += W * ph * gx;
+        Ph[nn + jn] += W * ph * gy;
+      }
+    }
+  }
+  for (int j = 0; j < nn; ++j) { Ph[j] /= ML[j]; Ph[nn + j] /= ML[j]; }
+  for (int e = 0; e < m->ncell; ++e) {
+    const double* c = uc + (size_t)e * nd;
+    double gxq[OR_MAXND], gyq[OR_MAXND], pxq[OR_MAXND], pyq[OR_MAXND], Wq[OR_MAXND];
+    for (int qi = 0; qi < nq; ++qi) {
+      double xi, eta;
+      or_qpoint(m, qi, &xi, &eta, &Wq[qi]);
+      gxq[qi] = or_du(m, c, 1, 0, xi, eta);
+      gyq[qi] = m->dim == 2 ? or_du(m, c, 0, 1, xi, eta) : 0.0;
+      pxq[qi] = pyq[qi] = 0.0;
+      for (int mj = 0; mj < nd; ++mj) {
+        int jn = or_cg_node(m, e, mj % m->n, mj / m->n);
+        double ph = or_dphi(m, mj, 0, 0, xi, eta);
+        pxq[qi] += Ph[jn] * ph;
+        pyq[qi] += Ph[nn + jn] * ph;
+      }
+    }
+    /* stage (d) */
+    int tr = d->sc_quadrature && gamma[e] < d->c_gamma && norm0[e] > 1e-30;
+    if (override_troubled && override_troubled[e] >= 0) tr = override_troubled[e] && norm0[e] > 1e-30;
+    troubled[e] = tr;
+    double al[OR_MAXND];
+    for (int qi = 0; qi < nq; ++qi) al[qi] = 1.0;
+    if (tr) {
+      double at[OR_MAXND], f[OR_MAXND], s1 = 0.0, s2 = 0.0;
+      for (int qi = 0; qi < nq; ++qi) {
+        double xi, eta, W;
+        or_qpoint(m, qi, &xi, &eta, &W);
+        double s = 0.0;
+        for (int t = 0; t < or_nk(m); ++t) {
+          int kx, ky;
+          or_kidx(m, t, &kx, &ky);
+          if (kx + ky == 0) continue;
+          double v = or_du(m, c, kx, ky, xi, eta);
+          s += or_ipow(m->h, 2 * (kx + ky)) * v * v;
+        }
+        at[qi] = sqrt(s) / norm0[e];
+        f[qi] = gxq[qi] * gxq[qi] + gyq[qi] * gyq[qi] - gamma[e] * (gxq[qi] * pxq[qi] + gyq[qi] * pyq[qi]);
+        s1 += W * f[qi];
+        s2 += W * at[qi] * f[qi];
+      }
+      if (s1 > 0.0 && s2 > 0.0)
+        for (int qi = 0; qi < nq; ++qi) al[qi] = at[qi] * s1 / s2;
+    }
+    for (int qi = 0; qi < nq; ++qi) alpha[(size_t)e * nq + qi] = al[qi];
+    /* stage (e) */
+    for (int qi = 0; qi < nq; ++qi) {
+      double xi, eta, W = Wq[qi];
+      or_qpoint(m, qi, &xi, &eta, &W);
+      double U = or_du(m, c, 0, 0, xi, eta), Fx, Fy;
+      or_flux(m, &U, &Fx, &Fy);
+      double vx = gxq[qi] - gamma[e] * pxq[qi], vy = gyq[qi] - gamma[e] * pyq[qi];
+      for (int mi = 0; mi < nd; ++mi) {
+        double px = or_dphi(m, mi, 1, 0, xi, eta), py = m->dim == 2 ? or_dphi(m, mi, 0, 1, xi, eta) : 0.0;
+        double val = W * (px * Fx + (m->dim == 2 ? py * Fy : 0.0)) - nu[e] * al[qi] * W * (px * vx + py * vy);
+        r[or_cg_node(m, e, mi % m->n, mi / m->n)] += val;
+      }
+    }
+  }
+  /* M^{-1} r: lumped mass, then two defect-correction sweeps du += ML^{-1}(r - M_C du) */
+  for (int j = 0; j < nn; ++j) dudt[j] = r[j] / ML[j];
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    or_cg_consistent_mass(m, dudt, tmp);
+    for (int j = 0; j < nn; ++j) dudt[j] += (r[j] - tmp[j]) / ML[j];
+  }
+  int st = OR_OK;
+  for (int j = 0; j < nn; ++j)
+    if (!isfinite(dudt[j])) st = OR_ERR_NONFINITE;
+  free(ML);
+  free(Ph);
+  free(r);
+  free(tmp);
+  return st;
+}
+
 /* ------------------------------------------------------------------------- */
 /* exported entry points                                                      */
 /* ------------------------------------------------------------------------- */
+
+/* cell-local view of a state: the state itself for DG, a gathered copy for CG */
+static const double* or_local_state(const or_mesh* m, const double* u, double** owned) {
+  *owned = NULL;
+  if (m->kind != OR_CG) return u;
+  double* uc = (double*)malloc(sizeof(double) * (size_t)m->nvar * m->ncell * m->nd);
+  if (!uc) return NULL;
+  or_cg_gather(m, u, uc);
+  *owned = uc;
+  return uc;
+}
+
+static size_t or_state_len(const or_mesh* m) {
+  return m->kind == OR_CG ? (size_t)m->nvar * m->nnode : (size_t)m->nvar * m->ncell * m->nd;
+}
+
+/* number of doubles in a state: nvar * ncell * (p+1)^dim (DG) or nvar * nnode (CG) */
+int or_state_size(const or_desc* d, int* n) {
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  *n = (int)or_state_len(&m);
+  or_mesh_free(&m);
+  return OR_OK;
+}
 
 int or_mesh_counts(const or_desc* d, int* ncell, int* ndof, int* nvar, int* nvert, int* nq) {
   or_mesh m;
@@ -754,7 +1011,11 @@ int or_hermite(const or_desc* d, const double* u, double* T, double* beta) {
   or_mesh m;
   int st = or_mesh_init(d, &m);
   if (st) return st;
-  or_hermite_m(&m, u, T, beta);
+  double* owned;
+  const double* ul = or_local_state(&m, u, &owned);
+  if (!ul) { or_mesh_free(&m); return OR_ERR_NOMEM; }
+  or_hermite_m(&m, ul, T, beta);
+  free(owned);
   or_mesh_free(&m);
   return OR_OK;
 }
@@ -767,8 +1028,12 @@ int or_vertex_average(const or_desc* d, const double* u, double* Tstar) {
   double* T = (double*)malloc(sizeof(double) * nT);
   double* beta = (double*)malloc(sizeof(double) * m.ncell * m.ncorner);
   if (!T || !beta) { free(T); free(beta); or_mesh_free(&m); return OR_ERR_NOMEM; }
-  or_hermite_m(&m, u, T, beta);
+  double* owned;
+  const double* ul = or_local_state(&m, u, &owned);
+  if (!ul) { free(T); free(beta); or_mesh_free(&m); return OR_ERR_NOMEM; }
+  or_hermite_m(&m, ul, T, beta);
   or_vertex_average_m(&m, T, beta, Tstar);
+  free(owned);
   free(T);
   free(beta);
   or_mesh_free(&m);
@@ -783,6 +1048,8 @@ int or_residual(const or_desc* d, const double* u, const int* override_troubled,
   int st = or_mesh_init(d, &m);
   if (st) return st;
   size_t nT = (size_t)m.ncell * m.ncorner * m.nd;
+  double* owned = NULL;
+  const double* ul = or_local_state(&m, u, &owned);
   double* T = (double*)malloc(sizeof(double) * nT);
   double* beta = (double*)malloc(sizeof(double) * m.ncell * m.ncorner);
   double* Tstar = (double*)malloc(sizeof(double) * (size_t)m.nvert * m.nd);
@@ -791,22 +1058,27 @@ int or_residual(const or_desc* d, const double* u, const int* override_troubled,
   double* norm0 = (double*)malloc(sizeof(double) * m.ncell);
   double* alpha = (double*)malloc(sizeof(double) * (size_t)m.ncell * m.nvar * m.nq);
   int* troubled = (int*)malloc(sizeof(int) * m.ncell);
-  double* r = dudt ? NULL : (double*)malloc(sizeof(double) * (size_t)m.nvar * m.ncell * m.nd);
-  if (!T || !beta || !Tstar || !gamma || !nu || !norm0 || !alpha || !troubled || (!dudt && !r)) {
+  double* r = dudt ? NULL : (double*)malloc(sizeof(double) * or_state_len(&m));
+  if (!ul || !T || !beta || !Tstar || !gamma || !nu || !norm0 || !alpha || !troubled || (!dudt && !r)) {
     st = OR_ERR_NOMEM;
     goto done;
   }
-  or_hermite_m(&m, u, T, beta);
+  or_hermite_m(&m, ul, T, beta);
   or_vertex_average_m(&m, T, beta, Tstar);
-  st = or_sensor_m(&m, u, Tstar, gamma, nu, norm0, NULL);
+  st = or_sensor_m(&m, ul, Tstar, gamma, nu, norm0, NULL);
   if (st) goto done;
-  or_sc_weights_m(&m, u, gamma, norm0, override_troubled, alpha, troubled);
-  st = or_residual_m(&m, u, gamma, nu, alpha, dudt ? dudt : r);
+  if (m.kind == OR_CG) {
+    st = or_cg_residual_m(&m, ul, gamma, nu, norm0, override_troubled, alpha, troubled, dudt ? dudt : r);
+  } else {
+    or_sc_weights_m(&m, ul, gamma, norm0, override_troubled, alpha, troubled);
+    st = or_residual_m(&m, ul, gamma, nu, alpha, dudt ? dudt : r);
+  }
   if (gamma_out) memcpy(gamma_out, gamma, sizeof(double) * m.ncell);
   if (nu_out) memcpy(nu_out, nu, sizeof(double) * m.ncell);
   if (alpha_out) memcpy(alpha_out, alpha, sizeof(double) * (size_t)m.ncell * m.nvar * m.nq);
   if (troubled_out) memcpy(troubled_out, troubled, sizeof(int) * m.ncell);
 done:
+  free(owned);
   free(T);
   free(beta);
   free(Tstar);
@@ -826,6 +1098,7 @@ int or_residual_given(const or_desc* d, const double* u, const double* gamma, co
   or_mesh m;
   int st = or_mesh_init(d, &m);
   if (st) return st;
+  if (m.kind != OR_DG) { or_mesh_free(&m); return OR_ERR_UNSUPPORTED; }
   st = or_residual_m(&m, u, gamma, nu, alpha, dudt);
   or_mesh_free(&m);
   return st;
@@ -836,6 +1109,7 @@ int or_sc_weights(const or_desc* d, const double* u, const double* gamma, double
   or_mesh m;
   int st = or_mesh_init(d, &m);
   if (st) return st;
+  if (m.kind != OR_DG) { or_mesh_free(&m); return OR_ERR_UNSUPPORTED; }
   double* norm0 = (double*)calloc(m.ncell, sizeof(double));
   int* tr = troubled ? troubled : (int*)malloc(sizeof(int) * m.ncell);
   if (!norm0 || !tr) { st = OR_ERR_NOMEM; goto done; }
@@ -870,14 +1144,18 @@ int or_max_wavespeed(const or_desc* d, const double* u, double* lam_max) {
   or_mesh m;
   int st = or_mesh_init(d, &m);
   if (st) return st;
+  double* owned;
+  const double* ul = or_local_state(&m, u, &owned);
+  if (!ul) { or_mesh_free(&m); return OR_ERR_NOMEM; }
   double best = 0.0;
   for (int e = 0; e < m.ncell; ++e) {
     double lam;
-    st = or_cell_lambda(&m, u, e, &lam);
+    st = or_cell_lambda(&m, ul, e, &lam);
     if (st) break;
     if (lam > best) best = lam;
   }
   *lam_max = best;
+  free(owned);
   or_mesh_free(&m);
   return st;
 }
@@ -887,7 +1165,7 @@ int or_ssprk3(const or_desc* d, double* u, double dt, int nsteps) {
   or_mesh m;
   int st = or_mesh_init(d, &m);
   if (st) return st;
-  size_t N = (size_t)m.nvar * m.ncell * m.nd;
+  size_t N = or_state_len(&m);
   or_mesh_free(&m);
   double* L = (double*)malloc(sizeof(double) * N);
   double* u1 = (double*)malloc(sizeof(double) * N);
@@ -915,16 +1193,20 @@ int or_mass_total(const or_desc* d, const double* u, double* totals) {
   or_mesh m;
   int st = or_mesh_init(d, &m);
   if (st) return st;
+  double* owned;
+  const double* ul = or_local_state(&m, u, &owned);
+  if (!ul) { or_mesh_free(&m); return OR_ERR_NOMEM; }
   for (int v = 0; v < m.nvar; ++v) {
     double s = 0.0;
     for (int e = 0; e < m.ncell; ++e)
       for (int qi = 0; qi < m.nq; ++qi) {
         double xi, eta, W;
         or_qpoint(&m, qi, &xi, &eta, &W);
-        s += W * or_du(&m, or_cell(&m, u, v, e), 0, 0, xi, eta);
+        s += W * or_du(&m, or_cell(&m, ul, v, e), 0, 0, xi, eta);
       }
     totals[v] = s;
   }
+  free(owned);
   or_mesh_free(&m);
   return OR_OK;
 }
@@ -998,6 +1280,19 @@ int or_project(const or_desc* d, int type, const double* params, double* u) {
   or_mesh m;
   int st = or_mesh_init(d, &m);
   if (st) return st;
+  if (m.kind == OR_CG) { /* CG: interpolation at the GLL nodes (reading A25) */
+    for (int J = 0; J < m.nny; ++J)
+      for (int I = 0; I < m.nnx; ++I) {
+        int i = I / m.p, a = I % m.p, j = J / m.p, b = J % m.p;
+        double x = d->x0 + (i + 0.5) * m.dx + 0.5 * m.dx * m.gll[a];
+        double y = m.dim == 2 ? d->y0 + (j + 0.5) * m.dy + 0.5 * m.dy * m.gll[b] : 0.0;
+        double U[4];
+        or_ic_eval(d, type, params, x, y, U);
+        for (int v = 0; v < m.nvar; ++v) u[(size_t)v * m.nnode + I + m.nnx * J] = U[v];
+      }
+    or_mesh_free(&m);
+    return OR_OK;
+  }
   double px[OR_NPROJ], pw[OR_NPROJ];
   or_gauss(OR_NPROJ, px, pw);
   int npy = m.dim == 2 ? OR_NPROJ : 1;
@@ -1039,6 +1334,9 @@ int or_eval_points(const or_desc* d, const double* u, int var, int nq1d, double*
   or_gauss(nq1d, px, pw);
   int npy = m.dim == 2 ? nq1d : 1;
   size_t t = 0;
+  double* owned;
+  const double* ul = or_local_state(&m, u, &owned);
+  if (!ul) { or_mesh_free(&m); return OR_ERR_NOMEM; }
   for (int e = 0; e < m.ncell; ++e) {
     int i = e % m.nx, j = e / m.nx;
     double xc = d->x0 + (i + 0.5) * m.dx;
@@ -1046,12 +1344,13 @@ int or_eval_points(const or_desc* d, const double* u, int var, int nq1d, double*
     for (int b = 0; b < npy; ++b)
       for (int a = 0; a < nq1d; ++a, ++t) {
         double xi = px[a], eta = m.dim == 2 ? px[b] : 0.0;
-        if (vals) vals[t] = or_du(&m, or_cell(&m, u, var, e), 0, 0, xi, eta);
+        if (vals) vals[t] = or_du(&m, or_cell(&m, ul, var, e), 0, 0, xi, eta);
         if (xs) xs[t] = xc + 0.5 * m.dx * xi;
         if (ys) ys[t] = yc + 0.5 * m.dy * eta;
         if (ws) ws[t] = pw[a] * (m.dim == 2 ? pw[b] : 1.0) * m.jac;
       }
   }
+  free(owned);
   or_mesh_free(&m);
   return OR_OK;
 }

@@ -84,6 +84,7 @@ def _load():
             ip = P(ctypes.c_int)
             sig = {
                 "or_mesh_counts": [d, ip, ip, ip, ip, ip],
+                "or_state_size": [d, ip],
                 "or_vertex_patches": [d, ip, ip, ip, ip],
                 "or_gauss_rule": [ctypes.c_int, dp, dp],
                 "or_hermite": [d, dp, dp, dp],
@@ -149,7 +150,12 @@ def counts(d: dict) -> dict:
 
 
 def state_shape(d: dict):
+    """(nvar, ncell, (p+1)^dim) for DG; (nvar, nnode) nodal GLL values for CG."""
     c = counts(d)
+    if d.get("kind", DG) == CG:
+        n = ctypes.c_int()
+        _check(_load().or_state_size(ctypes.byref(_cdesc(d)), ctypes.byref(n)), "state_size")
+        return (c["nvar"], n.value // c["nvar"])
     return (c["nvar"], c["ncell"], c["nd"])
 
 
@@ -204,7 +210,7 @@ def residual(d: dict, u, override_troubled=None):
     c = counts(d)
     u = _u(u)
     out = dict(
-        dudt=np.zeros((c["nvar"], c["ncell"], c["nd"])),
+        dudt=np.zeros(state_shape(d)),
         gamma=np.zeros(c["ncell"]),
         nu=np.zeros(c["ncell"]),
         alpha=np.zeros((c["ncell"], c["nvar"], c["nq"])),

@@ -9,9 +9,11 @@
 //   (d)     SC weights: alpha~_q from the density's pointwise indicator, the
 //           dissipation f_q of each conserved variable redistributed separately, so
 //           each variable keeps its own cell dissipation rate (eq. alphaq);
-//   (e)     HLL face fluxes with Davis wave-speed estimates (identical bits on both
-//           sides of a face), the volume flux and the viscous term by sum
-//           factorisation, M^{-1}, and the SSP-RK3 combination.
+//   (e)     HLL face fluxes with Davis wave-speed estimates, the volume flux and the
+//           viscous term by sum factorisation, M^{-1}, and the SSP-RK3 combination.
+//           As in the scalar kernel, every flux is evaluated as its deviation from the
+//           flux of the cell's mean state (exact: a constant flux has zero residual),
+//           so FP32 rounding is relative to the variation inside the cell.
 // Non-positive density or pressure at any node raises the positivity bit of the
 // status word (the computation continues; nothing traps).
 #include "dg_scalar_kernel.cuh"
@@ -21,41 +23,79 @@ namespace {
 
 constexpr int NV = 4;
 
-__device__ __forceinline__ void euler_flux(float g, const float* U, float* Fx, float* Fy, float& p_out) {
-  const float rho = U[0], ir = 1.0f / rho, vx = U[1] * ir, vy = U[2] * ir;
-  const float p = (g - 1.0f) * (U[3] - 0.5f * (U[1] * vx + U[2] * vy));
-  Fx[0] = U[1];
-  Fx[1] = fmaf(U[1], vx, p);
-  Fx[2] = U[2] * vx;
-  Fx[3] = (U[3] + p) * vx;
-  Fy[0] = U[2];
-  Fy[1] = U[1] * vy;
-  Fy[2] = fmaf(U[2], vy, p);
-  Fy[3] = (U[3] + p) * vy;
-  p_out = p;
+// Mean state of a cell and the derived quantities the deviation fluxes need.
+struct EulerMean {
+  float U[NV];      // rho, m_x, m_y, E of the cell mean
+  float vx, vy, H;  // mean velocity, E + p of the mean state
+};
+
+__device__ __forceinline__ EulerMean euler_mean(float g, const float* Ub) {
+  EulerMean M;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) M.U[v] = Ub[v];
+  const float ir = 1.0f / Ub[0];
+  M.vx = Ub[1] * ir;
+  M.vy = Ub[2] * ir;
+  const float p = (g - 1.0f) * (Ub[3] - 0.5f * (Ub[1] * M.vx + Ub[2] * M.vy));
+  M.H = Ub[3] + p;
+  return M;
 }
 
-// |v| + c at a node; flags non-positive density or pressure
+// F(Ubar + d) - F(Ubar) in x and y, written as sums of (mean quantity) x (deviation)
+// so that FP32 rounding is relative to |d|:
+//   dv = (dm - vbar drho) / rho,  dK = (mbar . dv + dm . vbar + dm . dv) / 2,
+//   dp = (g - 1)(dE - dK),        dH = dE + dp.
+__device__ __forceinline__ void euler_dflux(float g, const EulerMean& M, const float* d, float* dFx, float* dFy) {
+  const float ir = 1.0f / (M.U[0] + d[0]);
+  const float dvx = fmaf(-M.vx, d[0], d[1]) * ir, dvy = fmaf(-M.vy, d[0], d[2]) * ir;
+  const float dK = 0.5f * (M.U[1] * dvx + M.U[2] * dvy + d[1] * M.vx + d[2] * M.vy + d[1] * dvx + d[2] * dvy);
+  const float dp = (g - 1.0f) * (d[3] - dK);
+  const float dH = d[3] + dp;
+  dFx[0] = d[1];
+  dFx[1] = M.U[1] * dvx + d[1] * M.vx + d[1] * dvx + dp;
+  dFx[2] = M.U[2] * dvx + d[2] * M.vx + d[2] * dvx;
+  dFx[3] = M.H * dvx + dH * M.vx + dH * dvx;
+  dFy[0] = d[2];
+  dFy[1] = M.U[1] * dvy + d[1] * M.vy + d[1] * dvy;
+  dFy[2] = M.U[2] * dvy + d[2] * M.vy + d[2] * dvy + dp;
+  dFy[3] = M.H * dvy + dH * M.vy + dH * dvy;
+}
+
+__device__ __forceinline__ float euler_pressure(float g, const float* U) {
+  return (g - 1.0f) * (U[3] - 0.5f * (U[1] * U[1] + U[2] * U[2]) / U[0]);
+}
+
+// |v| + c at a node of full state U; flags non-positive density or pressure
 __device__ __forceinline__ float euler_speed(float g, const float* U, bool& bad) {
-  const float rho = U[0];
-  const float ir = 1.0f / rho, vx = U[1] * ir, vy = U[2] * ir;
-  const float p = (g - 1.0f) * (U[3] - 0.5f * (U[1] * vx + U[2] * vy));
+  const float rho = U[0], ir = 1.0f / rho;
+  const float vx = U[1] * ir, vy = U[2] * ir;
+  const float p = euler_pressure(g, U);
   bad |= !(rho > 0.0f) || !(p > 0.0f);
   return sqrtf(vx * vx + vy * vy) + sqrtf(g * fmaxf(p, 0.0f) * fabsf(ir));
 }
 
-// HLL flux across a face with normal along +x (dir 0) or +y (dir 1), left/lower state
-// UL, right/upper state UR (reading A14: Davis estimates).
-__device__ __forceinline__ void hll(float g, const float* UL, const float* UR, int dir, float* F, bool& bad) {
-  float FxL[NV], FyL[NV], FxR[NV], FyR[NV], pL, pR;
-  euler_flux(g, UL, FxL, FyL, pL);
-  euler_flux(g, UR, FxR, FyR, pR);
-  const float* fl = dir == 0 ? FxL : FyL;
-  const float* fr = dir == 0 ? FxR : FyR;
+// HLL flux minus F(Ubar) . n across a face with normal +x (dir 0) or +y (dir 1), from
+// the left/lower state Ubar + dL to the right/upper state Ubar + dR (reading A14, Davis
+// wave speeds from the full states).  The constant F(Ubar) drops out of every branch:
+// (S_R F(Ubar) - S_L F(Ubar)) / (S_R - S_L) = F(Ubar).
+__device__ __forceinline__ void hll_dev(float g, const EulerMean& M, const float* dL, const float* dR, int dir, float* F,
+                                        bool& bad) {
+  float UL[NV], UR[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    UL[v] = M.U[v] + dL[v];
+    UR[v] = M.U[v] + dR[v];
+  }
+  const float pL = euler_pressure(g, UL), pR = euler_pressure(g, UR);
   bad |= !(UL[0] > 0.0f) || !(UR[0] > 0.0f) || !(pL > 0.0f) || !(pR > 0.0f);
   const float vnl = UL[1 + dir] / UL[0], vnr = UR[1 + dir] / UR[0];
   const float cl = sqrtf(g * fmaxf(pL, 0.0f) / fabsf(UL[0])), cr = sqrtf(g * fmaxf(pR, 0.0f) / fabsf(UR[0]));
   const float sl = fminf(vnl - cl, vnr - cr), sr = fmaxf(vnl + cl, vnr + cr);
+  float fxl[NV], fyl[NV], fxr[NV], fyr[NV];
+  euler_dflux(g, M, dL, fxl, fyl);
+  euler_dflux(g, M, dR, fxr, fyr);
+  const float* fl = dir == 0 ? fxl : fyl;
+  const float* fr = dir == 0 ? fxr : fyr;
   if (sl >= 0.0f) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = fl[v];
@@ -65,7 +105,7 @@ __device__ __forceinline__ void hll(float g, const float* UL, const float* UR, i
   } else {
     const float inv = 1.0f / (sr - sl);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = (sr * fl[v] - sl * fr[v] + sl * sr * (UR[v] - UL[v])) * inv;
+    for (int v = 0; v < NV; ++v) F[v] = (sr * fl[v] - sl * fr[v] + sl * sr * (dR[v] - dL[v])) * inv;
   }
 }
 
@@ -119,10 +159,21 @@ __global__ void __launch_bounds__(TX* TY)
     const bool has_w = a.perx || gi_w >= 0, has_e = a.perx || gi_w + 1 < nx;
     const bool has_s = a.pery || gj_s >= 0, has_n = a.pery || gj_s + 1 < ny;
     const float* base = sc + vb * HX + va;
-    if (has_w && has_s) vertex_slot<2, P, 1, 1>(a, T, base, NH, acc, wsum);
-    if (has_e && has_s) vertex_slot<2, P, -1, 1>(a, T, base + 1, NH, acc, wsum);
-    if (has_w && has_n) vertex_slot<2, P, 1, -1>(a, T, base + HX, NH, acc, wsum);
-    if (has_e && has_n) vertex_slot<2, P, -1, -1>(a, T, base + HX + 1, NH, acc, wsum);
+    // slots SW, SE, NW, NE (density block only)
+#pragma unroll 1
+    for (int s = 0; s < NC; ++s) {
+      const int ex = s & 1, ey = (s >> 1) & 1;
+      if (!((ex ? has_e : has_w) && (ey ? has_n : has_s))) continue;
+      float t[ND];
+      corner_taylor<2, P>(T, base + ex + ey * HX, NH, ex ? -1.0f : 1.0f, ey ? -1.0f : 1.0f, t);
+      float b2 = 0.0f;
+#pragma unroll
+      for (int k = 1; k < ND; ++k) b2 = fmaf(T.sigma[k] * t[k], t[k], b2);
+      const float wt = 1.0f / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+      wsum += wt;
+#pragma unroll
+      for (int k = 0; k < ND; ++k) acc[k] = fmaf(wt, t[k], acc[k]);
+    }
     const float inv = 1.0f / wsum;
 #pragma unroll
     for (int k = 0; k < ND; ++k) st[k * NVT + vtx] = acc[k] * inv;
@@ -206,8 +257,12 @@ __global__ void __launch_bounds__(TX* TY)
       gam = 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
   }
 
-  // ---- own traces at the face nodes (all variables), lambda_e over volume + faces -------
+  // ---- own traces at the face nodes (deviations from the cell mean), lambda_e ---------------
   bool bad = false;
+  float Ubar[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Ubar[v] = C(v, 0, hc);
+  const EulerMean M = euler_mean(g, Ubar);
   float oR[NV][N], oL[NV][N], oT[NV][N], oB[NV][N];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -217,7 +272,7 @@ __global__ void __launch_bounds__(TX* TY)
       float r = 0.0f, l = 0.0f, t = 0.0f, b = 0.0f;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const float cr = C(v, i + N * j, hc), ct = C(v, j + N * i, hc);
+        const float cr = (i + N * j) ? C(v, i + N * j, hc) : 0.0f, ct = (j + N * i) ? C(v, j + N * i, hc) : 0.0f;
         r += cr;
         l += (i & 1) ? -cr : cr;
         t += ct;
@@ -249,16 +304,16 @@ __global__ void __launch_bounds__(TX* TY)
   for (int q = 0; q < N; ++q) {
     float U[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = oR[v][q];
+    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oR[v][q];
     lam = fmaxf(lam, euler_speed(g, U, bad));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = oL[v][q];
+    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oL[v][q];
     lam = fmaxf(lam, euler_speed(g, U, bad));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = oT[v][q];
+    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oT[v][q];
     lam = fmaxf(lam, euler_speed(g, U, bad));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = oB[v][q];
+    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oB[v][q];
     lam = fmaxf(lam, euler_speed(g, U, bad));
   }
   // volume nodes: values, and the gradient data needed by stage (d)
@@ -384,12 +439,16 @@ __global__ void __launch_bounds__(TX* TY)
         float r0 = 0.0f, l0 = 0.0f, t0 = 0.0f, b0 = 0.0f;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-          const float cr = C(v, i + N * j, hc + 1), cl = C(v, i + N * j, hc - 1);
-          r0 += (i & 1) ? -cr : cr;
-          l0 += cl;
-          const float ct = C(v, j + N * i, hc + HX), cb = C(v, j + N * i, hc - HX);
-          t0 += (i & 1) ? -ct : ct;
-          b0 += cb;
+          if (i + N * j) {
+            const float cr = C(v, i + N * j, hc + 1), cl = C(v, i + N * j, hc - 1);
+            r0 += (i & 1) ? -cr : cr;
+            l0 += cl;
+          }
+          if (j + N * i) {
+            const float ct = C(v, j + N * i, hc + HX), cb = C(v, j + N * i, hc - HX);
+            t0 += (i & 1) ? -ct : ct;
+            b0 += cb;
+          }
         }
         nR[j] = r0;
         nL[j] = l0;
@@ -406,10 +465,10 @@ __global__ void __launch_bounds__(TX* TY)
           xt = fmaf(T.B[q][j], nT[j], xt);
           xb = fmaf(T.B[q][j], nB[j], xb);
         }
-        vR[v][q] = hasR ? xr : oR[v][q];
-        vL[v][q] = hasL ? xl : oL[v][q];
-        vT[v][q] = hasT ? xt : oT[v][q];
-        vB[v][q] = hasB ? xb : oB[v][q];
+        vR[v][q] = hasR ? (C(v, 0, hc + 1) - Ubar[v]) + xr : oR[v][q];
+        vL[v][q] = hasL ? (C(v, 0, hc - 1) - Ubar[v]) + xl : oL[v][q];
+        vT[v][q] = hasT ? (C(v, 0, hc + HX) - Ubar[v]) + xt : oT[v][q];
+        vB[v][q] = hasB ? (C(v, 0, hc - HX) - Ubar[v]) + xb : oB[v][q];
       }
     }
 #pragma unroll
@@ -417,22 +476,22 @@ __global__ void __launch_bounds__(TX* TY)
       float UL[NV], UR[NV], F[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) { UL[v] = oR[v][q]; UR[v] = vR[v][q]; }
-      hll(g, UL, UR, 0, F, bad);
+      hll_dev(g, M, UL, UR, 0, F, bad);
 #pragma unroll
       for (int v = 0; v < NV; ++v) FR[v][q] = F[v];
 #pragma unroll
       for (int v = 0; v < NV; ++v) { UL[v] = vL[v][q]; UR[v] = oL[v][q]; }
-      hll(g, UL, UR, 0, F, bad);
+      hll_dev(g, M, UL, UR, 0, F, bad);
 #pragma unroll
       for (int v = 0; v < NV; ++v) FL[v][q] = F[v];
 #pragma unroll
       for (int v = 0; v < NV; ++v) { UL[v] = oT[v][q]; UR[v] = vT[v][q]; }
-      hll(g, UL, UR, 1, F, bad);
+      hll_dev(g, M, UL, UR, 1, F, bad);
 #pragma unroll
       for (int v = 0; v < NV; ++v) FT[v][q] = F[v];
 #pragma unroll
       for (int v = 0; v < NV; ++v) { UL[v] = vB[v][q]; UR[v] = oB[v][q]; }
-      hll(g, UL, UR, 1, F, bad);
+      hll_dev(g, M, UL, UR, 1, F, bad);
 #pragma unroll
       for (int v = 0; v < NV; ++v) FB[v][q] = F[v];
     }
@@ -476,8 +535,9 @@ __global__ void __launch_bounds__(TX* TY)
         float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
         for (int mx = 0; mx < N; ++mx) {
-          s0 = fmaf(T.B[qx][mx], C(v, mx + N * my, hc), s0);
-          s1 = fmaf(T.Bd[qx][mx], C(v, mx + N * my, hc), s1);
+          const float cm = (mx + N * my) ? C(v, mx + N * my, hc) : 0.0f;  // deviation: no mean mode
+          s0 = fmaf(T.B[qx][mx], cm, s0);
+          s1 = fmaf(T.Bd[qx][mx], cm, s1);
         }
         tb[v][my] = s0;
         td[v][my] = s1;
@@ -486,7 +546,7 @@ __global__ void __launch_bounds__(TX* TY)
 #pragma unroll
     for (int qy = 0; qy < N; ++qy) {
       const int q = qx + N * qy;
-      float U[NV], Ux[NV], Uy[NV], Fx[NV], Fy[NV], p;
+      float dU[NV], Ux[NV], Uy[NV], Fx[NV], Fy[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         float u = 0.0f, ux = 0.0f, uy = 0.0f;
@@ -496,11 +556,11 @@ __global__ void __launch_bounds__(TX* TY)
           ux = fmaf(T.B[qy][my], td[v][my], ux);
           uy = fmaf(T.Bd[qy][my], tb[v][my], uy);
         }
-        U[v] = u;
+        dU[v] = u;
         Ux[v] = ux;
         Uy[v] = uy;
       }
-      euler_flux(g, U, Fx, Fy, p);
+      euler_dflux(g, M, dU, Fx, Fy);
       const float W = T.w[qx] * T.w[qy];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {

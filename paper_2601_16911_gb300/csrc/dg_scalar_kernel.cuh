@@ -22,8 +22,10 @@
 //           cell mean (exact: a constant flux has zero residual), so FP32 rounding is
 //           relative to the variation within a cell, not to |f(u)|.
 //
-// All arithmetic is FP32.  The tabulations arrive through a __grid_constant__ kernel
-// parameter, so fully unrolled loops read them as constant-bank operands.
+// Code-size discipline: the loops over vertex slots, corners, face nodes and volume
+// nodes are rolled and read their tabulations (staged in shared memory) with uniform,
+// broadcast loads, so the kernel body stays within the instruction cache; only the
+// short loops over modes are unrolled into registers.  All arithmetic is FP32.
 #pragma once
 
 #include "cvweno_internal.cuh"
@@ -107,26 +109,38 @@ __device__ __forceinline__ float llf_dev(const Law& law, const StageArgs& a, flo
   return 0.5f * (law.flux_dev_dir(dL, dir) + law.flux_dev_dir(dR, dir)) - 0.5f * lam * (dR - dL);
 }
 
-// Reference Taylor data t[k] = d^k u (s_x, s_y) at corner (SX, SY) of one cell whose
-// coefficients sit at c[m * stride].
-template <int DIM, int P, int SX, int SY>
-__device__ __forceinline__ void corner_taylor(const DgTables<DIM, P>& T, const float* c, int stride, float* t) {
+// Reference Taylor data t[k] = d^k u (sx, sy) at corner (sx, sy) in {-1, 1}^2 of one
+// cell whose coefficients sit at c[m * stride]:
+//   t[kx + N ky] = sx^kx sy^ky sum_my E[ky][my] sy^my sum_mx E[kx][mx] sx^mx c[mx, my]
+// using P_m^(k)(-1) = (-1)^(m+k) P_m^(k)(1).
+template <int DIM, int P>
+__device__ __forceinline__ void corner_taylor(const DgTables<DIM, P>& T, const float* c, int stride, float sx, float sy,
+                                              float* t) {
   constexpr int N = P + 1;
+  float px[N], py[N];
+  px[0] = py[0] = 1.0f;
+#pragma unroll
+  for (int m = 1; m < N; ++m) {
+    px[m] = px[m - 1] * sx;
+    py[m] = py[m - 1] * sy;
+  }
   if constexpr (DIM == 1) {
+    float cl[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) cl[m] = c[m * stride] * px[m];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       float acc = 0.0f;
 #pragma unroll
-      for (int m = 0; m < N; ++m) {
-        float e = (SX < 0 && ((m + k) & 1)) ? -T.E[k][m] : T.E[k][m];
-        acc = fmaf(e, c[m * stride], acc);
-      }
-      t[k] = acc;
+      for (int m = 0; m < N; ++m) acc = fmaf(T.E[k][m], cl[m], acc);
+      t[k] = acc * px[k];
     }
   } else {
     float cl[N * N];
 #pragma unroll
-    for (int m = 0; m < N * N; ++m) cl[m] = c[m * stride];
+    for (int my = 0; my < N; ++my)
+#pragma unroll
+      for (int mx = 0; mx < N; ++mx) cl[mx + N * my] = c[(mx + N * my) * stride] * (px[mx] * py[my]);
     float tmp[N][N];  // [kx][my]
 #pragma unroll
     for (int kx = 0; kx < N; ++kx)
@@ -134,10 +148,7 @@ __device__ __forceinline__ void corner_taylor(const DgTables<DIM, P>& T, const f
       for (int my = 0; my < N; ++my) {
         float acc = 0.0f;
 #pragma unroll
-        for (int mx = 0; mx < N; ++mx) {
-          float e = (SX < 0 && ((mx + kx) & 1)) ? -T.E[kx][mx] : T.E[kx][mx];
-          acc = fmaf(e, cl[mx + N * my], acc);
-        }
+        for (int mx = 0; mx < N; ++mx) acc = fmaf(T.E[kx][mx], cl[mx + N * my], acc);
         tmp[kx][my] = acc;
       }
 #pragma unroll
@@ -146,49 +157,57 @@ __device__ __forceinline__ void corner_taylor(const DgTables<DIM, P>& T, const f
       for (int kx = 0; kx < N; ++kx) {
         float acc = 0.0f;
 #pragma unroll
-        for (int my = 0; my < N; ++my) {
-          float e = (SY < 0 && ((my + ky) & 1)) ? -T.E[ky][my] : T.E[ky][my];
-          acc = fmaf(e, tmp[kx][my], acc);
-        }
-        t[kx + N * ky] = acc;
+        for (int my = 0; my < N; ++my) acc = fmaf(T.E[ky][my], tmp[kx][my], acc);
+        t[kx + N * ky] = acc * (px[kx] * py[ky]);
       }
   }
 }
 
-// One slot of the vertex gather: cell at halo (hx, hy), touching corner (SX, SY).
-template <int DIM, int P, int SX, int SY>
-__device__ __forceinline__ void vertex_slot(const StageArgs& a, const DgTables<DIM, P>& T, const float* cell, int stride,
-                                            float* acc, float& wsum) {
-  constexpr int ND = DgTables<DIM, P>::ND;
-  float t[ND];
-  corner_taylor<DIM, P, SX, SY>(T, cell, stride, t);
-  float b2 = 0.0f;
-#pragma unroll
-  for (int k = 1; k < ND; ++k) b2 = fmaf(T.sigma[k] * t[k], t[k], b2);
-  float beta = powq(sqrtf(b2), a.q);
-  float wt = 1.0f / ipowf(a.eps + beta, a.r);
-  wsum += wt;
-#pragma unroll
-  for (int k = 0; k < ND; ++k) acc[k] = fmaf(wt, t[k], acc[k]);
-}
+// Shared-memory layout of the tile: halo coefficients, vertex candidates, the corner
+// matrices (rows padded to a multiple of 4 floats for 16-byte broadcast loads), the
+// 1D tabulations read with run-time node indices, and per-thread alpha~ storage.
+template <int DIM, int P, int TX, int TY>
+struct TileLayout {
+  using Tb = DgTables<DIM, P>;
+  static constexpr int N = P + 1, ND = Tb::ND, NS = Tb::NS, NC = Tb::NC;
+  static constexpr int NSP = (NS + 3) / 4 * 4;
+  static constexpr int NT = TX * TY;
+  static constexpr int HX = TX + 2, HY = DIM == 2 ? TY + 2 : 1, NH = HX * HY;
+  static constexpr int VXT = TX + 1, VYT = DIM == 2 ? TY + 1 : 1, NVT = VXT * VYT;
+  static constexpr int OFF_SC = 0;                                // [ND][NH]
+  static constexpr int OFF_ST = OFF_SC + ND * NH;                 // [ND][NVT]
+  static constexpr int OFF_A = (OFF_ST + ND * NVT + 3) / 4 * 4;   // [NC][NS][NSP]
+  static constexpr int OFF_B = OFF_A + NC * NS * NSP;             // [N][N]  B[q][m]
+  static constexpr int OFF_BD = OFF_B + N * N;                    // [N][N]  Bd[q][m]
+  static constexpr int OFF_BK = OFF_BD + N * N;                   // [N][N][N] Bk[k][q][m]
+  static constexpr int OFF_W = OFF_BK + N * N * N;                // [N]
+  static constexpr int OFF_NQ = OFF_W + N;                        // [ND][NT] pointwise indicators
+  static constexpr int FLOATS = OFF_NQ + ND * NT;
+  static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
+};
 
 template <int DIM, int P, int SYS, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY)
     dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
-  using Tb = DgTables<DIM, P>;
+  using L = TileLayout<DIM, P, TX, TY>;
   using Law = ScalarLaw<SYS, DIM>;
-  constexpr int N = P + 1, ND = Tb::ND, NS = Tb::NS, NC = Tb::NC;
-  constexpr int NT = TX * TY;
-  constexpr int HX = TX + 2, HY = DIM == 2 ? TY + 2 : 1, NH = HX * HY;
-  constexpr int VXT = TX + 1, VYT = DIM == 2 ? TY + 1 : 1, NVT = VXT * VYT;
-  extern __shared__ float smem[];
-  float* sc = smem;           // [ND][NH]  coefficients, mode-major
-  float* st = smem + ND * NH; // [ND][NVT] vertex candidates t* (reference units)
+  constexpr int N = L::N, ND = L::ND, NS = L::NS, NC = L::NC, NSP = L::NSP, NT = L::NT;
+  constexpr int HX = L::HX, NH = L::NH, VXT = L::VXT, NVT = L::NVT;
+  constexpr int NY1 = DIM == 2 ? N : 1;  // tensor extent in y (1 in 1D)
+  extern __shared__ __align__(16) float smem[];
+  float* sc = smem + L::OFF_SC;
+  float* st = smem + L::OFF_ST;
+  float* sA = smem + L::OFF_A;
+  float* sB = smem + L::OFF_B;
+  float* sBd = smem + L::OFF_BD;
+  float* sBk = smem + L::OFF_BK;
+  float* sW = smem + L::OFF_W;
+  float* sNq = smem + L::OFF_NQ;
 
   const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
   const int i0 = blockIdx.x * TX, j0 = DIM == 2 ? blockIdx.y * TY : 0;
 
-  // ---- load tile + halo ------------------------------------------------------------
+  // ---- load tile + halo, and the tabulations read with run-time indices ---------------
   for (int f = threadIdx.x; f < NH * ND; f += NT) {
     int r = f / (HX * ND);
     int rem = f - r * (HX * ND);
@@ -204,6 +223,16 @@ __global__ void __launch_bounds__(TX* TY)
     }
     sc[mm * NH + r * HX + cc] = ok ? __ldg(a.u_in + ((size_t)gj * nx + gi) * ND + mm) : 0.0f;
   }
+  for (int f = threadIdx.x; f < NC * NS * NSP; f += NT) {
+    int l = f / (NS * NSP), rem = f - l * (NS * NSP), i = rem / NSP, j = rem - i * NSP;
+    sA[f] = j < NS ? T.A[l][i][j] : 0.0f;
+  }
+  for (int f = threadIdx.x; f < N * N; f += NT) {
+    sB[f] = (&T.B[0][0])[f];
+    sBd[f] = (&T.Bd[0][0])[f];
+  }
+  for (int f = threadIdx.x; f < N * N * N; f += NT) sBk[f] = (&T.Bk[0][0][0])[f];
+  if (threadIdx.x < N) sW[threadIdx.x] = T.w[threadIdx.x];
   __syncthreads();
 
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
@@ -215,19 +244,25 @@ __global__ void __launch_bounds__(TX* TY)
 #pragma unroll
     for (int k = 0; k < ND; ++k) acc[k] = 0.0f;
     float wsum = 0.0f;
-    // halo coordinates of the SW (1D: W) cell of this vertex
     const int gi_w = i0 - 1 + va, gj_s = j0 - 1 + vb;
     const bool has_w = a.perx || gi_w >= 0, has_e = a.perx || gi_w + 1 < nx;
     const bool has_s = DIM == 1 || a.pery || gj_s >= 0, has_n = DIM == 1 || a.pery || gj_s + 1 < ny;
     const float* base = sc + (DIM == 2 ? vb * HX : 0) + va;
-    if constexpr (DIM == 1) {
-      if (has_w) vertex_slot<1, P, 1, 1>(a, T, base, NH, acc, wsum);
-      if (has_e) vertex_slot<1, P, -1, 1>(a, T, base + 1, NH, acc, wsum);
-    } else {
-      if (has_w && has_s) vertex_slot<2, P, 1, 1>(a, T, base, NH, acc, wsum);
-      if (has_e && has_s) vertex_slot<2, P, -1, 1>(a, T, base + 1, NH, acc, wsum);
-      if (has_w && has_n) vertex_slot<2, P, 1, -1>(a, T, base + HX, NH, acc, wsum);
-      if (has_e && has_n) vertex_slot<2, P, -1, -1>(a, T, base + HX + 1, NH, acc, wsum);
+    // slots SW, SE, NW, NE: the cell right of / above the vertex touches it with its
+    // left / lower corner (sign -1), the cell left of / below with its right / upper one
+#pragma unroll 1
+    for (int s = 0; s < NC; ++s) {
+      const int ex = s & 1, ey = (s >> 1) & 1;
+      if (!((ex ? has_e : has_w) && (ey ? has_n : has_s))) continue;
+      float t[ND];
+      corner_taylor<DIM, P>(T, base + ex + (DIM == 2 ? ey * HX : 0), NH, ex ? -1.0f : 1.0f, ey ? -1.0f : 1.0f, t);
+      float b2 = 0.0f;
+#pragma unroll
+      for (int k = 1; k < ND; ++k) b2 = fmaf(T.sigma[k] * t[k], t[k], b2);
+      const float wt = 1.0f / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+      wsum += wt;
+#pragma unroll
+      for (int k = 0; k < ND; ++k) acc[k] = fmaf(wt, t[k], acc[k]);
     }
     const float inv = 1.0f / wsum;
 #pragma unroll
@@ -276,19 +311,26 @@ __global__ void __launch_bounds__(TX* TY)
 #pragma unroll
     for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
     float osum = om0;
-#pragma unroll
+#pragma unroll 1
     for (int l = 0; l < NC; ++l) {
       const int vi = (tx + (l & 1)) + (DIM == 2 ? (ty + ((l >> 1) & 1)) * VXT : 0);
-      float tl[NS];
+      float tl[NSP];
 #pragma unroll
-      for (int k = 0; k < NS; ++k) tl[k] = st[(k + 1) * NVT + vi];
+      for (int k = 0; k < NSP; ++k) tl[k] = k < NS ? st[(k + 1) * NVT + vi] : 0.0f;
+      const float4* Al = reinterpret_cast<const float4*>(sA + l * NS * NSP);
       float wl[NS];
       float b2 = 0.0f;
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
         float acc = 0.0f;
 #pragma unroll
-        for (int j = 0; j < NS; ++j) acc = fmaf(T.A[l][i][j], tl[j], acc);
+        for (int j4 = 0; j4 < NSP / 4; ++j4) {
+          const float4 q4 = Al[i * (NSP / 4) + j4];
+          acc = fmaf(q4.x, tl[4 * j4 + 0], acc);
+          acc = fmaf(q4.y, tl[4 * j4 + 1], acc);
+          acc = fmaf(q4.z, tl[4 * j4 + 2], acc);
+          acc = fmaf(q4.w, tl[4 * j4 + 3], acc);
+        }
         wl[i] = acc;
         b2 = fmaf(acc, acc, b2);
       }
@@ -314,207 +356,150 @@ __global__ void __launch_bounds__(TX* TY)
       gam = 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
   }
 
-  // ---- values at volume Gauss nodes, in deviation form -------------------------------------
-  // u(x_q) = ubar + dU[q] with dU built from the non-mean modes only, so rounding is
-  // relative to the variation inside the cell rather than to |u| (the mean cancels
-  // exactly between the volume and face terms of every mode).
+  // ---- own trace polynomials along each face, as deviations from the mean -------------------
+  // u(x) = ubar + (non-mean modes): rounding stays relative to the in-cell variation.
   const float ubar = c[0];
   const Law law(a, ubar);
-  float cz[ND];
-#pragma unroll
-  for (int m = 0; m < ND; ++m) cz[m] = m == 0 ? 0.0f : c[m];
-  float dU[ND], Ux[ND], Uy[ND];
+  constexpr int NF = DIM == 2 ? N : 1;  // nodes per face
+  float trR[N], trL[N], trT[N], trB[N];
   if constexpr (DIM == 1) {
+    float sR = 0.0f, sL = 0.0f;
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
-      float u = 0.0f, ux = 0.0f;
-#pragma unroll
-      for (int m = 1; m < N; ++m) {
-        u = fmaf(T.B[q][m], cz[m], u);
-        ux = fmaf(T.Bd[q][m], cz[m], ux);
-      }
-      dU[q] = u;
-      Ux[q] = ux;
-      Uy[q] = 0.0f;
+    for (int m = 1; m < N; ++m) {
+      sR += c[m];
+      sL += (m & 1) ? -c[m] : c[m];
     }
+    trR[0] = sR;
+    trL[0] = sL;
   } else {
 #pragma unroll
-    for (int qx = 0; qx < N; ++qx) {
-      float tb[N], td[N];
+    for (int j = 0; j < N; ++j) {
+      float r = 0.0f, l = 0.0f, t = 0.0f, b = 0.0f;
 #pragma unroll
-      for (int my = 0; my < N; ++my) {
-        float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-        for (int mx = 0; mx < N; ++mx) {
-          s0 = fmaf(T.B[qx][mx], cz[mx + N * my], s0);
-          s1 = fmaf(T.Bd[qx][mx], cz[mx + N * my], s1);
-        }
-        tb[my] = s0;
-        td[my] = s1;
+      for (int i = 0; i < N; ++i) {
+        const float cr = (i + N * j) ? c[i + N * j] : 0.0f, ct = (j + N * i) ? c[j + N * i] : 0.0f;
+        r += cr;
+        l += (i & 1) ? -cr : cr;
+        t += ct;
+        b += (i & 1) ? -ct : ct;
       }
-#pragma unroll
-      for (int qy = 0; qy < N; ++qy) {
-        float u = 0.0f, ux = 0.0f, uy = 0.0f;
-#pragma unroll
-        for (int my = 0; my < N; ++my) {
-          u = fmaf(T.B[qy][my], tb[my], u);
-          ux = fmaf(T.B[qy][my], td[my], ux);
-          uy = fmaf(T.Bd[qy][my], tb[my], uy);
-        }
-        dU[qx + N * qy] = u;
-        Ux[qx + N * qy] = ux;
-        Uy[qx + N * qy] = uy;
-      }
+      trR[j] = r;
+      trL[j] = l;
+      trT[j] = t;
+      trB[j] = b;
     }
   }
 
-  // ---- own traces at the face Gauss nodes (deviations from ubar) ------------------------
-  // 1D: one node per face.  2D: x-faces carry N nodes in eta, y-faces N nodes in xi.
-  constexpr int NF = DIM == 2 ? N : 1;
-  float oR[NF], oL[NF], oT[NF], oB[NF];
-  {
-    if constexpr (DIM == 1) {
-      float sR = 0.0f, sL = 0.0f;
-#pragma unroll
-      for (int m = 1; m < N; ++m) {
-        sR += cz[m];
-        sL += (m & 1) ? -cz[m] : cz[m];
-      }
-      oR[0] = sR;
-      oL[0] = sL;
-    } else {
-      float trR[N], trL[N], trT[N], trB[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        float r = 0.0f, l = 0.0f, t = 0.0f, b = 0.0f;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          r += cz[i + N * j];
-          l += (i & 1) ? -cz[i + N * j] : cz[i + N * j];
-          t += cz[j + N * i];
-          b += (i & 1) ? -cz[j + N * i] : cz[j + N * i];
-        }
-        trR[j] = r;
-        trL[j] = l;
-        trT[j] = t;
-        trB[j] = b;
-      }
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        float r = 0.0f, l = 0.0f, t = 0.0f, b = 0.0f;
+  // ---- lambda_e (over face and volume nodes) and (d) the SC weights ------------------------------
+  bool troubled = false;
+  float afac = -1.0f;  // alpha_q = Nq[q] * afac where afac >= 0, else alpha_q = 1
+  float lam = a.lambda_const > 0.0f ? a.lambda_const : 0.0f;
+  if (!(a.lambda_const > 0.0f)) {
+#pragma unroll 1
+    for (int q = 0; q < NF; ++q) {
+      float vr = trR[0], vl = trL[0], vt = 0.0f, vbb = 0.0f;
+      if constexpr (DIM == 2) {
+        vr = vl = 0.0f;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          r = fmaf(T.B[q][j], trR[j], r);
-          l = fmaf(T.B[q][j], trL[j], l);
-          t = fmaf(T.B[q][j], trT[j], t);
-          b = fmaf(T.B[q][j], trB[j], b);
+          const float bq = sB[q * N + j];
+          vr = fmaf(bq, trR[j], vr);
+          vl = fmaf(bq, trL[j], vl);
+          vt = fmaf(bq, trT[j], vt);
+          vbb = fmaf(bq, trB[j], vbb);
         }
-        oR[q] = r;
-        oL[q] = l;
-        oT[q] = t;
-        oB[q] = b;
       }
+      lam = fmaxf(lam, fmaxf(law.speed(ubar + vr), law.speed(ubar + vl)));
+      if constexpr (DIM == 2) lam = fmaxf(lam, fmaxf(law.speed(ubar + vt), law.speed(ubar + vbb)));
     }
   }
-
-  // ---- lambda_e, nu_e ---------------------------------------------------------------------
-  float lam;
-  if (a.lambda_const > 0.0f) {
-    lam = a.lambda_const;
-  } else {
-    lam = 0.0f;
+  if (!(a.mode & kModeSensorOnly)) {
+    troubled = a.sc && gam < a.c_gamma && n0 > 1e-30f;
+    if (a.troubled_override) {
+      int ov = a.troubled_override[cell];
+      if (ov >= 0) troubled = ov && n0 > 1e-30f;
+    }
+  }
+  const bool need_sc = troubled && gam < 1.0f;
+  if (!(a.lambda_const > 0.0f) || need_sc) {
+    float s1 = 0.0f, s2 = 0.0f;
+#pragma unroll 1
+    for (int qx = 0; qx < N; ++qx) {
+      float tb[NY1], td[NY1];
 #pragma unroll
-    for (int q = 0; q < ND; ++q) lam = fmaxf(lam, law.speed(ubar + dU[q]));
+      for (int my = 0; my < NY1; ++my) {
+        float s0 = 0.0f, sd = 0.0f;
 #pragma unroll
-    for (int q = 0; q < NF; ++q) {
-      lam = fmaxf(lam, law.speed(ubar + oR[q]));
-      lam = fmaxf(lam, law.speed(ubar + oL[q]));
-      if constexpr (DIM == 2) {
-        lam = fmaxf(lam, law.speed(ubar + oT[q]));
-        lam = fmaxf(lam, law.speed(ubar + oB[q]));
+        for (int mx = 0; mx < N; ++mx) {
+          const float cm = (mx + N * my) ? c[mx + N * my] : 0.0f;
+          s0 = fmaf(sB[qx * N + mx], cm, s0);
+          sd = fmaf(sBd[qx * N + mx], cm, sd);
+        }
+        tb[my] = s0;
+        td[my] = sd;
+      }
+      float X[N][NY1];  // [kx][my]: x-derivatives of order kx at xi_qx (stage d only)
+      if (need_sc) {
+#pragma unroll
+        for (int kx = 0; kx < N; ++kx)
+#pragma unroll
+          for (int my = 0; my < NY1; ++my) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int mx = 0; mx < N; ++mx) acc = fmaf(sBk[(kx * N + qx) * N + mx], c[mx + N * my], acc);
+            X[kx][my] = acc;
+          }
+      }
+#pragma unroll 1
+      for (int qy = 0; qy < NY1; ++qy) {
+        float du = tb[0], ux = td[0], uy = 0.0f;
+        if constexpr (DIM == 2) {
+          du = ux = 0.0f;
+#pragma unroll
+          for (int my = 0; my < N; ++my) {
+            const float bq = sB[qy * N + my], dq = sBd[qy * N + my];
+            du = fmaf(bq, tb[my], du);
+            ux = fmaf(bq, td[my], ux);
+            uy = fmaf(dq, tb[my], uy);
+          }
+        }
+        if (!(a.lambda_const > 0.0f)) lam = fmaxf(lam, law.speed(ubar + du));
+        if (need_sc) {
+          float n2 = 0.0f;
+#pragma unroll
+          for (int ky = 0; ky < NY1; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < N; ++kx) {
+              if (kx + ky == 0) continue;
+              float dk = X[kx][0];
+              if constexpr (DIM == 2) {
+                dk = 0.0f;
+#pragma unroll
+                for (int my = 0; my < N; ++my) dk = fmaf(sBk[(ky * N + qy) * N + my], X[kx][my], dk);
+              }
+              n2 = fmaf(T.sigma[kx + N * ky] * dk, dk, n2);
+            }
+          const float nq = sqrtf(n2);
+          sNq[(qx + N * qy) * NT + threadIdx.x] = nq;
+          const float gx = a.two_dx * ux, gy = a.two_dy * uy;
+          const float g = fmaf(gx, gx, gy * gy);
+          const float W = sW[qx] * (DIM == 2 ? sW[qy] : 1.0f);
+          s1 = fmaf(W, g, s1);
+          s2 = fmaf(W * nq, g, s2);
+        }
       }
     }
+    if (need_sc && s2 > 0.0f) afac = s1 / s2;
   }
   const float nu = lam * a.nu_scale;
   if (a.gamma_out) a.gamma_out[cell] = gam;
   if (a.nu_out) a.nu_out[cell] = nu;
   if (a.lambda_out) a.lambda_out[cell] = lam;
   if (a.mode & kModeSensorOnly) return;
-
-  // ---- (d) shock-capturing quadrature weights ---------------------------------------------
-  bool troubled = a.sc && gam < a.c_gamma && n0 > 1e-30f;
-  if (a.troubled_override) {
-    int ov = a.troubled_override[cell];
-    if (ov >= 0) troubled = ov && n0 > 1e-30f;
-  }
-  float alpha[ND];
-#pragma unroll
-  for (int q = 0; q < ND; ++q) alpha[q] = 1.0f;
-  if (troubled && gam < 1.0f) {
-    float Nq[ND];
-    if constexpr (DIM == 1) {
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        float s2 = 0.0f;
-#pragma unroll
-        for (int k = 1; k < N; ++k) {
-          float d = 0.0f;
-#pragma unroll
-          for (int m = 0; m < N; ++m) d = fmaf(T.Bk[k][q][m], c[m], d);
-          s2 = fmaf(T.sigma[k] * d, d, s2);
-        }
-        Nq[q] = sqrtf(s2);
-      }
-    } else {
-#pragma unroll
-      for (int qx = 0; qx < N; ++qx) {
-        float X[N][N];  // [kx][my]
-#pragma unroll
-        for (int kx = 0; kx < N; ++kx)
-#pragma unroll
-          for (int my = 0; my < N; ++my) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int mx = 0; mx < N; ++mx) acc = fmaf(T.Bk[kx][qx][mx], c[mx + N * my], acc);
-            X[kx][my] = acc;
-          }
-#pragma unroll
-        for (int qy = 0; qy < N; ++qy) {
-          float s2 = 0.0f;
-#pragma unroll
-          for (int ky = 0; ky < N; ++ky)
-#pragma unroll
-            for (int kx = 0; kx < N; ++kx) {
-              if (kx + ky == 0) continue;
-              float d = 0.0f;
-#pragma unroll
-              for (int my = 0; my < N; ++my) d = fmaf(T.Bk[ky][qy][my], X[kx][my], d);
-              s2 = fmaf(T.sigma[kx + N * ky] * d, d, s2);
-            }
-          Nq[qx + N * qy] = sqrtf(s2);
-        }
-      }
-    }
-    float s1 = 0.0f, s2 = 0.0f;
-#pragma unroll
-    for (int q = 0; q < ND; ++q) {
-      const int qx = q % N, qy = q / N;
-      const float W = DIM == 2 ? T.w[qx] * T.w[qy] : T.w[q];
-      float gx = a.two_dx * Ux[q], gy = a.two_dy * Uy[q];
-      float g = fmaf(gx, gx, DIM == 2 ? gy * gy : 0.0f);
-      s1 = fmaf(W, g, s1);
-      s2 = fmaf(W * Nq[q], g, s2);
-    }
-    if (s2 > 0.0f) {
-      const float f = s1 / s2;
-#pragma unroll
-      for (int q = 0; q < ND; ++q) alpha[q] = Nq[q] * f;
-    }
-  }
   if (a.troubled_out) a.troubled_out[cell] = troubled ? 1 : 0;
   if (a.alpha_out) {
-#pragma unroll
-    for (int q = 0; q < ND; ++q) a.alpha_out[cell * ND + q] = alpha[q];
+#pragma unroll 1
+    for (int q = 0; q < ND; ++q) a.alpha_out[cell * ND + q] = afac >= 0.0f ? sNq[q * NT + threadIdx.x] * afac : 1.0f;
   }
 
   // ---- (e) residual, deviation form ----------------------------------------------------------
@@ -524,151 +509,145 @@ __global__ void __launch_bounds__(TX* TY)
   const float mu = (1.0f - gam) * nu;
   // faces: neighbour traces relative to this cell's mean (ghost = own trace on a
   // transmissive side)
-  {
+  if constexpr (DIM == 1) {
     const bool hasR = a.perx || gi + 1 < nx, hasL = a.perx || gi > 0;
-    float FR[NF], FL[NF];
-    if constexpr (DIM == 1) {
-      float nbR = oR[0], nbL = oL[0];
-      if (hasR) {
-        float s = 0.0f;
+    float nbR = trR[0], nbL = trL[0];
+    if (hasR) {
+      float s = 0.0f;
 #pragma unroll
-        for (int m = 1; m < N; ++m) s += (m & 1) ? -sc[m * NH + hc + 1] : sc[m * NH + hc + 1];
-        nbR = (sc[hc + 1] - ubar) + s;
-      }
-      if (hasL) {
-        float s = 0.0f;
+      for (int m = 1; m < N; ++m) s += (m & 1) ? -sc[m * NH + hc + 1] : sc[m * NH + hc + 1];
+      nbR = (sc[hc + 1] - ubar) + s;
+    }
+    if (hasL) {
+      float s = 0.0f;
 #pragma unroll
-        for (int m = 1; m < N; ++m) s += sc[m * NH + hc - 1];
-        nbL = (sc[hc - 1] - ubar) + s;
-      }
-      FR[0] = llf_dev(law, a, ubar, oR[0], nbR, 0);
-      FL[0] = llf_dev(law, a, ubar, nbL, oL[0], 0);
+      for (int m = 1; m < N; ++m) s += sc[m * NH + hc - 1];
+      nbL = (sc[hc - 1] - ubar) + s;
+    }
+    const float FR = llf_dev(law, a, ubar, trR[0], nbR, 0);
+    const float FL = llf_dev(law, a, ubar, nbL, trL[0], 0);
 #pragma unroll
-      for (int m = 0; m < N; ++m) r[m] = -a.two_dx * (FR[0] - ((m & 1) ? -FL[0] : FL[0]));
-    } else {
-      const bool hasT = a.pery || gj + 1 < ny, hasB = a.pery || gj > 0;
-      float FT[NF], FB[NF];
-      float nR[N], nL[N], nT[N], nB[N];
+    for (int m = 0; m < N; ++m) r[m] = -a.two_dx * (FR - ((m & 1) ? -FL : FL));
+  } else {
+    // face f: 0 right (+x), 1 left, 2 top (+y), 3 bottom.  The neighbour's trace along
+    // the shared face relative to ubar, a rolled loop over the face nodes, and the
+    // projection onto the tangential modes h[j] = sum_q w_q P_j(xi_q) F_q.
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int dirn = f >> 1;          // 0: x-face, 1: y-face
+      const bool upper = (f & 1) == 0;  // right / top
+      const int off = dirn == 0 ? (upper ? 1 : -1) : (upper ? HX : -HX);
+      const bool has = dirn == 0 ? (a.perx || (upper ? gi + 1 < nx : gi > 0))
+                                 : (a.pery || (upper ? gj + 1 < ny : gj > 0));
+      const float* own = dirn == 0 ? (upper ? trR : trL) : (upper ? trT : trB);
+      float nb[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        float r0 = 0.0f, l0 = 0.0f, t0 = 0.0f, b0 = 0.0f;
+        float s = 0.0f;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-          // right neighbour's left trace (xi = -1), left neighbour's right trace (xi = +1),
-          // top neighbour's bottom trace (eta = -1), bottom neighbour's top trace (eta = +1);
-          // the neighbours' means are added after the projection onto the face nodes
-          const int mr = i + N * j, mt = j + N * i;
-          if (mr != 0) {
-            float cr = sc[mr * NH + hc + 1], cl = sc[mr * NH + hc - 1];
-            r0 += (i & 1) ? -cr : cr;
-            l0 += cl;
-          }
-          if (mt != 0) {
-            float ct = sc[mt * NH + hc + HX], cb = sc[mt * NH + hc - HX];
-            t0 += (i & 1) ? -ct : ct;
-            b0 += cb;
-          }
+          const int m = dirn == 0 ? i + N * j : j + N * i;
+          if (m == 0) continue;
+          const float v = sc[m * NH + hc + off];
+          // the neighbour meets this face with its opposite side: sign (-1)^i on a
+          // right/top face (its left/bottom side), +1 on a left/bottom face
+          s += (upper && (i & 1)) ? -v : v;
         }
-        nR[j] = r0;
-        nL[j] = l0;
-        nT[j] = t0;
-        nB[j] = b0;
+        nb[j] = s;
       }
-      const float mR = sc[hc + 1] - ubar, mL = sc[hc - 1] - ubar;
-      const float mT = sc[hc + HX] - ubar, mB = sc[hc - HX] - ubar;
+      const float dmean = has ? sc[hc + off] - ubar : 0.0f;
+      float h[N];
 #pragma unroll
+      for (int j = 0; j < N; ++j) h[j] = 0.0f;
+#pragma unroll 1
       for (int q = 0; q < N; ++q) {
-        float vr = 0.0f, vl = 0.0f, vt = 0.0f, vb = 0.0f;
+        float vo = 0.0f, vn = 0.0f;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          vr = fmaf(T.B[q][j], nR[j], vr);
-          vl = fmaf(T.B[q][j], nL[j], vl);
-          vt = fmaf(T.B[q][j], nT[j], vt);
-          vb = fmaf(T.B[q][j], nB[j], vb);
+          const float bq = sB[q * N + j];
+          vo = fmaf(bq, own[j], vo);
+          vn = fmaf(bq, nb[j], vn);
         }
-        vr = hasR ? mR + vr : oR[q];
-        vl = hasL ? mL + vl : oL[q];
-        vt = hasT ? mT + vt : oT[q];
-        vb = hasB ? mB + vb : oB[q];
-        FR[q] = llf_dev(law, a, ubar, oR[q], vr, 0);
-        FL[q] = llf_dev(law, a, ubar, vl, oL[q], 0);
-        FT[q] = llf_dev(law, a, ubar, oT[q], vt, 1);
-        FB[q] = llf_dev(law, a, ubar, vb, oB[q], 1);
-      }
-      // project the face fluxes: r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (...)
-      float hR[N], hL[N], hT[N], hB[N];
+        vn = has ? dmean + vn : vo;
+        const float F = upper ? llf_dev(law, a, ubar, vo, vn, dirn) : llf_dev(law, a, ubar, vn, vo, dirn);
+        const float wq = sW[q] * F;
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-          float wb = T.w[q] * T.B[q][j];
-          s0 = fmaf(wb, FR[q], s0);
-          s1 = fmaf(wb, FL[q], s1);
-          s2 = fmaf(wb, FT[q], s2);
-          s3 = fmaf(wb, FB[q], s3);
-        }
-        hR[j] = s0;
-        hL[j] = s1;
-        hT[j] = s2;
-        hB[j] = s3;
+        for (int j = 0; j < N; ++j) h[j] = fmaf(wq, sB[q * N + j], h[j]);
       }
+      // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
+      const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
 #pragma unroll
       for (int my = 0; my < N; ++my)
 #pragma unroll
         for (int mx = 0; mx < N; ++mx) {
-          float fxv = hR[my] - ((mx & 1) ? -hL[my] : hL[my]);
-          float fyv = hT[mx] - ((my & 1) ? -hB[mx] : hB[mx]);
-          r[mx + N * my] = -(a.two_dx * fxv + a.two_dy * fyv);
+          const int nrm = dirn == 0 ? mx : my;  // mode index along the normal
+          const float hv = dirn == 0 ? h[my] : h[mx];
+          if (upper)
+            r[mx + N * my] = fmaf(-s2d, hv, r[mx + N * my]);
+          else
+            r[mx + N * my] = fmaf(s2d, (nrm & 1) ? -hv : hv, r[mx + N * my]);
         }
     }
   }
   // volume: flux deviation and alpha-weighted viscous term, projected by sum factorisation
-  if constexpr (DIM == 1) {
+#pragma unroll 1
+  for (int qx = 0; qx < N; ++qx) {
+    float tb[NY1], td[NY1];
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
+    for (int my = 0; my < NY1; ++my) {
+      float s0 = 0.0f, sd = 0.0f;
+#pragma unroll
+      for (int mx = 0; mx < N; ++mx) {
+        const float cm = (mx + N * my) ? c[mx + N * my] : 0.0f;
+        s0 = fmaf(sB[qx * N + mx], cm, s0);
+        sd = fmaf(sBd[qx * N + mx], cm, sd);
+      }
+      tb[my] = s0;
+      td[my] = sd;
+    }
+    float hx[NY1], hy[NY1];
+#pragma unroll
+    for (int my = 0; my < NY1; ++my) hx[my] = hy[my] = 0.0f;
+    const float wx = sW[qx];
+#pragma unroll 1
+    for (int qy = 0; qy < NY1; ++qy) {
+      float du = tb[0], ux = td[0], uy = 0.0f;
+      if constexpr (DIM == 2) {
+        du = ux = 0.0f;
+#pragma unroll
+        for (int my = 0; my < N; ++my) {
+          const float bq = sB[qy * N + my], dq = sBd[qy * N + my];
+          du = fmaf(bq, tb[my], du);
+          ux = fmaf(bq, td[my], ux);
+          uy = fmaf(dq, tb[my], uy);
+        }
+      }
       float fx, fy;
-      law.flux_dev(dU[q], fx, fy);
-      float G = T.w[q] * (fx - mu * alpha[q] * a.two_dx * Ux[q]);
+      law.flux_dev(du, fx, fy);
+      const float al = afac >= 0.0f ? sNq[(qx + N * qy) * NT + threadIdx.x] * afac : 1.0f;
+      const float W = DIM == 2 ? wx * sW[qy] : wx;
+      const float gx = W * (fx - mu * al * a.two_dx * ux);
+      if constexpr (DIM == 2) {
+        const float gy = W * (fy - mu * al * a.two_dy * uy);
 #pragma unroll
-      for (int m = 1; m < N; ++m) r[m] = fmaf(a.two_dx * T.Bd[q][m], G, r[m]);
-    }
-  } else {
-#pragma unroll
-    for (int qx = 0; qx < N; ++qx) {
-      float Gx[N], Gy[N];
-#pragma unroll
-      for (int qy = 0; qy < N; ++qy) {
-        const int q = qx + N * qy;
-        float fx, fy;
-        law.flux_dev(dU[q], fx, fy);
-        const float W = T.w[qx] * T.w[qy];
-        Gx[qy] = W * (fx - mu * alpha[q] * a.two_dx * Ux[q]);
-        Gy[qy] = W * (fy - mu * alpha[q] * a.two_dy * Uy[q]);
-      }
-      float hx[N], hy[N];
-#pragma unroll
-      for (int my = 0; my < N; ++my) {
-        float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-        for (int qy = 0; qy < N; ++qy) {
-          s0 = fmaf(T.B[qy][my], Gx[qy], s0);
-          s1 = fmaf(T.Bd[qy][my], Gy[qy], s1);
+        for (int my = 0; my < N; ++my) {
+          hx[my] = fmaf(sB[qy * N + my], gx, hx[my]);
+          hy[my] = fmaf(sBd[qy * N + my], gy, hy[my]);
         }
-        hx[my] = s0;
-        hy[my] = s1;
+      } else {
+        hx[0] = gx;
       }
-#pragma unroll
-      for (int my = 0; my < N; ++my)
-#pragma unroll
-        for (int mx = 0; mx < N; ++mx) {
-          if (mx + my == 0) continue;
-          float v = r[mx + N * my];
-          v = fmaf(a.two_dx * T.Bd[qx][mx], hx[my], v);
-          v = fmaf(a.two_dy * T.B[qx][mx], hy[my], v);
-          r[mx + N * my] = v;
-        }
     }
+#pragma unroll
+    for (int my = 0; my < NY1; ++my)
+#pragma unroll
+      for (int mx = 0; mx < N; ++mx) {
+        if (mx + my == 0) continue;
+        float v = r[mx + N * my];
+        v = fmaf(a.two_dx * sBd[qx * N + mx], hx[my], v);
+        if constexpr (DIM == 2) v = fmaf(a.two_dy * sB[qx * N + mx], hy[my], v);
+        r[mx + N * my] = v;
+      }
   }
   // M^{-1} and output
   bool bad = false;

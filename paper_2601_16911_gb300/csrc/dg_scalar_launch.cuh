@@ -8,9 +8,7 @@ namespace cvw {
 template <int DIM, int P, int SYS, int TX, int TY>
 cudaError_t launch_scalar(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
   using Tb = DgTables<DIM, P>;
-  constexpr int HX = TX + 2, HY = DIM == 2 ? TY + 2 : 1;
-  constexpr int VXT = TX + 1, VYT = DIM == 2 ? TY + 1 : 1;
-  constexpr size_t smem = sizeof(float) * Tb::ND * (size_t)(HX * HY + VXT * VYT);
+  constexpr size_t smem = TileLayout<DIM, P, TX, TY>::BYTES;
   static_assert(smem <= 200 * 1024, "tile too large for shared memory");
   auto kern = dg_scalar_stage<DIM, P, SYS, TX, TY>;
   if (smem > 48 * 1024) {

@@ -118,13 +118,59 @@ def test_conservation_many_steps():
     mesh.close()
 
 
-def test_euler_not_yet_supported_or_runs():
-    d, ic = I.euler_quadrants(0, n=16, degree=2)
-    try:
-        mesh = cv.Mesh(d)
-    except cv.CvwenoError as e:
-        assert e.code == cv.ERR_UNSUPPORTED
-        return
+def window(d, u, i0, j0, w, h):
+    """Sub-mesh around the w x h block of cells starting at (i0, j0): the block plus a
+    one-cell ring, except along a transmissive domain side, where the sub-mesh's own
+    transmissive side coincides with the domain's.  The residual of a cell depends only
+    on its 3x3 neighbourhood, so the oracle's residual of the block on the sub-mesh
+    equals the full mesh's."""
+    nx, ny = d["nx"], d["ny"]
+    dx = (d["x1"] - d["x0"]) / nx
+    dy = (d["y1"] - d["y0"]) / ny
+    px, py = d["bc"][0] == I.PERIODIC, d["bc"][2] == I.PERIODIC
+    lx = i0 - 1 if (px or i0 > 0) else i0
+    hx = i0 + w + 1 if (px or i0 + w < nx) else i0 + w
+    ly = j0 - 1 if (py or j0 > 0) else j0
+    hy = j0 + h + 1 if (py or j0 + h < ny) else j0 + h
+    sub = dict(d, nx=hx - lx, ny=hy - ly, bc=(I.TRANSMISSIVE,) * 4, x0=d["x0"] + lx * dx, x1=d["x0"] + hx * dx,
+               y0=d["y0"] + ly * dy, y1=d["y0"] + hy * dy)
+    ii, jj = np.arange(lx, hx) % nx, np.arange(ly, hy) % ny
+    cells = (jj[:, None] * nx + ii[None, :]).reshape(-1)
+    bi, bj = np.arange(i0, i0 + w), np.arange(j0, j0 + h)
+    inner = (bj[:, None] * nx + bi[None, :]).reshape(-1)
+    sub_inner = ((bj - ly)[:, None] * (hx - lx) + (bi - lx)[None, :]).reshape(-1)
+    return sub, u[:, cells, :], inner, sub_inner
+
+
+def test_euler_full_size_stage_sampled_windows():
+    """512 x 512 DG Q3 Euler quadrants, one stage on the full mesh; the oracle checks
+    sampled 10x10 blocks (including the quadrant interfaces and the centre) exactly."""
+    d, ic = I.euler_quadrants(0, n=512, degree=3)
+    mesh = cv.Mesh(d)
+    u = mesh.project(*ic)
+    out = mesh.residual_ex(u)
+    mesh.status_check()
+    ug = u.cpu().numpy().astype(np.float64)
+    r = out["dudt"].cpu().numpy()
+    scale = np.abs(r).max()
+    for (i0, j0) in [(251, 251), (100, 251), (251, 400), (37, 37), (480, 100), (0, 0), (502, 502)]:
+        sub, us, inner, sub_inner = window(d, ug, i0, j0, 10, 10)
+        ref = O.residual(sub, us)
+        err = np.abs(r[:, inner, :] - ref["dudt"][:, sub_inner, :]).max() / scale
+        assert err < RES_TOL, (i0, j0, err)
+    mesh.close()
+
+
+def test_euler_positivity_status():
+    """A negative density in the input raises the positivity status (no trap)."""
+    d, ic = I.euler_quadrants(2, n=32, degree=2)
+    mesh = cv.Mesh(d)
+    u = mesh.project(*ic)
+    u[0, 300, 0] = -1.0
+    mesh.residual(u)
+    with pytest.raises(cv.CvwenoError) as ei:
+        mesh.status_check()
+    assert ei.value.code == cv.ERR_POSITIVITY
     mesh.close()
 
 

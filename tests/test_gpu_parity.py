@@ -41,6 +41,12 @@ def case(name):
     if name == "linadv_circle":
         d = I.mesh(2, 17, 9, degree=2, system=I.LINADV, adv_vx=0.7, adv_vy=-0.4)
         return d, (I.IC_CIRCLE, [0.4, 0.5, 0.3, 2.0, -1.0])
+    if name.startswith("euler_p"):
+        p = int(name[-1])
+        return I.euler_quadrants(4, n=20, degree=p)
+    if name == "euler_wave":
+        d = I.mesh(2, 18, 11, degree=2, system=I.EULER)
+        return d, (I.IC_DENSITY_WAVE, [0.3, 1.0, 2.0, 0.7, -0.4, 0.9])
     if name.startswith("tiny"):
         nx, ny, bc = {"tiny11p": (1, 1, I.PERIODIC), "tiny23p": (2, 3, I.PERIODIC),
                       "tiny31t": (3, 1, I.TRANSMISSIVE), "tiny22t": (2, 2, I.TRANSMISSIVE)}[name]
@@ -57,7 +63,8 @@ def initial(d, ic):
 
 
 ALL = (["burgers1d_cfg1"] + [f"burgers1d_p{p}" for p in (1, 3, 4)] + [f"kpp_p{p}" for p in (1, 2, 3, 4)]
-       + ["burgers2d_p2", "burgers2d_p3", "linadv_circle", "tiny11p", "tiny23p", "tiny31t", "tiny22t"])
+       + ["burgers2d_p2", "burgers2d_p3", "linadv_circle", "tiny11p", "tiny23p", "tiny31t", "tiny22t"]
+       + ["euler_p1", "euler_p2", "euler_p3", "euler_p4", "euler_wave"])
 
 
 @pytest.mark.parametrize("name", ALL)
@@ -143,7 +150,7 @@ def test_sensor_entry_point_matches_full_stage(name):
     mesh.close()
 
 
-@pytest.mark.parametrize("name", ["kpp_p2", "burgers1d_cfg1", "linadv_circle", "burgers2d_p3"])
+@pytest.mark.parametrize("name", ["kpp_p2", "burgers1d_cfg1", "linadv_circle", "burgers2d_p3", "euler_p3"])
 def test_ssprk3_step_parity(name):
     d, ic = case(name)
     u = rounded(initial(d, ic))
