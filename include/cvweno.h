@@ -32,6 +32,11 @@
  *     entry point) reads and clears.
  *   - A mesh owns its tables and scratch (two stage buffers of the state size).
  *     Calls on one mesh must not overlap on different streams.
+ *   - CG meshes (kind CVWENO_CG) hold nodal values at the Gauss-Lobatto nodes instead:
+ *     u[var][node] (see cvweno_state_size); the sensor and the SC weights are
+ *     computed per cell exactly as for DG.  CG residual: Sec. 2.2 (CG form of eq. stab),
+ *     P_h by the lumped-mass L2 projection, M^{-1} by the lumped mass with two
+ *     defect-correction sweeps.
  */
 #ifndef CVWENO_H
 #define CVWENO_H
@@ -93,7 +98,8 @@ typedef struct {
   int dim;              /* 1 or 2 */
   int nx, ny;           /* cells per direction (ny ignored in 1D) */
   int degree;           /* p in 1..4 */
-  int kind;             /* CVWENO_DG (CG returns CVWENO_ERR_UNSUPPORTED) */
+  int kind;             /* CVWENO_DG, or CVWENO_CG (scalar laws, periodic meshes; state =
+                           values at the GLL nodes, see cvweno_state_size) */
   int system;           /* CVWENO_BURGERS | KPP | LINADV | EULER (KPP, EULER: 2D only) */
   int bc[4];            /* x-low, x-high, y-low, y-high: PERIODIC or TRANSMISSIVE;
                            periodic sides must come in pairs */
@@ -106,8 +112,9 @@ void cvweno_default_params(cvweno_params* p);
 
 /* Build the mesh: host tables (vertex patches, colouring), basis tabulations in
  * FP64 rounded once to FP32, device scratch.  desc and out are host pointers.
- * Returns ERR_ARG for inconsistent sizes/sides, ERR_UNSUPPORTED for CG, degree > 4,
- * 1D Euler/KPP or a non-integer r.  Makes the current device the mesh's device. */
+ * Returns ERR_ARG for inconsistent sizes/sides, ERR_UNSUPPORTED for degree > 4, 1D
+ * Euler/KPP, CG with Euler or a transmissive side, or a non-integer r.  Records the
+ * current device as the mesh's device. */
 cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* desc, cvweno_mesh* out);
 
 /* Free everything the mesh owns (synchronises its device).  NULL is accepted. */
@@ -118,6 +125,11 @@ cvweno_status cvweno_mesh_destroy(cvweno_mesh m);
  * their vertices), quadrature points per cell ((p+1)^dim Gauss-Legendre). */
 cvweno_status cvweno_mesh_info(cvweno_mesh m, int64_t* ncells, int64_t* ndof_per_var, int* nvars,
                                int64_t* nverts, int* nquad);
+
+/* Number of floats of one state (host out-pointer): nvars * ncells * (p+1)^dim for DG,
+ * nvars * (p nx) * (p ny) nodal values for CG (GLL nodes of the periodic lattice,
+ * node I + (p nx) J). */
+cvweno_status cvweno_state_size(cvweno_mesh m, int64_t* nstate);
 
 /* Host copies of the integer mesh tables (host arrays, each may be NULL):
  *   cell_vertices[ncells][2^dim]  vertex of corner c = cx + 2 cy of each cell
@@ -179,6 +191,69 @@ cvweno_status cvweno_max_wavespeed(cvweno_mesh m, const float* u, double* lam, v
 
 /* Synchronise the stream, read and clear the mesh's device status word. */
 cvweno_status cvweno_status_check(cvweno_mesh m, void* stream);
+
+/* ---- batches of independent problems ------------------------------------------------
+ * Many independent 2D DG meshes of uneven size and degree advanced together: each
+ * SSP-RK3 stage of the whole batch is one persistent launch (or one per degree present),
+ * and cvweno_batch_advance replays a captured CUDA graph of one step.  The per-mesh
+ * arithmetic is that of cvweno_residual / cvweno_step on the same mesh; only the work
+ * distribution differs.  The paper advances one problem at a time; batching is a
+ * deployment form of its stage (a)-(e) residual.
+ *
+ * The state of instance k is u[offsets[k] .. offsets[k+1]) of ONE device array, in the
+ * state layout of that instance's mesh (cvweno_state_size). */
+typedef struct cvweno_batch_s* cvweno_batch;
+
+enum { CVWENO_BATCH_FUSED = 0, CVWENO_BATCH_GROUPED = 1 };
+
+/* Launch shape of a batch stage.  schedule: FUSED = one launch per stage whose CTAs
+ * take tiles of every degree; GROUPED = one launch per degree present, forked onto
+ * concurrent streams.  tile: 0 = 16x8 cells per CTA, 1 = 8x8.  dynamic: 1 = CTAs claim
+ * tiles from a device counter (reset by the last CTA to leave), 0 = static
+ * round-robin.  ctas_per_sm: persistent grid = ctas_per_sm x SM count, 0 = as many as
+ * fit.  use_graph: cvweno_batch_advance replays a captured graph of one step.
+ * ms (output of cvweno_batch_autotune): measured time of one residual pass. */
+typedef struct {
+  int schedule;
+  int tile;
+  int dynamic;
+  int ctas_per_sm;
+  int use_graph;
+  float ms;
+} cvweno_batch_plan;
+
+/* Create a batch of count >= 1 meshes from descs[count] (host).  Every desc must be
+ * 2D, DG, the same scalar system (BURGERS only in this build), degree 1..4, with
+ * square cells (dx == dy, so that one set of reference tabulations serves each
+ * degree); other checks are those of cvweno_mesh_create.  Default plan: FUSED, 16x8,
+ * dynamic, ctas_per_sm 0, use_graph 1.  Records the current device. */
+cvweno_status cvweno_batch_create(const cvweno_mesh_desc* descs, int count, cvweno_batch* out);
+cvweno_status cvweno_batch_destroy(cvweno_batch b);
+
+/* offsets[count + 1] (host): start of each instance's state in the batch state array;
+ * offsets[count] is the total length in floats. */
+cvweno_status cvweno_batch_offsets(cvweno_batch b, int64_t* offsets);
+
+/* Replace the launch shape; ERR_ARG for a field out of range. */
+cvweno_status cvweno_batch_set_plan(cvweno_batch b, const cvweno_batch_plan* plan);
+cvweno_status cvweno_batch_get_plan(cvweno_batch b, cvweno_batch_plan* plan);
+
+/* Time every launch shape on the residual of state u (device, not modified) and keep
+ * the fastest; *best (host, may be NULL) receives it.  Synchronises; not capturable. */
+cvweno_status cvweno_batch_autotune(cvweno_batch b, const float* u, cvweno_batch_plan* best, void* stream);
+
+/* dudt of every instance (stages (a)-(e) and M^-1), same layout as u; one stage launch
+ * (or one per degree).  Enqueued without synchronisation. */
+cvweno_status cvweno_batch_residual(cvweno_batch b, const float* u, float* dudt, void* stream);
+
+/* nsteps SSP-RK3 steps of every instance in place, instance k with step dt[k] > 0
+ * (host array of count).  Enqueued without synchronisation; with use_graph the first
+ * call for a given u captures and instantiates the step graph. */
+cvweno_status cvweno_batch_advance(cvweno_batch b, float* u, const double* dt, int nsteps, void* stream);
+
+/* Synchronise, read and clear the per-instance status words.  *first_bad (host, may be
+ * NULL) receives the lowest instance index with a raised status, or -1. */
+cvweno_status cvweno_batch_status_check(cvweno_batch b, int* first_bad, void* stream);
 
 /* One SSP-RK3 step of fixed size dt > 0, in place on the caller's state u (device,
  * state layout of desc), that allocates nothing -- for callers that cannot allocate

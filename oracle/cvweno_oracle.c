@@ -370,10 +370,14 @@ static void or_cg_gather(const or_mesh* m, const double* u, double* uc) {
             u[(size_t)v * m->nnode + or_cg_node(m, e, mi % m->n, mi / m->n)];
 }
 
-/* D^k u^e at (xi, eta) for one variable's coefficient block c[nd]. */
+/* D^k u^e at (xi, eta) for one variable's coefficient block c[nd].  For the nodal CG
+ * basis a derivative (k != 0) is taken of the differences c_a - c_0: the derivative
+ * weights of the Lagrange basis sum to zero, so this is the same derivative, and a
+ * constant cell gets exactly zero derivatives. */
 static double or_du(const or_mesh* m, const double* c, int kx, int ky, double xi, double eta) {
   double s = 0.0;
-  for (int mi = 0; mi < m->nd; ++mi) s += c[mi] * or_dphi(m, mi, kx, ky, xi, eta);
+  const double ref = (m->kind == OR_CG && kx + ky > 0) ? c[0] : 0.0;
+  for (int mi = 0; mi < m->nd; ++mi) s += (c[mi] - ref) * or_dphi(m, mi, kx, ky, xi, eta);
   return s;
 }
 

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcvweno.so")
-SOURCES = ["tables.cpp", "api.cu", "dg_scalar_1d.cu", "dg_scalar_2d.cu", "dg_euler.cu", "noalloc.cu"]
+SOURCES = ["tables.cpp", "api.cu", "dg_scalar_1d.cu", "dg_scalar_2d.cu", "dg_euler.cu", "cg_scalar.cu", "noalloc.cu",
+           "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -32,6 +33,7 @@ def _nvcc() -> str:
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    files.append(os.path.abspath(__file__))  # a change of the source list or flags
     return files
 
 

@@ -128,7 +128,42 @@ __global__ void project_kernel(const __grid_constant__ ProjArgs a, const __grid_
   }
 }
 
+// CG: interpolation at the GLL nodes of the periodic lattice (reading A25)
+__global__ void project_cg_kernel(const __grid_constant__ ProjArgs a, const __grid_constant__ ProjTables T,
+                                  int p, int nnx, int nny, const float* __restrict__ xg_dev) {
+  (void)T;
+  const int64_t nn = (int64_t)nnx * nny;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(j % nnx), J = (int)(j / nnx);
+    const int i = I / p, ai = I % p, jj = J / p, bj = J % p;
+    const float x = (float)(a.x0 + (i + 0.5) * a.dx + 0.5 * a.dx * xg_dev[ai]);
+    const float y = a.dim == 2 ? (float)(a.y0 + (jj + 0.5) * a.dy + 0.5 * a.dy * xg_dev[bj]) : 0.0f;
+    float U[4];
+    ic_eval(a, x, y, U);
+    a.u[j] = U[0];
+  }
+}
+
 // ---- FP64 reductions --------------------------------------------------------------------
+
+// CG: partial sums of ML_j u_j (FP64) with the lumped mass of each lattice node
+__global__ void sum_cg_partial(const float* __restrict__ u, int nnx, int nny, int p, const double* __restrict__ ml1x,
+                               const double* __restrict__ ml1y, double* __restrict__ partial) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0.0;
+  const int64_t nn = (int64_t)nnx * nny;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(j % nnx), J = (int)(j / nnx);
+    acc += ml1x[I % p] * ml1y[J % p] * (double)u[j];
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
 
 // partial[b] = sum over a grid-stride slice of x[i * stride] (FP64), fixed order per block
 __global__ void sum_mode0_partial(const float* __restrict__ x, int64_t n, int stride, double* __restrict__ partial) {
@@ -198,10 +233,18 @@ StageArgs base_args(const cvweno_mesh_s* m) {
   a.adv_vy = (float)p.adv_vy;
   a.gas_gamma = (float)p.gas_gamma;
   a.rk_b = 1.0f;
+  a.nnx = m->nnx;
+  a.nny = m->nny;
+  a.rloc = m->d_rloc;
+  a.rnode = m->d_r;
+  a.du = m->d_du;
+  a.mloc = m->d_mloc;
+  a.ubar = m->d_ubar;
   return a;
 }
 
 cudaError_t launch(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
+  if (m->kind == CVWENO_CG) return launch_stage_cg(m, a, s);
   return m->desc.system == CVWENO_EULER ? launch_stage_euler(m, a, s) : launch_stage(m, a, s);
 }
 
@@ -242,6 +285,10 @@ cvweno_status enqueue_step(cvweno_mesh m, float* u, float dt, cudaStream_t s) {
 
 }  // namespace
 
+namespace cvw {
+StageArgs stage_base_args(const cvweno_mesh_s* m) { return base_args(m); }
+}  // namespace cvw
+
 extern "C" {
 
 void cvweno_default_params(cvweno_params* p) {
@@ -281,12 +328,20 @@ cvweno_status cvweno_mesh_destroy(cvweno_mesh m) {
   cudaFree(m->d_lambda);
   cudaFree(m->d_red);
   cudaFree(m->d_status);
+  cudaFree(m->d_rloc);
+  cudaFree(m->d_r);
+  cudaFree(m->d_du);
+  cudaFree(m->d_mloc);
+  cudaFree(m->d_ubar);
+  cudaFree(m->d_cg_xg);
+  cudaFree(m->d_cg_ml);
   cudaFreeHost(m->h_status);
   cudaFreeHost(m->h_red);
   free(m->cell_vertices);
   free(m->vertex_cells);
   free(m->colour);
   free(m->tables);
+  free(m->cg_tables);
   free(m);
   return CVWENO_OK;
 }
@@ -307,7 +362,11 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   if (!(p.eps > 0.0) || !(p.q >= 1.0) || !(p.gamma_vertex > 0.0) || (1 << d->dim) * p.gamma_vertex >= 1.0)
     return CVWENO_ERR_ARG;
   if (p.sensor_mode < 0 || p.sensor_mode > 2) return CVWENO_ERR_ARG;
-  if (d->kind != CVWENO_DG) return CVWENO_ERR_UNSUPPORTED;
+  if (d->kind != CVWENO_DG && d->kind != CVWENO_CG) return CVWENO_ERR_ARG;
+  // CG: scalar laws on periodic meshes (no boundary flux term is implemented)
+  if (d->kind == CVWENO_CG && (d->system == CVWENO_EULER || d->bc[0] != CVWENO_PERIODIC ||
+                               (d->dim == 2 && d->bc[2] != CVWENO_PERIODIC)))
+    return CVWENO_ERR_UNSUPPORTED;
   if (d->degree < 1 || d->degree > kMaxP) return CVWENO_ERR_UNSUPPORTED;
   if (p.r != floor(p.r) || p.r < 1.0 || p.r > 8.0) return CVWENO_ERR_UNSUPPORTED;
   if ((d->system == CVWENO_KPP || d->system == CVWENO_EULER) && d->dim != 2) return CVWENO_ERR_UNSUPPORTED;
@@ -329,7 +388,11 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   m->vy = d->dim == 2 ? (d->bc[2] == CVWENO_PERIODIC ? m->ny : m->ny + 1) : 1;
   m->ncell = (int64_t)m->nx * m->ny;
   m->nvert = (int64_t)m->vx * m->vy;
-  m->nstate = m->ncell * m->nd * m->nvar;
+  m->kind = d->kind;
+  m->nnx = d->kind == CVWENO_CG ? m->p * m->nx : 0;
+  m->nny = d->kind == CVWENO_CG ? (d->dim == 2 ? m->p * m->ny : 1) : 0;
+  m->nnode = (int64_t)m->nnx * m->nny;
+  m->nstate = d->kind == CVWENO_CG ? m->nnode * m->nvar : m->ncell * m->nd * m->nvar;
   m->dx = (d->x1 - d->x0) / m->nx;
   m->dy = d->dim == 2 ? (d->y1 - d->y0) / m->ny : 1.0;
   m->h = d->dim == 2 ? sqrt(m->dx * m->dx + m->dy * m->dy) : m->dx;
@@ -341,6 +404,27 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->d_u1, sbytes);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_u2, sbytes);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_lambda, sizeof(float) * (size_t)m->ncell);
+  if (m->kind == CVWENO_CG) {
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_rloc, sizeof(float) * (size_t)m->ncell * m->nd);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_mloc, sizeof(float) * (size_t)m->ncell * m->nd);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_ubar, sizeof(float) * (size_t)m->ncell);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_r, sizeof(float) * (size_t)m->nnode);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_du, sizeof(float) * (size_t)m->nnode);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_cg_xg, sizeof(float) * (kMaxP + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_cg_ml, sizeof(double) * 2 * (kMaxP + 1));
+    if (e == cudaSuccess) {
+      float xg[kMaxP + 1];
+      double ml[2 * (kMaxP + 1)];
+      for (int i = 0; i <= kMaxP; ++i) {
+        xg[i] = i <= m->p ? (float)m->cg_xg[i] : 0.0f;
+        const double w = i <= m->p ? m->cg_wl[i] * (i == 0 ? 2.0 : 1.0) : 0.0;  // vertex nodes: two cells
+        ml[i] = w * 0.5 * m->dx;
+        ml[kMaxP + 1 + i] = m->dim == 2 ? w * 0.5 * m->dy : 1.0;
+      }
+      e = cudaMemcpy(m->d_cg_xg, xg, sizeof(xg), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(m->d_cg_ml, ml, sizeof(ml), cudaMemcpyHostToDevice);
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&m->d_red, sizeof(double) * (kRedBlocks + 8));
   if (e == cudaSuccess) e = cudaMalloc(&m->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->d_status, 0, sizeof(int));
@@ -362,6 +446,12 @@ cvweno_status cvweno_mesh_info(cvweno_mesh m, int64_t* ncells, int64_t* ndof, in
   if (nvars) *nvars = m->nvar;
   if (nverts) *nverts = m->nvert;
   if (nquad) *nquad = m->nq;
+  return CVWENO_OK;
+}
+
+cvweno_status cvweno_state_size(cvweno_mesh m, int64_t* nstate) {
+  if (!m || !nstate) return CVWENO_ERR_ARG;
+  *nstate = m->nstate;
   return CVWENO_OK;
 }
 
@@ -408,6 +498,12 @@ cvweno_status cvweno_project(cvweno_mesh m, int ic_type, const double* ic_params
       legendre_values(x[q], kMaxP, pv);
       for (int mm = 0; mm <= kMaxP; ++mm) T.P[q][mm] = (float)pv[mm];
     }
+  }
+  if (m->kind == CVWENO_CG) {
+    int blocks = (int)((m->nnode + 255) / 256);
+    if (blocks > 65535) blocks = 65535;
+    project_cg_kernel<<<blocks, 256, 0, S(stream)>>>(a, T, m->p, m->nnx, m->nny, m->d_cg_xg);
+    return cuda_status(cudaGetLastError());
   }
   int blocks = (int)((m->ncell + 127) / 128);
   if (blocks > 65535) blocks = 65535;
@@ -503,6 +599,18 @@ cvweno_status cvweno_advance(cvweno_mesh m, float* u, double dt, int nsteps, voi
 cvweno_status cvweno_mass_total(cvweno_mesh m, const float* u, double* totals, void* stream) {
   if (!m || !u || !totals) return CVWENO_ERR_ARG;
   cudaStream_t s = S(stream);
+  if (m->kind == CVWENO_CG) {
+    // sum_j ML_j u_j with ML_j = ml1x(I mod p) ml1y(J mod p)
+    sum_cg_partial<<<kRedBlocks, kRedThreads, 0, s>>>(u, m->nnx, m->nny, m->p, m->d_cg_ml, m->d_cg_ml + (kMaxP + 1),
+                                                     m->d_red);
+    finish_reduce<<<1, kRedThreads, 0, s>>>(m->d_red, kRedBlocks, 0, m->d_red + kRedBlocks);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_red, m->d_red + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return CVWENO_ERR_CUDA;
+    totals[0] = m->h_red[0];
+    return CVWENO_OK;
+  }
   // int_{K_e} u_h = |K_e| * (Legendre mode 0)
   const double vol = m->dim == 2 ? m->dx * m->dy : m->dx;
   for (int v = 0; v < m->nvar; ++v) {

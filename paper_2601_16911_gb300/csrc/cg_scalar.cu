@@ -1,0 +1,566 @@
+// Continuous Galerkin (CG) stage for scalar conservation laws on periodic meshes.
+//
+// State: values at the Gauss-Lobatto-Legendre nodes of the global lattice
+// (p nx) x (p ny), node I + (p nx) J.  One RK stage is
+//   K1 cg_stage_cells   tile of cells + one-cell halo: nodal -> Legendre modes, the same
+//                       vertex phase and cell sensor as DG (stages a-c), the lumped-mass
+//                       projection P_h grad u at the cell's own nodes (reading A13, from
+//                       the local integrals of the tile and halo cells), the CG SC weights
+//                       with f_q = |grad u|^2 - gamma grad u . P_h grad u (Sec. 4; A24),
+//                       and the cell-local residual
+//                       int grad phi . f(u) - nu_e sum_q alpha_q w_q grad phi . (grad u - gamma P_h grad u)
+//                       (Sec. 2.2, CG form of eq. stab)
+//   K2 cg_node_rhs      deterministic nodal assembly r_j and du = r_j / ML_j
+//   K3 cg_cell_mass     consistent mass times du, per cell
+//   K4 cg_node_correct  du += ML^{-1}(r - M_C du) (reading A12); the second sweep also
+//                       writes the SSP-RK3 combination (or du itself for a residual)
+// with K3/K4 run twice.  Nodal sums gather the cells around a node in a fixed order.
+#include "dg_scalar_kernel.cuh"
+
+namespace cvw {
+namespace {
+
+template <int DIM, int P, int TX, int TY>
+struct CgLayout {
+  using L = TileLayout<DIM, P, TX, TY>;
+  static constexpr int N = P + 1, ND = L::ND, NH = L::NH;
+  static constexpr int NNX = P * (TX + 2) + 1, NNY = DIM == 2 ? P * (TY + 2) + 1 : 1;
+  static constexpr int OFF_NODE = L::FLOATS;              // [NNY][NNX] nodal values
+  static constexpr int OFF_BX = OFF_NODE + NNX * NNY;     // [ND][NH] int phi_a d_x u
+  static constexpr int OFF_BY = OFF_BX + ND * NH;         // [ND][NH] int phi_a d_y u
+  static constexpr int FLOATS = OFF_BY + ND * NH;
+  static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
+};
+
+// lumped mass of a 1D lattice node with local index a in [0, p): its GLL weight times
+// dx/2, counted twice at cell vertices (two cells share them)
+template <int DIM, int P>
+__device__ __forceinline__ float ml1(const CgTables<DIM, P>& C, int a, float h) {
+  return (a == 0 ? 2.0f : 1.0f) * C.wl[a] * h;
+}
+
+template <int DIM, int P, int SYS, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__ StageArgs a,
+                                                          const __grid_constant__ DgTables<DIM, P> T,
+                                                          const __grid_constant__ CgTables<DIM, P> C) {
+  using L = TileLayout<DIM, P, TX, TY>;
+  using G = CgLayout<DIM, P, TX, TY>;
+  using Law = ScalarLaw<SYS, DIM>;
+  constexpr int N = L::N, ND = L::ND, NT = L::NT, HX = L::HX, NH = L::NH;
+  constexpr int NNX = G::NNX, NNY = G::NNY;
+  constexpr int NY1 = DIM == 2 ? N : 1;
+  extern __shared__ __align__(16) float smem[];
+  float* sc = smem + L::OFF_SC;
+  float* st = smem + L::OFF_ST;
+  const float* sA = smem + L::OFF_A;
+  const float* sB = smem + L::OFF_B;
+  const float* sBd = smem + L::OFF_BD;
+  const float* sBk = smem + L::OFF_BK;
+  const float* sW = smem + L::OFF_W;
+  float* sNq = smem + L::OFF_NQ;
+  float* snode = smem + G::OFF_NODE;
+  float* sbx = smem + G::OFF_BX;
+  float* sby = smem + G::OFF_BY;
+
+  const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
+  const int nnx = a.nnx, nny = DIM == 2 ? a.nny : 1;
+  const int i0 = blockIdx.x * TX, j0 = DIM == 2 ? blockIdx.y * TY : 0;
+  const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
+
+  // ---- nodal values of the tile and its halo (periodic lattice) -------------------------
+  {
+    const int I0 = P * (i0 - 1), J0 = DIM == 2 ? P * (j0 - 1) : 0;
+    for (int f = threadIdx.x; f < NNX * NNY; f += NT) {
+      const int ix = f % NNX, iy = f / NNX;
+      const int I = ((I0 + ix) % nnx + nnx) % nnx;
+      const int J = DIM == 2 ? ((J0 + iy) % nny + nny) % nny : 0;
+      snode[f] = __ldg(a.u_in + (size_t)J * nnx + I);
+    }
+  }
+  stage_tables_to_smem<DIM, P, TX, TY>(T, smem);
+  __syncthreads();
+  // ---- every halo cell: nodal -> Legendre modes c = (V x V) u_loc -------------------------
+  // The transform is applied to u_loc - u_ref (u_ref = the cell's first node): every mode
+  // but the mean is unchanged (the rows of V beyond the mean sum to zero), the mean gets
+  // u_ref back, and a constant cell yields exactly zero non-mean modes.
+  for (int h = threadIdx.x; h < NH; h += NT) {
+    const int hx = h % HX, hy = DIM == 2 ? h / HX : 0;
+    float ul[ND];
+#pragma unroll
+    for (int b = 0; b < NY1; ++b)
+#pragma unroll
+      for (int aa = 0; aa < N; ++aa) ul[aa + N * b] = snode[(P * hx + aa) + NNX * (P * hy + b)];
+    const float uref = ul[0];
+#pragma unroll
+    for (int m = 0; m < ND; ++m) ul[m] -= uref;
+    float tmp[N][NY1];  // [mx][b]
+#pragma unroll
+    for (int mx = 0; mx < N; ++mx)
+#pragma unroll
+      for (int b = 0; b < NY1; ++b) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int aa = 0; aa < N; ++aa) acc = fmaf(C.V[mx][aa], ul[aa + N * b], acc);
+        tmp[mx][b] = acc;
+      }
+#pragma unroll
+    for (int my = 0; my < NY1; ++my)
+#pragma unroll
+      for (int mx = 0; mx < N; ++mx) {
+        float acc = tmp[mx][0];
+        if constexpr (DIM == 2) {
+          acc = 0.0f;
+#pragma unroll
+          for (int b = 0; b < N; ++b) acc = fmaf(C.V[my][b], tmp[mx][b], acc);
+        }
+        sc[(mx + N * my) * NH + h] = (mx + my == 0) ? acc + uref : acc;
+      }
+  }
+  __syncthreads();
+  // ---- (a)+(b) vertex candidates (shared with DG) ---------------------------------------
+  tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
+  // ---- P_h local integrals b_a = int phi_a grad u for every halo cell ------------------------
+  for (int h = threadIdx.x; h < NH; h += NT) {
+    float c[ND];
+#pragma unroll
+    for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + h];
+    float bx[ND], by[ND];
+#pragma unroll
+    for (int m = 0; m < ND; ++m) bx[m] = by[m] = 0.0f;
+#pragma unroll 1
+    for (int qx = 0; qx < N; ++qx) {
+      float tb[NY1], td[NY1];
+#pragma unroll
+      for (int my = 0; my < NY1; ++my) {
+        float s0 = 0.0f, sd = 0.0f;
+#pragma unroll
+        for (int mx = 0; mx < N; ++mx) {
+          s0 = fmaf(sB[qx * N + mx], c[mx + N * my], s0);
+          sd = fmaf(sBd[qx * N + mx], c[mx + N * my], sd);
+        }
+        tb[my] = s0;
+        td[my] = sd;
+      }
+      float hx_[NY1], hy_[NY1];
+#pragma unroll
+      for (int b = 0; b < NY1; ++b) hx_[b] = hy_[b] = 0.0f;
+#pragma unroll
+      for (int qy = 0; qy < NY1; ++qy) {
+        float gx = td[0], gy = 0.0f;
+        if constexpr (DIM == 2) {
+          gx = 0.0f;
+#pragma unroll
+          for (int my = 0; my < N; ++my) {
+            gx = fmaf(T.B[qy][my], td[my], gx);
+            gy = fmaf(T.Bd[qy][my], tb[my], gy);
+          }
+        }
+        const float W = sW[qx] * (DIM == 2 ? T.w[qy] : 1.0f) * hdx * hdy;
+        gx *= a.two_dx * W;
+        gy *= a.two_dy * W;
+#pragma unroll
+        for (int b = 0; b < NY1; ++b) {
+          const float lb = DIM == 2 ? C.Lq[qy][b] : 1.0f;
+          hx_[b] = fmaf(lb, gx, hx_[b]);
+          hy_[b] = fmaf(lb, gy, hy_[b]);
+        }
+      }
+      // accumulate with the run-time row qx
+#pragma unroll
+      for (int aa = 0; aa < N; ++aa) {
+        const float la = (&C.Lq[0][0])[qx * N + aa];
+#pragma unroll
+        for (int b = 0; b < NY1; ++b) {
+          bx[aa + N * b] = fmaf(la, hx_[b], bx[aa + N * b]);
+          by[aa + N * b] = fmaf(la, hy_[b], by[aa + N * b]);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < ND; ++m) {
+      sbx[m * NH + h] = bx[m];
+      sby[m * NH + h] = by[m];
+    }
+  }
+  __syncthreads();
+
+  // ---- one thread per own cell ------------------------------------------------------------------
+  const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
+  const int gi = i0 + tx, gj = j0 + ty;
+  if (gi >= nx || gj >= ny) return;
+  const int hcx = tx + 1, hcy = DIM == 2 ? ty + 1 : 0;
+  const int hc = hcy * HX + hcx;
+  const size_t cell = (size_t)gj * nx + gi;
+  float c[ND];
+#pragma unroll
+  for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + hc];
+  float n0;
+  const float gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0);
+  const Law law(a, c[0]);
+
+  // lambda_e over the volume and face Gauss nodes of the cell polynomial
+  float lam = a.lambda_const;
+  if (!(a.lambda_const > 0.0f)) {
+    lam = 0.0f;
+    float tr[4][N];  // right, left, top, bottom traces (tangential modes)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float r = 0.0f, l = 0.0f, t = 0.0f, b = 0.0f;
+      if constexpr (DIM == 1) {
+        if (j == 0)
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            r += c[i];
+            l += (i & 1) ? -c[i] : c[i];
+          }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          r += c[i + N * j];
+          l += (i & 1) ? -c[i + N * j] : c[i + N * j];
+          t += c[j + N * i];
+          b += (i & 1) ? -c[j + N * i] : c[j + N * i];
+        }
+      }
+      tr[0][j] = r;
+      tr[1][j] = l;
+      tr[2][j] = t;
+      tr[3][j] = b;
+    }
+#pragma unroll
+    for (int q = 0; q < (DIM == 2 ? N : 1); ++q) {
+#pragma unroll
+      for (int f = 0; f < (DIM == 2 ? 4 : 2); ++f) {
+        float v = tr[f][0];
+        if constexpr (DIM == 2) {
+          v = 0.0f;
+#pragma unroll
+          for (int j = 0; j < N; ++j) v = fmaf(T.B[q][j], tr[f][j], v);
+        }
+        lam = fmaxf(lam, law.speed(v));
+      }
+    }
+#pragma unroll 1
+    for (int q = 0; q < ND; ++q) {
+      const int qx = q % N, qy = DIM == 2 ? q / N : 0;
+      float u = 0.0f;
+#pragma unroll
+      for (int m = 0; m < ND; ++m) {
+        const int mx = m % N, my = DIM == 2 ? m / N : 0;
+        u = fmaf(sB[qx * N + mx] * (DIM == 2 ? sB[qy * N + my] : 1.0f), c[m], u);
+      }
+      lam = fmaxf(lam, law.speed(u));
+    }
+  }
+  const float nu = lam * a.nu_scale;
+  if (a.gamma_out) a.gamma_out[cell] = gam;
+  if (a.nu_out) a.nu_out[cell] = nu;
+  if (a.lambda_out) a.lambda_out[cell] = lam;
+  if (a.mode & kModeSensorOnly) return;
+
+  // P_h grad u at the own cell's nodes: sum over the cells sharing each node / ML
+  float phx[ND], phy[ND];
+#pragma unroll
+  for (int bb = 0; bb < NY1; ++bb)
+#pragma unroll
+    for (int aa = 0; aa < N; ++aa) {
+      float sx = 0.0f, sy = 0.0f;
+      // x-neighbours of the node: (halo column, local index)
+      const int ncx = (aa == 0 || aa == P) ? 2 : 1;
+      const int ncy = DIM == 2 ? ((bb == 0 || bb == P) ? 2 : 1) : 1;
+#pragma unroll
+      for (int jy = 0; jy < ncy; ++jy)
+#pragma unroll
+        for (int jx = 0; jx < ncx; ++jx) {
+          int cx = hcx, la = aa, cy = hcy, lb = bb;
+          if (aa == 0) { cx = jx == 0 ? hcx - 1 : hcx; la = jx == 0 ? P : 0; }
+          if (aa == P) { cx = jx == 0 ? hcx : hcx + 1; la = jx == 0 ? P : 0; }
+          if (DIM == 2 && bb == 0) { cy = jy == 0 ? hcy - 1 : hcy; lb = jy == 0 ? P : 0; }
+          if (DIM == 2 && bb == P) { cy = jy == 0 ? hcy : hcy + 1; lb = jy == 0 ? P : 0; }
+          const int hh = cy * HX + cx, lm = la + N * lb;
+          sx += sbx[lm * NH + hh];
+          sy += sby[lm * NH + hh];
+        }
+      const float ml = ml1(C, aa == P ? 0 : aa, hdx) * (DIM == 2 ? ml1(C, bb == P ? 0 : bb, hdy) : 1.0f);
+      phx[aa + N * bb] = sx / ml;
+      phy[aa + N * bb] = sy / ml;
+    }
+
+  // (d) SC weights (A24) and (e) local residual over the volume Gauss nodes
+  bool troubled = a.sc && gam < a.c_gamma && n0 > 1e-30f;
+  if (a.troubled_override) {
+    const int ov = a.troubled_override[cell];
+    if (ov >= 0) troubled = ov && n0 > 1e-30f;
+  }
+  float afac = -1.0f;
+  // per node values: u, physical gradient, P_h grad u
+  auto point = [&](int qx, int qy, float& u, float& gx, float& gy, float& px, float& py) {
+    u = gx = gy = px = py = 0.0f;
+#pragma unroll
+    for (int m = 0; m < ND; ++m) {
+      const int mx = m % N, my = DIM == 2 ? m / N : 0;
+      const float bx_ = sB[qx * N + mx], by_ = DIM == 2 ? sB[qy * N + my] : 1.0f;
+      u = fmaf(bx_ * by_, c[m], u);
+      gx = fmaf(sBd[qx * N + mx] * by_, c[m], gx);
+      if constexpr (DIM == 2) gy = fmaf(bx_ * sBd[qy * N + my], c[m], gy);
+      const float lx = (&C.Lq[0][0])[qx * N + mx], ly = DIM == 2 ? (&C.Lq[0][0])[qy * N + my] : 1.0f;
+      px = fmaf(lx * ly, phx[m], px);
+      py = fmaf(lx * ly, phy[m], py);
+    }
+    gx *= a.two_dx;
+    gy *= a.two_dy;
+  };
+  if (troubled && gam < 1.0f) {
+    float s1 = 0.0f, s2 = 0.0f;
+#pragma unroll 1
+    for (int q = 0; q < ND; ++q) {
+      const int qx = q % N, qy = DIM == 2 ? q / N : 0;
+      float u, gx, gy, px, py;
+      point(qx, qy, u, gx, gy, px, py);
+      float n2 = 0.0f;
+#pragma unroll
+      for (int k = 1; k < ND; ++k) {
+        const int kx = k % N, ky = DIM == 2 ? k / N : 0;
+        float dk = 0.0f;
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+          const int mx = m % N, my = DIM == 2 ? m / N : 0;
+          dk = fmaf(sBk[(kx * N + qx) * N + mx] * (DIM == 2 ? sBk[(ky * N + qy) * N + my] : 1.0f), c[m], dk);
+        }
+        n2 = fmaf(T.sigma[k] * dk, dk, n2);
+      }
+      const float nq = sqrtf(n2);
+      sNq[q * NT + threadIdx.x] = nq;
+      const float f = fmaf(gx, gx, gy * gy) - gam * (gx * px + gy * py);
+      const float W = sW[qx] * (DIM == 2 ? sW[qy] : 1.0f);
+      s1 = fmaf(W, f, s1);
+      s2 = fmaf(W * nq, f, s2);
+    }
+    if (s1 > 0.0f && s2 > 0.0f) afac = s1 / s2;
+  }
+  if (a.troubled_out) a.troubled_out[cell] = troubled ? 1 : 0;
+  if (a.alpha_out) {
+#pragma unroll 1
+    for (int q = 0; q < ND; ++q) a.alpha_out[cell * ND + q] = afac >= 0.0f ? sNq[q * NT + threadIdx.x] * afac : 1.0f;
+  }
+  float r[ND];
+#pragma unroll
+  for (int m = 0; m < ND; ++m) r[m] = 0.0f;
+#pragma unroll 1
+  for (int q = 0; q < ND; ++q) {
+    const int qx = q % N, qy = DIM == 2 ? q / N : 0;
+    float u, gx, gy, px, py;
+    point(qx, qy, u, gx, gy, px, py);
+    // f(u) - f(ubar): the cell constant f(ubar) contributes f(ubar) int_K grad phi_a,
+    // which lives on the cell's edges and telescopes between neighbours; cg_node_rhs adds
+    // it as differences f(ubar_R) - f(ubar_L) of neighbouring means
+    float fx, fy;
+    law.flux_dev(u - c[0], fx, fy);
+    const float al = afac >= 0.0f ? sNq[q * NT + threadIdx.x] * afac : 1.0f;
+    const float W = sW[qx] * (DIM == 2 ? sW[qy] : 1.0f) * hdx * hdy;
+    const float Gx = W * (fx - nu * al * (gx - gam * px));
+    const float Gy = W * (fy - nu * al * (gy - gam * py));
+#pragma unroll
+    for (int m = 0; m < ND; ++m) {
+      const int mx = m % N, my = DIM == 2 ? m / N : 0;
+      const float lx = (&C.Lq[0][0])[qx * N + mx], dx_ = (&C.Ldq[0][0])[qx * N + mx];
+      if constexpr (DIM == 2) {
+        const float ly = (&C.Lq[0][0])[qy * N + my], dy_ = (&C.Ldq[0][0])[qy * N + my];
+        r[m] = fmaf(a.two_dx * dx_ * ly, Gx, r[m]);
+        r[m] = fmaf(a.two_dy * lx * dy_, Gy, r[m]);
+      } else {
+        r[m] = fmaf(a.two_dx * dx_, Gx, r[m]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < ND; ++m) a.rloc[cell * ND + m] = r[m];
+  a.ubar[cell] = c[0];
+}
+
+// cells around lattice node (I, J) in a fixed order, with the node's local index in each
+template <int DIM, int P>
+__device__ __forceinline__ int node_cells(int I, int J, int nx, int ny, int* cells, int* locs) {
+  constexpr int N = P + 1;
+  const int i = I / P, aa = I % P, j = DIM == 2 ? J / P : 0, bb = DIM == 2 ? J % P : 0;
+  int cx[2], lx[2], ncx = 1, cy[2], ly[2], ncy = 1;
+  if (aa == 0) { cx[0] = (i - 1 + nx) % nx; lx[0] = P; cx[1] = i; lx[1] = 0; ncx = 2; }
+  else { cx[0] = i; lx[0] = aa; }
+  if (DIM == 2 && bb == 0) { cy[0] = (j - 1 + ny) % ny; ly[0] = P; cy[1] = j; ly[1] = 0; ncy = 2; }
+  else { cy[0] = j; ly[0] = bb; }
+  int n = 0;
+  for (int y = 0; y < ncy; ++y)
+    for (int x = 0; x < ncx; ++x) {
+      cells[n] = cx[x] + nx * cy[y];
+      locs[n] = lx[x] + (DIM == 2 ? N * ly[y] : 0);
+      ++n;
+    }
+  return n;
+}
+
+// Nodal assembly.  Besides the cell-local residuals, the constant part of the flux:
+// int_K d_x phi_ab f(ubar_e) = (delta_{a,p} - delta_{a,0}) wl_b (dy/2) f_x(ubar_e) (and
+// likewise in y), which at a node shared by a left cell L and a right cell R sums to
+// -(f_x(ubar_R) - f_x(ubar_L)) wl_b dy/2; the difference of the two means' fluxes is
+// formed accurately by the deviation formula of the left cell's law.
+template <int DIM, int P, int SYS>
+__global__ void cg_node_rhs(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C) {
+  using Law = ScalarLaw<SYS, DIM>;
+  constexpr int ND = DIM == 2 ? (P + 1) * (P + 1) : P + 1;
+  const int64_t nn = (int64_t)a.nnx * (DIM == 2 ? a.nny : 1);
+  const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
+  const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(j % a.nnx), J = (int)(j / a.nnx);
+    int cells[4], locs[4];
+    const int n = node_cells<DIM, P>(I, J, nx, ny, cells, locs);
+    float r = 0.0f;
+    for (int k = 0; k < n; ++k) r += a.rloc[(size_t)cells[k] * ND + locs[k]];
+    const int i = I / P, ai = I % P, jj = J / P, bj = J % P;
+    if (ai == 0) {  // vertical cell edge: x-flux differences across it, one per cell row
+      const int iL = (i - 1 + nx) % nx;
+      const int nrow = (DIM == 2 && bj == 0) ? 2 : 1;
+      for (int k = 0; k < nrow; ++k) {
+        const int row = DIM == 2 ? ((bj == 0 && k == 0) ? (jj - 1 + ny) % ny : jj) : 0;
+        const int lb = DIM == 2 ? ((bj == 0) ? (k == 0 ? P : 0) : bj) : 0;
+        const float uL = a.ubar[iL + (size_t)nx * row], uR = a.ubar[i + (size_t)nx * row];
+        const Law law(a, uL);
+        float dfx, dfy;
+        law.flux_dev(uR - uL, dfx, dfy);
+        r -= dfx * (DIM == 2 ? C.wl[lb] * hdy : 1.0f);
+      }
+    }
+    if (DIM == 2 && bj == 0) {  // horizontal cell edge: y-flux differences, one per cell column
+      const int jB = (jj - 1 + ny) % ny;
+      const int ncol = ai == 0 ? 2 : 1;
+      for (int k = 0; k < ncol; ++k) {
+        const int col = (ai == 0 && k == 0) ? (i - 1 + nx) % nx : i;
+        const int la = (ai == 0) ? (k == 0 ? P : 0) : ai;
+        const float uB = a.ubar[col + (size_t)nx * jB], uT = a.ubar[col + (size_t)nx * jj];
+        const Law law(a, uB);
+        float dfx, dfy;
+        law.flux_dev(uT - uB, dfx, dfy);
+        r -= dfy * C.wl[la] * hdx;
+      }
+    }
+    const float ml = ml1(C, ai, hdx) * (DIM == 2 ? ml1(C, bj, hdy) : 1.0f);
+    a.rnode[j] = r;
+    a.du[j] = r / ml;
+  }
+}
+
+template <int DIM, int P>
+__global__ void cg_cell_mass(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C) {
+  constexpr int N = P + 1, ND = DIM == 2 ? N * N : N;
+  const int64_t ncell = (int64_t)a.nx * (DIM == 2 ? a.ny : 1);
+  const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncell; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % a.nx), j = (int)(e / a.nx);
+    float x[ND];
+#pragma unroll
+    for (int m = 0; m < ND; ++m) {
+      const int aa = m % N, bb = DIM == 2 ? m / N : 0;
+      const int I = (P * i + aa) % a.nnx, J = DIM == 2 ? (P * j + bb) % a.nny : 0;
+      x[m] = a.du[(size_t)J * a.nnx + I];
+    }
+    float y[ND];
+#pragma unroll
+    for (int m = 0; m < ND; ++m) {
+      const int aa = m % N, bb = DIM == 2 ? m / N : 0;
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        const int ka = k % N, kb = DIM == 2 ? k / N : 0;
+        acc = fmaf(C.M1[aa][ka] * (DIM == 2 ? C.M1[bb][kb] : 1.0f), x[k], acc);
+      }
+      y[m] = acc * hdx * hdy;
+    }
+#pragma unroll
+    for (int m = 0; m < ND; ++m) a.mloc[e * ND + m] = y[m];
+  }
+}
+
+template <int DIM, int P>
+__global__ void cg_node_correct(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C,
+                                int final_sweep) {
+  constexpr int ND = DIM == 2 ? (P + 1) * (P + 1) : P + 1;
+  const int64_t nn = (int64_t)a.nnx * (DIM == 2 ? a.nny : 1);
+  const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(j % a.nnx), J = (int)(j / a.nnx);
+    int cells[4], locs[4];
+    const int n = node_cells<DIM, P>(I, J, a.nx, a.ny, cells, locs);
+    float mc = 0.0f;
+    for (int k = 0; k < n; ++k) mc += a.mloc[(size_t)cells[k] * ND + locs[k]];
+    const float ml = ml1(C, I % P, hdx) * (DIM == 2 ? ml1(C, J % P, hdy) : 1.0f);
+    const float du = a.du[j] + (a.rnode[j] - mc) / ml;
+    if (!final_sweep) {
+      a.du[j] = du;
+    } else if (a.mode & kModeRK) {
+      float v = fmaf(a.dt, du, a.u_in[j]);
+      if (a.rk_a != 0.0f) v = fmaf(a.rk_b, v - a.u_n[j], a.u_n[j]);  // plain load: u_n may alias u_out
+      a.u_out[j] = v;
+      if (!isfinite(v)) atomicOr(a.status, kStatNonfinite);
+    } else {
+      a.u_out[j] = du;
+      if (!isfinite(du)) atomicOr(a.status, kStatNonfinite);
+    }
+  }
+}
+
+template <int DIM, int P, int SYS, int TX, int TY>
+cudaError_t launch_cg_t(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
+  using Tb = DgTables<DIM, P>;
+  using Cb = CgTables<DIM, P>;
+  constexpr size_t smem = CgLayout<DIM, P, TX, TY>::BYTES;
+  static_assert(smem <= 220 * 1024, "tile too large for shared memory");
+  if (m->tables_bytes != sizeof(Tb) || m->cg_tables_bytes != sizeof(Cb)) return cudaErrorInvalidValue;
+  const Tb& T = *static_cast<const Tb*>(m->tables);
+  const Cb& C = *static_cast<const Cb*>(m->cg_tables);
+  auto k1 = cg_stage_cells<DIM, P, SYS, TX, TY>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((a.nx + TX - 1) / TX, DIM == 2 ? (a.ny + TY - 1) / TY : 1);
+  k1<<<grid, TX * TY, smem, s>>>(a, T, C);
+  if (a.mode & kModeSensorOnly) return cudaGetLastError();
+  const int64_t nn = m->nnode, nc = m->ncell;
+  const int bn = (int)((nn + 255) / 256 < 4096 ? (nn + 255) / 256 : 4096);
+  const int bc = (int)((nc + 255) / 256 < 4096 ? (nc + 255) / 256 : 4096);
+  cg_node_rhs<DIM, P, SYS><<<bn, 256, 0, s>>>(a, C);
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    cg_cell_mass<DIM, P><<<bc, 256, 0, s>>>(a, C);
+    cg_node_correct<DIM, P><<<bn, 256, 0, s>>>(a, C, sweep == 1);
+  }
+  return cudaGetLastError();
+}
+
+template <int DIM, int P>
+cudaError_t launch_cg_p(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
+  constexpr int TX = DIM == 2 ? 16 : 128, TY = DIM == 2 ? 8 : 1;
+  switch (m->desc.system) {
+    case CVWENO_BURGERS: return launch_cg_t<DIM, P, CVWENO_BURGERS, TX, TY>(m, a, s);
+    case CVWENO_KPP: return DIM == 2 ? launch_cg_t<DIM, P, CVWENO_KPP, TX, TY>(m, a, s) : cudaErrorNotSupported;
+    case CVWENO_LINADV: return launch_cg_t<DIM, P, CVWENO_LINADV, TX, TY>(m, a, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stage_cg(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
+  switch (m->dim * 10 + m->p) {
+    case 11: return launch_cg_p<1, 1>(m, a, s);
+    case 12: return launch_cg_p<1, 2>(m, a, s);
+    case 13: return launch_cg_p<1, 3>(m, a, s);
+    case 14: return launch_cg_p<1, 4>(m, a, s);
+    case 21: return launch_cg_p<2, 1>(m, a, s);
+    case 22: return launch_cg_p<2, 2>(m, a, s);
+    case 23: return launch_cg_p<2, 3>(m, a, s);
+    case 24: return launch_cg_p<2, 4>(m, a, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace cvw

@@ -44,6 +44,22 @@ struct DgTables {
   float A[NC][NS][NS];
 };
 
+// CG tabulations (Gauss-Lobatto-Legendre nodal basis l_a on [-1,1]):
+//   V[m][a]   Legendre mode m of l_a: (2m+1)/2 int P_m l_a      (nodal -> modal)
+//   Lq[q][a]  l_a(xi_q) and Ldq[q][a] = l_a'(xi_q) at the Gauss nodes
+//   M1[a][b]  int l_a l_b (1D reference mass), wl[a] = int l_a (GLL weight)
+//   xg[a]     GLL nodes
+template <int DIM, int P>
+struct CgTables {
+  static constexpr int N = P + 1;
+  float V[N][N];
+  float Lq[N][N];
+  float Ldq[N][N];
+  float M1[N][N];
+  float wl[N];
+  float xg[N];
+};
+
 // Run-time arguments of one stage launch.
 struct StageArgs {
   const float* u_in;   // state the residual is evaluated on
@@ -61,7 +77,11 @@ struct StageArgs {
   int perx, pery;      // periodic flags
   int vx;              // vertices per row (nx if periodic in x, nx+1 otherwise)
   int mode;            // kMode* flags
-  float rk_a, rk_b, dt;  // u_out = rk_a u_n + rk_b (u_in + dt L(u_in))
+  // u_out = rk_a u_n + rk_b (u_in + dt L(u_in)) with rk_a = 1 - rk_b, evaluated as the
+  // increment u_n + rk_b (w - u_n): 1/3 + 2/3 rounded to float sum to 1 + 3e-8, a growth
+  // that compounds over thousands of steps; the increment form keeps constants exact.
+  // rk_a == 0 selects u_out = w.
+  float rk_a, rk_b, dt;
   float two_dx, two_dy;  // 2/dx, 2/dy
   float nu_scale;        // h_e / (2p)
   float eps, gamma_vertex, c_gamma, q, lambda_const;
@@ -69,11 +89,18 @@ struct StageArgs {
   int sc, sensor_mode;
   float adv_vx, adv_vy;
   float gas_gamma;
+  // CG only: nodal lattice and the per-stage work arrays
+  int nnx, nny;
+  float* rloc;  // [ncell][nd] cell-local residuals
+  float* rnode; // [nnode] assembled residual
+  float* du;    // [nnode] du/dt iterate
+  float* mloc;  // [ncell][nd] cell-local consistent-mass products
+  float* ubar;  // [ncell] cell means (Legendre mode 0)
 };
 
 enum : int {
   kModeResidual = 1,   // write dudt to u_out
-  kModeRK = 2,         // write rk_a u_n + rk_b (u_in + dt L) to u_out
+  kModeRK = 2,         // write u_n + rk_b (u_in + dt L - u_n) (or u_in + dt L) to u_out
   kModeSensorOnly = 4, // stop after stage (c) (gamma, nu, lambda outputs)
 };
 
@@ -93,6 +120,21 @@ struct cvweno_mesh_s {
   // reference tabulations, one per (dim, p) -- only the matching one is filled
   void* tables;            // host copy of DgTables<dim, p>
   size_t tables_bytes;
+  // CG: nodal lattice, tabulations and stage work arrays
+  int kind;
+  int nnx, nny;
+  int64_t nnode;
+  void* cg_tables;         // host copy of CgTables<dim, p>
+  size_t cg_tables_bytes;
+  float* d_rloc;
+  float* d_r;
+  float* d_du;
+  float* d_mloc;
+  float* d_ubar;
+  double cg_xg[cvw::kMaxP + 1];  // GLL nodes (host, FP64)
+  double cg_wl[cvw::kMaxP + 1];  // GLL weights (host, FP64)
+  float* d_cg_xg;           // GLL nodes (device)
+  double* d_cg_ml;          // 1D lumped masses by local node index, x then y (device)
   // device scratch
   float* d_u1;
   float* d_u2;
@@ -111,4 +153,8 @@ void legendre_values(double x, int mmax, double* out);  // P_0..P_mmax at x
 // dg_scalar.cu / dg_euler.cu
 cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
+// cg_scalar.cu
+cudaError_t launch_stage_cg(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
+// api.cu: the stage arguments common to every launch on mesh m (no state pointers, no RK)
+StageArgs stage_base_args(const cvweno_mesh_s* m);
 }  // namespace cvw

@@ -41,15 +41,34 @@ __device__ __forceinline__ EulerMean euler_mean(float g, const float* Ub) {
   return M;
 }
 
+// a*b - c*d with the rounding of c*d compensated (Kahan's FMA form): the result is
+// accurate relative to itself even when the two products nearly cancel.
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+  const float w = c * d;
+  const float e = fmaf(-c, d, w);  // w - c*d, exactly
+  const float f = fmaf(a, b, -w);  // a*b - w, one rounding
+  return f + e;
+}
+
 // F(Ubar + d) - F(Ubar) in x and y, written as sums of (mean quantity) x (deviation)
 // so that FP32 rounding is relative to |d|:
-//   dv = (dm - vbar drho) / rho,  dK = (mbar . dv + dm . vbar + dm . dv) / 2,
-//   dp = (g - 1)(dE - dK),        dH = dE + dp.
+//   dv = (dm rhobar - mbar drho) / (rho rhobar),
+//   dE - dK = (dE rhobar - dm . mbar / 2) / rhobar - (mbar + dm) . dv / 2,
+//   dp = (g - 1)(dE - dK),  dH = dE + dp.
+// The two differences that cancel exactly in uniform flow (dv for a uniform velocity,
+// dE - dK for a uniform pressure) are formed with compensated products.
 __device__ __forceinline__ void euler_dflux(float g, const EulerMean& M, const float* d, float* dFx, float* dFy) {
-  const float ir = 1.0f / (M.U[0] + d[0]);
-  const float dvx = fmaf(-M.vx, d[0], d[1]) * ir, dvy = fmaf(-M.vy, d[0], d[2]) * ir;
-  const float dK = 0.5f * (M.U[1] * dvx + M.U[2] * dvy + d[1] * M.vx + d[2] * M.vy + d[1] * dvx + d[2] * dvy);
-  const float dp = (g - 1.0f) * (d[3] - dK);
+  const float rb = M.U[0];
+  const float ir = 1.0f / (rb * (rb + d[0]));
+  const float dvx = diff_of_products(d[1], rb, M.U[1], d[0]) * ir;
+  const float dvy = diff_of_products(d[2], rb, M.U[2], d[0]) * ir;
+  // dE rhobar - (dmx mbarx + dmy mbary) / 2, compensated
+  const float x1 = diff_of_products(d[3], rb, 0.5f * d[1], M.U[1]);
+  const float p2 = 0.5f * d[2] * M.U[2];
+  const float e2 = fmaf(0.5f * d[2], M.U[2], -p2);
+  const float x = (x1 - p2) - e2;
+  const float dEmK = x / rb - 0.5f * ((M.U[1] + d[1]) * dvx + (M.U[2] + d[2]) * dvy);
+  const float dp = (g - 1.0f) * dEmK;
   const float dH = d[3] + dp;
   dFx[0] = d[1];
   dFx[1] = M.U[1] * dvx + d[1] * M.vx + d[1] * dvx + dp;
@@ -606,8 +625,8 @@ __global__ void __launch_bounds__(TX* TY)
       const float d = r[v][m] * (0.25f * (2 * mx + 1) * (2 * my + 1));
       nonfinite |= !isfinite(d);
       if (a.mode & kModeRK) {
-        float val = a.rk_b * fmaf(a.dt, d, C(v, m, hc));
-        if (a.rk_a != 0.0f) val = fmaf(a.rk_a, un[m], val);
+        float val = fmaf(a.dt, d, C(v, m, hc));
+        if (a.rk_a != 0.0f) val = fmaf(a.rk_b, val - un[m], un[m]);
         out[m] = val;
       } else {
         out[m] = d;

@@ -58,6 +58,7 @@ struct ScalarLaw<CVWENO_BURGERS, DIM> {
     fy = fx;
   }
   __device__ __forceinline__ float flux_dev_dir(float d, int) const { return dev(d); }
+  __device__ __forceinline__ void flux_mean(float& fx, float& fy) const { fx = fy = 0.5f * ubar * ubar; }
   // |f'(u)| (Euclidean) for nu_e, and |f'(u) . n| for an axis-aligned face
   __device__ __forceinline__ float speed(float u) const { return DIM == 2 ? 1.41421356237f * fabsf(u) : fabsf(u); }
   __device__ __forceinline__ float nspeed(float u, int) const { return fabsf(u); }
@@ -81,6 +82,10 @@ struct ScalarLaw<CVWENO_KPP, DIM> {
     flux_dev(d, fx, fy);
     return dir == 0 ? fx : fy;
   }
+  __device__ __forceinline__ void flux_mean(float& fx, float& fy) const {
+    fx = sb;
+    fy = cb;
+  }
   __device__ __forceinline__ float speed(float) const { return 1.0f; }
   __device__ __forceinline__ float nspeed(float u, int dir) const {
     return dir == 0 ? fabsf(cosf(u)) : fabsf(sinf(u));
@@ -89,8 +94,12 @@ struct ScalarLaw<CVWENO_KPP, DIM> {
 
 template <int DIM>
 struct ScalarLaw<CVWENO_LINADV, DIM> {
-  float vx, vy;
-  __device__ __forceinline__ ScalarLaw(const StageArgs& a, float) : vx(a.adv_vx), vy(a.adv_vy) {}
+  float vx, vy, ubar;
+  __device__ __forceinline__ ScalarLaw(const StageArgs& a, float ub) : vx(a.adv_vx), vy(a.adv_vy), ubar(ub) {}
+  __device__ __forceinline__ void flux_mean(float& fx, float& fy) const {
+    fx = vx * ubar;
+    fy = vy * ubar;
+  }
   __device__ __forceinline__ void flux_dev(float d, float& fx, float& fy) const {
     fx = vx * d;
     fy = vy * d;
@@ -186,56 +195,31 @@ struct TileLayout {
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
 };
 
-template <int DIM, int P, int SYS, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
-    dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
+// Copies the tabulations read with run-time indices into shared memory.
+template <int DIM, int P, int TX, int TY>
+__device__ __forceinline__ void stage_tables_to_smem(const DgTables<DIM, P>& T, float* smem) {
   using L = TileLayout<DIM, P, TX, TY>;
-  using Law = ScalarLaw<SYS, DIM>;
-  constexpr int N = L::N, ND = L::ND, NS = L::NS, NC = L::NC, NSP = L::NSP, NT = L::NT;
-  constexpr int HX = L::HX, NH = L::NH, VXT = L::VXT, NVT = L::NVT;
-  constexpr int NY1 = DIM == 2 ? N : 1;  // tensor extent in y (1 in 1D)
-  extern __shared__ __align__(16) float smem[];
-  float* sc = smem + L::OFF_SC;
-  float* st = smem + L::OFF_ST;
+  constexpr int N = L::N, NS = L::NS, NC = L::NC, NSP = L::NSP, NT = L::NT;
   float* sA = smem + L::OFF_A;
-  float* sB = smem + L::OFF_B;
-  float* sBd = smem + L::OFF_BD;
-  float* sBk = smem + L::OFF_BK;
-  float* sW = smem + L::OFF_W;
-  float* sNq = smem + L::OFF_NQ;
-
-  const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
-  const int i0 = blockIdx.x * TX, j0 = DIM == 2 ? blockIdx.y * TY : 0;
-
-  // ---- load tile + halo, and the tabulations read with run-time indices ---------------
-  for (int f = threadIdx.x; f < NH * ND; f += NT) {
-    int r = f / (HX * ND);
-    int rem = f - r * (HX * ND);
-    int cc = rem / ND;
-    int mm = rem - cc * ND;
-    int gi = i0 - 1 + cc, gj = DIM == 2 ? j0 - 1 + r : 0;
-    bool ok = true;
-    if (gi < 0 || gi >= nx) {
-      if (a.perx) gi = (gi + nx) % nx; else ok = false;
-    }
-    if (DIM == 2 && (gj < 0 || gj >= ny)) {
-      if (a.pery) gj = (gj + ny) % ny; else ok = false;
-    }
-    sc[mm * NH + r * HX + cc] = ok ? __ldg(a.u_in + ((size_t)gj * nx + gi) * ND + mm) : 0.0f;
-  }
   for (int f = threadIdx.x; f < NC * NS * NSP; f += NT) {
     int l = f / (NS * NSP), rem = f - l * (NS * NSP), i = rem / NSP, j = rem - i * NSP;
     sA[f] = j < NS ? T.A[l][i][j] : 0.0f;
   }
   for (int f = threadIdx.x; f < N * N; f += NT) {
-    sB[f] = (&T.B[0][0])[f];
-    sBd[f] = (&T.Bd[0][0])[f];
+    smem[L::OFF_B + f] = (&T.B[0][0])[f];
+    smem[L::OFF_BD + f] = (&T.Bd[0][0])[f];
   }
-  for (int f = threadIdx.x; f < N * N * N; f += NT) sBk[f] = (&T.Bk[0][0][0])[f];
-  if (threadIdx.x < N) sW[threadIdx.x] = T.w[threadIdx.x];
-  __syncthreads();
+  for (int f = threadIdx.x; f < N * N * N; f += NT) smem[L::OFF_BK + f] = (&T.Bk[0][0][0])[f];
+  if (threadIdx.x < N) smem[L::OFF_W + threadIdx.x] = T.w[threadIdx.x];
+}
 
-  // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
+// Stages (a)+(b) for the tile's vertices, from the halo coefficients sc (mode-major):
+// vertex candidates t* into st, and (optionally) the physical vertex data to tstar_out.
+template <int DIM, int P, int TX, int TY>
+__device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTables<DIM, P>& T, const float* sc,
+                                                  float* st, int i0, int j0, int nx, int ny) {
+  using L = TileLayout<DIM, P, TX, TY>;
+  constexpr int ND = L::ND, NC = L::NC, NT = L::NT, HX = L::HX, NH = L::NH, VXT = L::VXT, NVT = L::NVT;
   const int act_x = min(TX, nx - i0), act_y = DIM == 2 ? min(TY, ny - j0) : 1;
   for (int v = threadIdx.x; v < NVT; v += NT) {
     int va = v % VXT, vb = DIM == 2 ? v / VXT : 0;
@@ -279,19 +263,15 @@ __global__ void __launch_bounds__(TX* TY)
       }
     }
   }
-  __syncthreads();
+}
 
-  // ---- one thread per cell from here on (no further barriers) ----------------------------
-  const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
-  const int gi = i0 + tx, gj = j0 + ty;
-  if (gi >= nx || gj >= ny) return;
-  const int hc = (DIM == 2 ? (ty + 1) * HX : 0) + tx + 1;
-  const size_t cell = (size_t)gj * nx + gi;
-  float c[ND];
-#pragma unroll
-  for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + hc];
-
-  // ---- (c) cell-vertex reconstruction and sensor --------------------------------------
+// Stage (c) for one cell with Legendre coefficients c: the cell-vertex reconstruction
+// and the sensor gamma_e (eq. gamma); n0 returns ||u^e||_e.
+template <int DIM, int P, int TX, int TY>
+__device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<DIM, P>& T, const float* st,
+                                             const float* sA, const float* c, int tx, int ty, float& n0) {
+  using L = TileLayout<DIM, P, TX, TY>;
+  constexpr int NS = L::NS, NC = L::NC, NSP = L::NSP, VXT = L::VXT, NVT = L::NVT;
   float w0[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
@@ -303,58 +283,111 @@ __global__ void __launch_bounds__(TX* TY)
   float n0sq = 0.0f;
 #pragma unroll
   for (int i = 0; i < NS; ++i) n0sq = fmaf(w0[i], w0[i], n0sq);
-  const float n0 = sqrtf(n0sq);
-  float gam;
-  {
-    const float om0 = (1.0f - NC * a.gamma_vertex) / ipowf(a.eps + powq(n0, a.q), a.r);
-    float S[NS];
+  n0 = sqrtf(n0sq);
+  const float om0 = (1.0f - NC * a.gamma_vertex) / ipowf(a.eps + powq(n0, a.q), a.r);
+  float S[NS];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
-    float osum = om0;
+  for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
+  float osum = om0;
 #pragma unroll 1
-    for (int l = 0; l < NC; ++l) {
-      const int vi = (tx + (l & 1)) + (DIM == 2 ? (ty + ((l >> 1) & 1)) * VXT : 0);
-      float tl[NSP];
+  for (int l = 0; l < NC; ++l) {
+    const int vi = (tx + (l & 1)) + (DIM == 2 ? (ty + ((l >> 1) & 1)) * VXT : 0);
+    float tl[NSP];
 #pragma unroll
-      for (int k = 0; k < NSP; ++k) tl[k] = k < NS ? st[(k + 1) * NVT + vi] : 0.0f;
-      const float4* Al = reinterpret_cast<const float4*>(sA + l * NS * NSP);
-      float wl[NS];
-      float b2 = 0.0f;
-#pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int j4 = 0; j4 < NSP / 4; ++j4) {
-          const float4 q4 = Al[i * (NSP / 4) + j4];
-          acc = fmaf(q4.x, tl[4 * j4 + 0], acc);
-          acc = fmaf(q4.y, tl[4 * j4 + 1], acc);
-          acc = fmaf(q4.z, tl[4 * j4 + 2], acc);
-          acc = fmaf(q4.w, tl[4 * j4 + 3], acc);
-        }
-        wl[i] = acc;
-        b2 = fmaf(acc, acc, b2);
-      }
-      const float om = a.gamma_vertex / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
-      osum += om;
-#pragma unroll
-      for (int i = 0; i < NS; ++i) S[i] = fmaf(om, wl[i], S[i]);
-    }
-    const float inv = 1.0f / osum;
-    float d2 = 0.0f;
+    for (int k = 0; k < NSP; ++k) tl[k] = k < NS ? st[(k + 1) * NVT + vi] : 0.0f;
+    const float4* Al = reinterpret_cast<const float4*>(sA + l * NS * NSP);
+    float wl[NS];
+    float b2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-      float df = w0[i] - S[i] * inv;
-      d2 = fmaf(df, df, d2);
+      float acc = 0.0f;
+#pragma unroll
+      for (int j4 = 0; j4 < NSP / 4; ++j4) {
+        const float4 q4 = Al[i * (NSP / 4) + j4];
+        acc = fmaf(q4.x, tl[4 * j4 + 0], acc);
+        acc = fmaf(q4.y, tl[4 * j4 + 1], acc);
+        acc = fmaf(q4.z, tl[4 * j4 + 2], acc);
+        acc = fmaf(q4.w, tl[4 * j4 + 3], acc);
+      }
+      wl[i] = acc;
+      b2 = fmaf(acc, acc, b2);
     }
-    if (a.sensor_mode == CVWENO_SENSOR_SMOOTH)
-      gam = 1.0f;
-    else if (a.sensor_mode == CVWENO_SENSOR_TROUBLED)
-      gam = 0.0f;
-    else if (n0 <= 1e-30f)
-      gam = 1.0f;
-    else
-      gam = 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
+    const float om = a.gamma_vertex / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+    osum += om;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) S[i] = fmaf(om, wl[i], S[i]);
   }
+  const float inv = 1.0f / osum;
+  float d2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    float df = w0[i] - S[i] * inv;
+    d2 = fmaf(df, df, d2);
+  }
+  if (a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
+  if (a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
+  if (n0 <= 1e-30f) return 1.0f;
+  return 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
+}
+
+// One tile of one stage: the whole path (a)-(e) for the cells [i0, i0+TX) x [j0, j0+TY)
+// of the mesh described by a.  The tabulations must already be staged in smem
+// (stage_tables_to_smem) and visible to the CTA; the function contains its own barriers
+// and is called by every thread of the CTA.
+template <int DIM, int P, int SYS, int TX, int TY>
+__device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<DIM, P>& T, int i0, int j0,
+                                            float* smem) {
+  using L = TileLayout<DIM, P, TX, TY>;
+  using Law = ScalarLaw<SYS, DIM>;
+  constexpr int N = L::N, ND = L::ND, NT = L::NT;
+  constexpr int HX = L::HX, NH = L::NH;
+  constexpr int NY1 = DIM == 2 ? N : 1;  // tensor extent in y (1 in 1D)
+  float* sc = smem + L::OFF_SC;
+  float* st = smem + L::OFF_ST;
+  float* sA = smem + L::OFF_A;
+  float* sB = smem + L::OFF_B;
+  float* sBd = smem + L::OFF_BD;
+  float* sBk = smem + L::OFF_BK;
+  float* sW = smem + L::OFF_W;
+  float* sNq = smem + L::OFF_NQ;
+
+  const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
+
+  // ---- load tile + halo --------------------------------------------------------------------
+  for (int f = threadIdx.x; f < NH * ND; f += NT) {
+    int r = f / (HX * ND);
+    int rem = f - r * (HX * ND);
+    int cc = rem / ND;
+    int mm = rem - cc * ND;
+    int gi = i0 - 1 + cc, gj = DIM == 2 ? j0 - 1 + r : 0;
+    bool ok = true;
+    if (gi < 0 || gi >= nx) {
+      if (a.perx) gi = (gi + nx) % nx; else ok = false;
+    }
+    if (DIM == 2 && (gj < 0 || gj >= ny)) {
+      if (a.pery) gj = (gj + ny) % ny; else ok = false;
+    }
+    sc[mm * NH + r * HX + cc] = ok ? __ldg(a.u_in + ((size_t)gj * nx + gi) * ND + mm) : 0.0f;
+  }
+  __syncthreads();
+
+  // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
+  tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
+  __syncthreads();
+
+  // ---- one thread per cell from here on (no further barriers in this tile) -----------------
+  const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
+  const int gi = i0 + tx, gj = j0 + ty;
+  if (gi >= nx || gj >= ny) return;
+  const int hc = (DIM == 2 ? (ty + 1) * HX : 0) + tx + 1;
+  const size_t cell = (size_t)gj * nx + gi;
+  float c[ND];
+#pragma unroll
+  for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + hc];
+
+  // ---- (c) cell-vertex reconstruction and sensor --------------------------------------
+  float n0;
+  const float gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0);
 
   // ---- own trace polynomials along each face, as deviations from the mean -------------------
   // u(x) = ubar + (non-mean modes): rounding stays relative to the in-cell variation.
@@ -660,14 +693,22 @@ __global__ void __launch_bounds__(TX* TY)
     float d = r[m] * minv;
     bad |= !isfinite(d);
     if (a.mode & kModeRK) {
-      float v = a.rk_b * fmaf(a.dt, d, c[m]);
-      if (a.rk_a != 0.0f) v = fmaf(a.rk_a, un[m], v);  // plain load: u_n may alias u_out
+      float v = fmaf(a.dt, d, c[m]);
+      if (a.rk_a != 0.0f) v = fmaf(a.rk_b, v - un[m], un[m]);  // plain load: u_n may alias u_out
       out[m] = v;
     } else {
       out[m] = d;
     }
   }
   if (bad) atomicOr(a.status, kStatNonfinite);
+}
+
+template <int DIM, int P, int SYS, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+    dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
+  extern __shared__ __align__(16) float smem[];
+  stage_tables_to_smem<DIM, P, TX, TY>(T, smem);  // made visible by the tile's first barrier
+  scalar_tile<DIM, P, SYS, TX, TY>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
 }
 
 }  // namespace cvw

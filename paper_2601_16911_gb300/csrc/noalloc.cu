@@ -148,9 +148,13 @@ bool fill_tables(cvw::DgTables<DIM, P>& t, double dx, double dy, double h) {
     }
     t.w[q] = (float)gw[q];
   }
+  // scalings as functions of h/dx and h/dy only (h = sqrt(dx^2 + dy^2) in 2D, dx in 1D)
+  (void)h;
+  const double ax = DIM == 2 ? sqrt(1.0 + (dy / dx) * (dy / dx)) : 1.0;
+  const double ay = DIM == 2 ? sqrt((dx / dy) * (dx / dy) + 1.0) : 1.0;
   for (int k = 0; k < ND; ++k) {
     int kx = k % N, ky = DIM == 2 ? k / N : 0;
-    t.sigma[k] = k == 0 ? 0.0f : (float)(pow(2.0 * h / dx, 2 * kx) * (DIM == 2 ? pow(2.0 * h / dy, 2 * ky) : 1.0));
+    t.sigma[k] = k == 0 ? 0.0f : (float)(pow(2.0 * ax, 2 * kx) * (DIM == 2 ? pow(2.0 * ay, 2 * ky) : 1.0));
     t.tscale[k] = (float)(pow(2.0 / dx, kx) * (DIM == 2 ? pow(2.0 / dy, ky) : 1.0));
   }
   const int NG = 8;
@@ -163,11 +167,12 @@ bool fill_tables(cvw::DgTables<DIM, P>& t, double dx, double dy, double h) {
       for (int a = 0; a < N; ++a)
         for (int b = 0; b < N; ++b) g[k][a][b] += qw[q] * L[k][a] * L[k][b];
   }
-  const double jac = DIM == 2 ? 0.25 * dx * dy : 0.5 * dx;
   double G[ND][ND] = {};
   for (int k = 1; k < ND; ++k) {
     int kx = k % N, ky = DIM == 2 ? k / N : 0;
-    double rho = pow(h, 2 * (kx + ky) - DIM) * pow(2.0 / dx, 2 * kx) * (DIM == 2 ? pow(2.0 / dy, 2 * ky) : 1.0) * jac;
+    // h^(2|k| - dim) (2/dx)^(2kx) (2/dy)^(2ky) |J|
+    double rho = pow(2.0 * ax, 2 * kx) * (DIM == 2 ? pow(2.0 * ay, 2 * ky) : 1.0) /
+                 (DIM == 2 ? 4.0 * ax * ay : 2.0 * ax);
     for (int a = 0; a < ND; ++a)
       for (int b = 0; b < ND; ++b) {
         double v = g[kx][a % N][b % N];

@@ -112,7 +112,12 @@ cvweno_status fill(cvweno_mesh m) {
   constexpr int N = T::N, ND = T::ND, NS = T::NS, NC = T::NC;
   T* t = (T*)calloc(1, sizeof(T));
   if (!t) return CVWENO_ERR_NOMEM;
-  const double dx = m->dx, dy = m->dy, h = m->h;
+  const double dx = m->dx, dy = m->dy;
+  // h/dx and h/dy (h = sqrt(dx^2 + dy^2) in 2D, dx in 1D) from the aspect ratio alone:
+  // every scaling below is a function of these two ratios, so square cells of any size
+  // get bitwise the same tabulations (except tscale)
+  const double ax = DIM == 2 ? sqrt(1.0 + (dy / dx) * (dy / dx)) : 1.0;
+  const double ay = DIM == 2 ? sqrt((dx / dy) * (dx / dy) + 1.0) : 1.0;
   double gx[N], gw[N];
   gauss_golub_welsch(N, gx, gw);
   double tab[N * N];
@@ -132,7 +137,7 @@ cvweno_status fill(cvweno_mesh m) {
   // pointwise semi-norm weights and reference->physical scales
   for (int k = 0; k < ND; ++k) {
     int kx = k % N, ky = DIM == 2 ? k / N : 0;
-    double sx = pow(2.0 * h / dx, 2 * kx), sy = DIM == 2 ? pow(2.0 * h / dy, 2 * ky) : 1.0;
+    double sx = pow(2.0 * ax, 2 * kx), sy = DIM == 2 ? pow(2.0 * ay, 2 * ky) : 1.0;
     t->sigma[k] = (k == 0) ? 0.0f : (float)(sx * sy);
     t->tscale[k] = (float)(pow(2.0 / dx, kx) * (DIM == 2 ? pow(2.0 / dy, ky) : 1.0));
   }
@@ -148,12 +153,14 @@ cvweno_status fill(cvweno_mesh m) {
       for (int a = 0; a < N; ++a)
         for (int b = 0; b < N; ++b) g[(k * N + a) * N + b] += qw[q] * tq[k * N + a] * tq[k * N + b];
   }
-  // element semi-norm Gram matrix on modes (eq. snorm), physical scaling folded in
-  const double jac = DIM == 2 ? 0.25 * dx * dy : 0.5 * dx;
+  // element semi-norm Gram matrix on modes (eq. snorm), physical scaling folded in:
+  // h^(2|k| - dim) (2/dx)^(2kx) (2/dy)^(2ky) |J| = (2h/dx)^(2kx) (2h/dy)^(2ky) |J| / h^dim
+  // with |J| / h^dim = 1 / (4 ax ay) in 2D and 1 / (2 ax) in 1D
   std::vector<double> G((size_t)ND * ND, 0.0);
   for (int k = 1; k < ND; ++k) {
     int kx = k % N, ky = DIM == 2 ? k / N : 0;
-    double rho = pow(h, 2 * (kx + ky) - DIM) * pow(2.0 / dx, 2 * kx) * (DIM == 2 ? pow(2.0 / dy, 2 * ky) : 1.0) * jac;
+    double rho = pow(2.0 * ax, 2 * kx) * (DIM == 2 ? pow(2.0 * ay, 2 * ky) : 1.0) /
+                 (DIM == 2 ? 4.0 * ax * ay : 2.0 * ax);
     for (int a = 0; a < ND; ++a)
       for (int b = 0; b < ND; ++b) {
         int ax = a % N, ay = DIM == 2 ? a / N : 0, bx = b % N, by = DIM == 2 ? b / N : 0;
@@ -214,6 +221,99 @@ cvweno_status fill(cvweno_mesh m) {
   return CVWENO_OK;
 }
 
+// Gauss-Lobatto-Legendre nodes: the endpoints and the interior nodes, which are the
+// zeros of P_p' (a multiple of the Jacobi polynomial P^(1,1)_{p-1}), obtained as the
+// eigenvalues of the symmetric Jacobi matrix of the (1,1) recurrence with
+// off-diagonal sqrt(k (k+2) / ((2k+1)(2k+3))).
+void gll_nodes(int p, double* x) {
+  x[0] = -1.0;
+  x[p] = 1.0;
+  const int n = p - 1;
+  if (n <= 0) return;
+  std::vector<double> J((size_t)n * n, 0.0), lam, V;
+  for (int k = 1; k < n; ++k) {
+    const double b = sqrt(k * (k + 2.0) / ((2.0 * k + 1.0) * (2.0 * k + 3.0)));
+    J[(k - 1) * n + k] = J[k * n + k - 1] = b;
+  }
+  jacobi_eigen(n, J, lam, V);
+  std::vector<double> srt(lam);
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (srt[j] < srt[i]) { double t = srt[i]; srt[i] = srt[j]; srt[j] = t; }
+  for (int i = 0; i < n; ++i) x[i + 1] = srt[i];
+}
+
+// Lagrange basis on nodes x[0..p]: value and first derivative of l_a at y (product rule)
+void lagrange_eval(int p, const double* x, int a, double y, double* val, double* der) {
+  double v = 1.0, d = 0.0;
+  for (int b = 0; b <= p; ++b) {
+    if (b == a) continue;
+    const double f = (y - x[b]) / (x[a] - x[b]);
+    d = d * f + v / (x[a] - x[b]);
+    v *= f;
+  }
+  *val = v;
+  *der = d;
+}
+
+template <int DIM, int P>
+cvweno_status fill_cg(cvweno_mesh m) {
+  using C = CgTables<DIM, P>;
+  constexpr int N = P + 1;
+  C* t = (C*)calloc(1, sizeof(C));
+  if (!t) return CVWENO_ERR_NOMEM;
+  double xg[N], gx[N], gw[N];
+  gll_nodes(P, xg);
+  gauss_golub_welsch(N, gx, gw);
+  const int NG = 8;
+  double qx[NG], qw[NG];
+  gauss_golub_welsch(NG, qx, qw);
+  for (int a = 0; a < N; ++a) {
+    t->xg[a] = (float)xg[a];
+    m->cg_xg[a] = xg[a];
+    for (int q = 0; q < N; ++q) {
+      double v, d;
+      lagrange_eval(P, xg, a, gx[q], &v, &d);
+      t->Lq[q][a] = (float)v;
+      t->Ldq[q][a] = (float)d;
+    }
+    double wl = 0.0;
+    for (int q = 0; q < NG; ++q) {
+      double va, da;
+      lagrange_eval(P, xg, a, qx[q], &va, &da);
+      wl += qw[q] * va;
+    }
+    t->wl[a] = (float)wl;
+    m->cg_wl[a] = wl;
+  }
+  // V[m][a] = (2m+1)/2 int P_m l_a and M1[a][b] = int l_a l_b, in FP64 then rounded once
+  for (int mm = 0; mm < N; ++mm)
+    for (int a = 0; a < N; ++a) {
+      double acc = 0.0, tab[N * N];
+      for (int q = 0; q < NG; ++q) {
+        double va, da;
+        lagrange_eval(P, xg, a, qx[q], &va, &da);
+        legendre_derivs(qx[q], P, 0, tab);
+        acc += qw[q] * tab[mm] * va;
+      }
+      t->V[mm][a] = (float)(0.5 * (2 * mm + 1) * acc);
+    }
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      double acc = 0.0;
+      for (int q = 0; q < NG; ++q) {
+        double va, da, vb, db;
+        lagrange_eval(P, xg, a, qx[q], &va, &da);
+        lagrange_eval(P, xg, b, qx[q], &vb, &db);
+        acc += qw[q] * va * vb;
+      }
+      t->M1[a][b] = (float)acc;
+    }
+  m->cg_tables = t;
+  m->cg_tables_bytes = sizeof(C);
+  return CVWENO_OK;
+}
+
 }  // namespace
 
 void gauss_rule(int n, double* x, double* w) { gauss_golub_welsch(n, x, w); }
@@ -253,15 +353,16 @@ cvweno_status build_tables(cvweno_mesh m) {
       }
     }
   // reference tabulations
+  cvweno_status st;
   switch (m->dim * 10 + m->p) {
-    case 11: return fill<1, 1>(m);
-    case 12: return fill<1, 2>(m);
-    case 13: return fill<1, 3>(m);
-    case 14: return fill<1, 4>(m);
-    case 21: return fill<2, 1>(m);
-    case 22: return fill<2, 2>(m);
-    case 23: return fill<2, 3>(m);
-    case 24: return fill<2, 4>(m);
+    case 11: st = fill<1, 1>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<1, 1>(m); return st;
+    case 12: st = fill<1, 2>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<1, 2>(m); return st;
+    case 13: st = fill<1, 3>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<1, 3>(m); return st;
+    case 14: st = fill<1, 4>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<1, 4>(m); return st;
+    case 21: st = fill<2, 1>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<2, 1>(m); return st;
+    case 22: st = fill<2, 2>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<2, 2>(m); return st;
+    case 23: st = fill<2, 3>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<2, 3>(m); return st;
+    case 24: st = fill<2, 4>(m); if (st == CVWENO_OK && m->kind == CVWENO_CG) st = fill_cg<2, 4>(m); return st;
     default: return CVWENO_ERR_UNSUPPORTED;
   }
 }

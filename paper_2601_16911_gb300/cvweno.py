@@ -52,6 +52,15 @@ class cvweno_mesh_desc(ctypes.Structure):
     ]
 
 
+class cvweno_batch_plan(ctypes.Structure):
+    _fields_ = [
+        ("schedule", ctypes.c_int), ("tile", ctypes.c_int), ("dynamic", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int), ("ms", ctypes.c_float),
+    ]
+
+
+BATCH_FUSED, BATCH_GROUPED = 0, 1
+
 _VP = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
 _IP = ctypes.POINTER(ctypes.c_int)
@@ -64,6 +73,7 @@ _SIGNATURES = {
     "cvweno_mesh_destroy": (ctypes.c_int, [_VP]),
     "cvweno_mesh_info": (ctypes.c_int, [_VP, _I64P, _I64P, _IP, _I64P, _IP]),
     "cvweno_mesh_tables": (ctypes.c_int, [_VP, _I32P, _I32P, _I32P]),
+    "cvweno_state_size": (ctypes.c_int, [_VP, _I64P]),
     "cvweno_project": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _VP, _VP]),
     "cvweno_vertex_data": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "cvweno_sensor": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -77,6 +87,15 @@ _SIGNATURES = {
     "cvweno_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cvweno_step_static": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), _VP, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int32), _VP]),
+    "cvweno_batch_create": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), ctypes.c_int, ctypes.POINTER(_VP)]),
+    "cvweno_batch_destroy": (ctypes.c_int, [_VP]),
+    "cvweno_batch_offsets": (ctypes.c_int, [_VP, _I64P]),
+    "cvweno_batch_set_plan": (ctypes.c_int, [_VP, ctypes.POINTER(cvweno_batch_plan)]),
+    "cvweno_batch_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(cvweno_batch_plan)]),
+    "cvweno_batch_autotune": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(cvweno_batch_plan), _VP]),
+    "cvweno_batch_residual": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "cvweno_batch_advance": (ctypes.c_int, [_VP, _VP, _DP, ctypes.c_int, _VP]),
+    "cvweno_batch_status_check": (ctypes.c_int, [_VP, _IP, _VP]),
 }
 
 
@@ -163,7 +182,13 @@ class Mesh:
         _check(lib.cvweno_mesh_info(self._h, ctypes.byref(nc), ctypes.byref(nd), ctypes.byref(nv),
                                     ctypes.byref(nverts), ctypes.byref(nq)), "cvweno_mesh_info")
         self.ncells, self.ndof, self.nvars, self.nverts, self.nquad = nc.value, nd.value, nv.value, nverts.value, nq.value
-        self.state_shape = (self.nvars, self.ncells, self.ndof)
+        ns = ctypes.c_int64()
+        _check(lib.cvweno_state_size(self._h, ctypes.byref(ns)), "cvweno_state_size")
+        self.nstate = ns.value
+        if int(d.get("kind", DG)) == CG:
+            self.state_shape = (self.nvars, self.nstate // self.nvars)
+        else:
+            self.state_shape = (self.nvars, self.ncells, self.ndof)
 
     def close(self):
         if self._h:
@@ -277,6 +302,10 @@ def cvweno_mesh_tables(mesh: Mesh):
     return mesh.tables()
 
 
+def cvweno_state_size(mesh: Mesh) -> int:
+    return mesh.nstate
+
+
 def cvweno_project(mesh: Mesh, ic_type: int, params, u, stream=None):
     return mesh.project(ic_type, params, out=u, stream=stream)
 
@@ -335,3 +364,120 @@ def cvweno_step_static(desc: dict, u, dt: float, check_status: bool = False, str
                                      ctypes.byref(st) if check_status else None, _stream(stream)),
            "cvweno_step_static")
     return st.value
+
+
+def _plan_dict(p: cvweno_batch_plan) -> dict:
+    return {f: getattr(p, f) for f, _ in cvweno_batch_plan._fields_}
+
+
+class Batch:
+    """Owning handle of a cvweno_batch: independent 2D DG meshes advanced together.
+    The batch state is one flat float32 CUDA tensor; instance k occupies
+    ``u[offsets[k]:offsets[k+1]]`` in that mesh's state layout."""
+
+    def __init__(self, descs):
+        lib = load()
+        self.descs = [dict(d) for d in descs]
+        arr = (cvweno_mesh_desc * len(descs))(*[make_desc(d) for d in descs])
+        self._h = _VP()
+        _check(lib.cvweno_batch_create(arr, len(descs), ctypes.byref(self._h)), "cvweno_batch_create")
+        off = (ctypes.c_int64 * (len(descs) + 1))()
+        _check(lib.cvweno_batch_offsets(self._h, off), "cvweno_batch_offsets")
+        self.offsets = [int(v) for v in off]
+        self.count = len(descs)
+
+    def close(self):
+        if self._h:
+            load().cvweno_batch_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nstate(self) -> int:
+        return self.offsets[-1]
+
+    def empty_state(self, device="cuda"):
+        return torch.empty(self.nstate, dtype=torch.float32, device=device)
+
+    def view(self, u, k: int):
+        """Instance k's slice of the batch state (a view, flat)."""
+        return u[self.offsets[k]:self.offsets[k + 1]]
+
+    def set_plan(self, **kw):
+        p = cvweno_batch_plan()
+        _check(load().cvweno_batch_get_plan(self._h, ctypes.byref(p)), "cvweno_batch_get_plan")
+        for k, v in kw.items():
+            setattr(p, k, type(getattr(p, k))(v))
+        _check(load().cvweno_batch_set_plan(self._h, ctypes.byref(p)), "cvweno_batch_set_plan")
+
+    def plan(self) -> dict:
+        p = cvweno_batch_plan()
+        _check(load().cvweno_batch_get_plan(self._h, ctypes.byref(p)), "cvweno_batch_get_plan")
+        return _plan_dict(p)
+
+    def autotune(self, u, stream=None) -> dict:
+        p = cvweno_batch_plan()
+        _check(load().cvweno_batch_autotune(self._h, _ptr(u), ctypes.byref(p), _stream(stream)),
+               "cvweno_batch_autotune")
+        return _plan_dict(p)
+
+    def residual(self, u, out=None, stream=None):
+        out = torch.empty_like(u) if out is None else out
+        _check(load().cvweno_batch_residual(self._h, _ptr(u), _ptr(out), _stream(stream)), "cvweno_batch_residual")
+        return out
+
+    def advance(self, u, dt, nsteps: int, stream=None):
+        dts = (ctypes.c_double * self.count)(*[float(x) for x in dt])
+        _check(load().cvweno_batch_advance(self._h, _ptr(u), dts, int(nsteps), _stream(stream)),
+               "cvweno_batch_advance")
+
+    def status_check(self, stream=None) -> int:
+        bad = ctypes.c_int(-1)
+        _check(load().cvweno_batch_status_check(self._h, ctypes.byref(bad), _stream(stream)),
+               "cvweno_batch_status_check")
+        return bad.value
+
+
+def cvweno_batch_create(descs) -> Batch:
+    return Batch(descs)
+
+
+def cvweno_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def cvweno_batch_offsets(batch: Batch):
+    return list(batch.offsets)
+
+
+def cvweno_batch_set_plan(batch: Batch, **plan):
+    batch.set_plan(**plan)
+
+
+def cvweno_batch_get_plan(batch: Batch) -> dict:
+    return batch.plan()
+
+
+def cvweno_batch_autotune(batch: Batch, u, stream=None) -> dict:
+    return batch.autotune(u, stream)
+
+
+def cvweno_batch_residual(batch: Batch, u, dudt, stream=None):
+    batch.residual(u, dudt, stream)
+
+
+def cvweno_batch_advance(batch: Batch, u, dt, nsteps: int, stream=None):
+    batch.advance(u, dt, nsteps, stream)
+
+
+def cvweno_batch_status_check(batch: Batch, stream=None) -> int:
+    return batch.status_check(stream)

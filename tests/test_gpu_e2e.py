@@ -176,7 +176,7 @@ def test_euler_positivity_status():
 
 def test_argument_errors():
     base = I.mesh(2, 8, 8, degree=2, system=I.KPP, lambda_const=1.0)
-    for bad, code in [(dict(nx=0), cv.ERR_ARG), (dict(degree=5), cv.ERR_UNSUPPORTED), (dict(kind=I.CG), cv.ERR_UNSUPPORTED),
+    for bad, code in [(dict(nx=0), cv.ERR_ARG), (dict(degree=5), cv.ERR_UNSUPPORTED), (dict(kind=I.CG, bc=(I.TRANSMISSIVE,) * 4), cv.ERR_UNSUPPORTED), (dict(kind=7), cv.ERR_ARG),
                       (dict(bc=(I.PERIODIC, I.TRANSMISSIVE, I.PERIODIC, I.PERIODIC)), cv.ERR_ARG),
                       (dict(r=2.5), cv.ERR_UNSUPPORTED), (dict(x1=-3.0), cv.ERR_ARG), (dict(dim=3), cv.ERR_ARG)]:
         d = dict(base, **bad)
