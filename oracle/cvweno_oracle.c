@@ -27,6 +27,9 @@
  *   or_sc_weights     Sec. 4, eq. dissrateorig, eq. alphaq, eq. alpha_prelim (stage d)
  *   or_residual       Sec. 2.1 eq. convop, Sec. 2.2 eq. stab/lostab, eq. sdstab (stage e)
  *   or_ssprk3         Sec. 2.2 (SSP Runge-Kutta), Sec. 5 (third order SSP-RK)
+ *   or_limit          Sec. 3 (HWENO limiter: u^e overwritten by u^{e,*} of eq. finalweno
+ *                     built from the average-corrected candidates, the equation for
+ *                     ubar*_i after Fig. stencils)
  *
  * Readings of the paper where it is silent or ambiguous (numbered A1..A20, the same
  * numbers used throughout the project):
@@ -55,6 +58,12 @@
  *   A24 CG SC weights: f_q = |grad u|^2 - gamma_e grad u . P_h grad u can be negative;
  *       alpha_q = 1 unless sum w f > 0 and sum w alpha~ f > 0.
  *   A25 CG initial data: interpolation at the GLL nodes (periodic meshes only).
+ *   A27 HWENO limiter: a cell is overwritten iff gamma_e < C_gamma and it is not flat
+ *       (A7), the same cutoff that turns the SC quadrature on; the limiter acts on the
+ *       result of every RK stage (DG, scalar laws); the artificial viscosity stays as
+ *       sensor_mode sets it (SMOOTH gives the classical limiter-only scheme).
+ *   A28 the overwrite uses the average-corrected candidates, so u^{e,*} keeps the cell
+ *       mean; its weights omega_l are those of the sensor (eq. finalweno).
  * CG is parity-unpinned against the paper's exact values (A12, A13 are readings); its
  * pins are conservation, the sweeps' convergence to the consistent-mass solve, the
  * shared sensor's pins and the design order / Table bur2 magnitudes.
@@ -98,6 +107,7 @@ typedef struct {
   double eps, r, q, gamma_vertex, c_gamma;
   int sc_quadrature, sensor_mode; /* sensor_mode: 0 computed, 1 gamma=1, 2 gamma=0 */
   double lambda_const, gas_gamma, adv_vx, adv_vy;
+  int hweno_limiter; /* 1: or_ssprk3 applies or_limit to every stage result (A27) */
 } or_desc;
 
 /* ------------------------------------------------------------------------- */
@@ -591,7 +601,7 @@ static int or_cell_lambda(const or_mesh* m, const double* u, int e, double* lam)
 /* stage (c): cell-vertex WENO reconstruction, smoothness sensor and viscosity.
  * norm0[e] returns ||u^e||_e (needed by stage d). */
 static int or_sensor_m(const or_mesh* m, const double* u, const double* Tstar, double* gamma, double* nu,
-                       double* norm0, double* lamv) {
+                       double* norm0, double* lamv, double* omega) {
   const or_desc* d = &m->d;
   int nk = or_nk(m), nq = m->nq, ncand = m->ncorner + 1;
   double* Dv = (double*)malloc(sizeof(double) * ncand * nk * nq);
@@ -629,6 +639,8 @@ static int or_sensor_m(const or_mesh* m, const double* u, const double* Tstar, d
       osum += om[l];
     }
     for (int l = 0; l < ncand; ++l) om[l] /= osum;
+    if (omega)
+      for (int l = 0; l < ncand; ++l) omega[(size_t)e * ncand + l] = om[l];
     double diff2 = 0.0;
     for (int t = 0; t < nk; ++t) {
       int jx, jy;
@@ -812,6 +824,68 @@ static int or_residual_m(const or_mesh* m, const double* u, const double* gamma,
 /* ------------------------------------------------------------------------- */
 
 /* Lumped mass ML_j = sum_e int phi_j (Gauss rule, exact). */
+/* HWENO limiter (Sec. 3; readings A27, A28).  out = u except in limited cells, where
+ * the Legendre coefficients of u^{e,*} = sum_l omega_l ubar*_l replace those of u^e:
+ * each vertex candidate (its Taylor form, eq. taylorcand) is projected onto the cell's
+ * Legendre modes by the volume Gauss rule (exact: the Taylor polynomial lies in Q_p),
+ * and the average correction sets every candidate's mean to that of u^e, so mode 0
+ * of the blend is the mean of u^e.  DG, scalar laws.  troubled (may be NULL) marks
+ * the limited cells. */
+static int or_limit_m(const or_mesh* m, const double* u, int all_cells, double* out, int* troubled) {
+  const int nk = or_nk(m), nq = m->nq, ncand = m->ncorner + 1;
+  size_t nT = (size_t)m->ncell * m->ncorner * nk;
+  double* T = (double*)malloc(sizeof(double) * nT);
+  double* beta = (double*)malloc(sizeof(double) * m->ncell * m->ncorner);
+  double* Tstar = (double*)malloc(sizeof(double) * (size_t)m->nvert * nk);
+  double* gamma = (double*)malloc(sizeof(double) * m->ncell);
+  double* nu = (double*)malloc(sizeof(double) * m->ncell);
+  double* norm0 = (double*)malloc(sizeof(double) * m->ncell);
+  double* omega = (double*)malloc(sizeof(double) * (size_t)m->ncell * ncand);
+  int st = OR_OK;
+  if (!T || !beta || !Tstar || !gamma || !nu || !norm0 || !omega) st = OR_ERR_NOMEM;
+  if (!st) {
+    /* the limiter's troubled set comes from the computed sensor whatever sensor_mode
+     * says about the viscosity (A27) */
+    or_mesh mc = *m;
+    mc.d.sensor_mode = 0;
+    or_hermite_m(&mc, u, T, beta);
+    or_vertex_average_m(&mc, T, beta, Tstar);
+    st = or_sensor_m(&mc, u, Tstar, gamma, nu, norm0, NULL, omega);
+  }
+  for (int e = 0; e < m->ncell && !st; ++e) {
+    const double* c0 = or_cell(m, u, 0, e);
+    double* o = out + (size_t)e * m->nd;
+    int lim = all_cells || (gamma[e] < m->d.c_gamma && norm0[e] > 1e-30);
+    if (troubled) troubled[e] = lim;
+    if (!lim) {
+      for (int mi = 0; mi < m->nd; ++mi) o[mi] = c0[mi];
+      continue;
+    }
+    const double* om = omega + (size_t)e * ncand;
+    for (int mi = 0; mi < m->nd; ++mi) {
+      double num = 0.0, den = 0.0;
+      for (int qi = 0; qi < nq; ++qi) {
+        double xi, eta, W;
+        or_qpoint(m, qi, &xi, &eta, &W);
+        double ph = or_dphi(m, mi, 0, 0, xi, eta);
+        double blend = 0.0; /* sum over vertex candidates of omega_l u_l(x_q) */
+        for (int l = 1; l < ncand; ++l) {
+          int c = l - 1, vtx = m->cvert[e * m->ncorner + c];
+          double ox, oy;
+          or_offset_from_corner(m, c, xi, eta, &ox, &oy);
+          blend += om[l] * or_taylor_dj(m, Tstar + (size_t)vtx * nk, 0, 0, ox, oy);
+        }
+        num += W * ph * blend;
+        den += W * ph * ph;
+      }
+      o[mi] = om[0] * c0[mi] + num / den;
+    }
+    o[0] = c0[0]; /* every candidate carries the mean of u^e and the weights sum to 1 */
+  }
+  free(T); free(beta); free(Tstar); free(gamma); free(nu); free(norm0); free(omega);
+  return st;
+}
+
 static void or_cg_lumped_mass(const or_mesh* m, double* ML) {
   for (int j = 0; j < m->nnode; ++j) ML[j] = 0.0;
   for (int e = 0; e < m->ncell; ++e)
@@ -1069,7 +1143,7 @@ int or_residual(const or_desc* d, const double* u, const int* override_troubled,
   }
   or_hermite_m(&m, ul, T, beta);
   or_vertex_average_m(&m, T, beta, Tstar);
-  st = or_sensor_m(&m, ul, Tstar, gamma, nu, norm0, NULL);
+  st = or_sensor_m(&m, ul, Tstar, gamma, nu, norm0, NULL, NULL);
   if (st) goto done;
   if (m.kind == OR_CG) {
     st = or_cg_residual_m(&m, ul, gamma, nu, norm0, override_troubled, alpha, troubled, dudt ? dudt : r);
@@ -1144,6 +1218,18 @@ done:
 }
 
 /* max over cells of lambda_e (reading A2), for the CFL time step */
+/* HWENO limiter of a DG scalar state (see or_limit_m); all_cells = 1 limits every
+ * cell regardless of the sensor. */
+int or_limit(const or_desc* d, const double* u, int all_cells, double* out, int* troubled) {
+  if (d->kind != OR_DG || d->system == OR_EULER) return OR_ERR_UNSUPPORTED;
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  st = or_limit_m(&m, u, all_cells, out, troubled);
+  or_mesh_free(&m);
+  return st;
+}
+
 int or_max_wavespeed(const or_desc* d, const double* u, double* lam_max) {
   or_mesh m;
   int st = or_mesh_init(d, &m);
@@ -1174,21 +1260,35 @@ int or_ssprk3(const or_desc* d, double* u, double dt, int nsteps) {
   double* L = (double*)malloc(sizeof(double) * N);
   double* u1 = (double*)malloc(sizeof(double) * N);
   double* u2 = (double*)malloc(sizeof(double) * N);
-  if (!L || !u1 || !u2) { free(L); free(u1); free(u2); return OR_ERR_NOMEM; }
+  double* lim = (double*)malloc(sizeof(double) * N);
+  if (!L || !u1 || !u2 || !lim) { free(L); free(u1); free(u2); free(lim); return OR_ERR_NOMEM; }
+  /* A27: with the HWENO limiter on, every stage result is limited */
+#define OR_LIMIT_STAGE(x)                                              \
+  if (d->hweno_limiter && !st) {                                       \
+    st = or_limit(d, x, 0, lim, NULL);                                 \
+    if (!st) memcpy(x, lim, sizeof(double) * N);                       \
+  }
   for (int s = 0; s < nsteps && !st; ++s) {
     st = or_residual(d, u, NULL, L, NULL, NULL, NULL, NULL);
     if (st) break;
     for (size_t t = 0; t < N; ++t) u1[t] = u[t] + dt * L[t];
+    OR_LIMIT_STAGE(u1)
+    if (st) break;
     st = or_residual(d, u1, NULL, L, NULL, NULL, NULL, NULL);
     if (st) break;
     for (size_t t = 0; t < N; ++t) u2[t] = 0.75 * u[t] + 0.25 * (u1[t] + dt * L[t]);
+    OR_LIMIT_STAGE(u2)
+    if (st) break;
     st = or_residual(d, u2, NULL, L, NULL, NULL, NULL, NULL);
     if (st) break;
     for (size_t t = 0; t < N; ++t) u[t] = u[t] / 3.0 + 2.0 / 3.0 * (u2[t] + dt * L[t]);
+    OR_LIMIT_STAGE(u)
   }
+#undef OR_LIMIT_STAGE
   free(L);
   free(u1);
   free(u2);
+  free(lim);
   return st;
 }
 
