@@ -92,6 +92,9 @@ typedef struct {
   double lambda_const;  /* > 0: fixed wave speed for nu_e and LLF (KPP: 1); <= 0: computed */
   double gas_gamma;     /* Euler heat capacity ratio */
   double adv_vx, adv_vy;/* LINADV velocity */
+  int hweno_limiter;    /* 1: after every RK stage, cells with computed gamma_e < c_gamma are
+                           overwritten by their average-preserving cell-vertex WENO
+                           reconstruction (Sec. 3; DG scalar laws only); 0: off */
 } cvweno_params;
 
 typedef struct {
@@ -191,6 +194,30 @@ cvweno_status cvweno_max_wavespeed(cvweno_mesh m, const float* u, double* lam, v
 
 /* Synchronise the stream, read and clear the mesh's device status word. */
 cvweno_status cvweno_status_check(cvweno_mesh m, void* stream);
+
+/* HWENO limiter (Sec. 3): out = u, except that every cell whose computed sensor gamma_e
+ * is below c_gamma (or every cell, when all_cells is set) is overwritten by its
+ * cell-vertex WENO reconstruction u^{e,*} (eq. finalweno) built from the
+ * average-corrected vertex candidates, so cell means are kept.  The troubled set
+ * ignores sensor_mode.  u and out: device states of the mesh layout, distinct;
+ * troubled (device [ncells], may be NULL) receives 1 for limited cells.  DG scalar
+ * laws (ERR_UNSUPPORTED otherwise).  Enqueued without synchronisation. */
+cvweno_status cvweno_limit(cvweno_mesh m, const float* u, float* out, int all_cells, int32_t* troubled,
+                           void* stream);
+
+/* Per-launch device times, a measurement aid (the paper has no counterpart).
+ * cvweno_mesh_set_kernel_timing(m, 1) makes every following step of m (cvweno_step,
+ * cvweno_advance) record a timing event before its first kernel and after each kernel
+ * it launches; under stream capture the records become event-record nodes, so a graph
+ * captured from such a step times each of its replays.  cvweno_kernel_times waits for
+ * the last recorded event and writes the durations (ms) of the kernels of the most
+ * recent step into ms[capacity] (host), in launch order: DG and Euler one per stage,
+ * CG six per stage (cells, node right-hand side, then cell mass and node correction
+ * twice); *count receives how many were written.  Timing costs one event record per
+ * kernel; turn it off (enable 0) for production runs.  Turning it off keeps the events
+ * of the last timed step (and of graphs captured while it was on) readable. */
+cvweno_status cvweno_mesh_set_kernel_timing(cvweno_mesh m, int enable);
+cvweno_status cvweno_kernel_times(cvweno_mesh m, float* ms, int capacity, int* count);
 
 /* ---- batches of independent problems ------------------------------------------------
  * Many independent 2D DG meshes of uneven size and degree advanced together: each

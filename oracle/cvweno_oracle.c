@@ -27,6 +27,9 @@
  *   or_sc_weights     Sec. 4, eq. dissrateorig, eq. alphaq, eq. alpha_prelim (stage d)
  *   or_residual       Sec. 2.1 eq. convop, Sec. 2.2 eq. stab/lostab, eq. sdstab (stage e)
  *   or_ssprk3         Sec. 2.2 (SSP Runge-Kutta), Sec. 5 (third order SSP-RK)
+ *   or_features       inputs of the surrogate sensor (not in the paper): per corner
+ *                     vertex candidate (eq. taylorcand) mean minus cell mean and
+ *                     h-scaled gradient at the vertex, over ||u^e||_e + eps (eq. snorm)
  *   or_limit          Sec. 3 (HWENO limiter: u^e overwritten by u^{e,*} of eq. finalweno
  *                     built from the average-corrected candidates, the equation for
  *                     ubar*_i after Fig. stencils)
@@ -1218,6 +1221,65 @@ done:
 }
 
 /* max over cells of lambda_e (reading A2), for the CFL time step */
+/* Surrogate-sensor inputs of every cell (2D DG scalar).  For corner c of K_e with
+ * vertex candidate u*_v (Taylor form, eq. taylorcand):
+ *   feats[e][3c+0] = ((1/|K_e|) int_{K_e} u*_v - mean of u^e) / s_e
+ *   feats[e][3c+1] = h_e d_x u*_v(x_v) / s_e,   feats[e][3c+2] = h_e d_y u*_v(x_v) / s_e
+ * with s_e = ||u^e||_e + eps (element semi-norm, eq. snorm), each clamped to [-8, 8]
+ * (reading S2).  gamma (may be NULL) receives the computed sensor (eq. gamma) of every
+ * cell, whatever sensor_mode says, and norm (may be NULL) ||u^e||_e. */
+int or_features(const or_desc* d, const double* u, double* feats, double* gamma_out, double* norm_out) {
+  if (d->dim != 2 || d->kind != OR_DG || d->system == OR_EULER) return OR_ERR_UNSUPPORTED;
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  m.d.sensor_mode = 0;
+  const int nk = or_nk(&m), nq = m.nq;
+  size_t nT = (size_t)m.ncell * m.ncorner * nk;
+  double* T = (double*)malloc(sizeof(double) * nT);
+  double* beta = (double*)malloc(sizeof(double) * m.ncell * m.ncorner);
+  double* Tstar = (double*)malloc(sizeof(double) * (size_t)m.nvert * nk);
+  double* gamma = (double*)malloc(sizeof(double) * m.ncell);
+  double* nu = (double*)malloc(sizeof(double) * m.ncell);
+  double* norm0 = (double*)malloc(sizeof(double) * m.ncell);
+  if (!T || !beta || !Tstar || !gamma || !nu || !norm0) st = OR_ERR_NOMEM;
+  if (!st) {
+    or_hermite_m(&m, u, T, beta);
+    or_vertex_average_m(&m, T, beta, Tstar);
+    st = or_sensor_m(&m, u, Tstar, gamma, nu, norm0, NULL, NULL);
+  }
+  for (int e = 0; e < m.ncell && !st; ++e) {
+    const double* c0 = or_cell(&m, u, 0, e);
+    double vol = 0.0, mean_u = 0.0;
+    for (int qi = 0; qi < nq; ++qi) {
+      double xi, eta, W;
+      or_qpoint(&m, qi, &xi, &eta, &W);
+      vol += W;
+      mean_u += W * or_du(&m, c0, 0, 0, xi, eta);
+    }
+    mean_u /= vol;
+    const double s = norm0[e] + d->eps;
+    for (int c = 0; c < 4; ++c) {
+      const double* Ts = Tstar + (size_t)m.cvert[e * 4 + c] * nk;
+      double mc = 0.0;
+      for (int qi = 0; qi < nq; ++qi) {
+        double xi, eta, W, ox, oy;
+        or_qpoint(&m, qi, &xi, &eta, &W);
+        or_offset_from_corner(&m, c, xi, eta, &ox, &oy);
+        mc += W * or_taylor_dj(&m, Ts, 0, 0, ox, oy);
+      }
+      double f[3] = {(mc / vol - mean_u) / s, m.h * or_taylor_dj(&m, Ts, 1, 0, 0.0, 0.0) / s,
+                     m.h * or_taylor_dj(&m, Ts, 0, 1, 0.0, 0.0) / s};
+      for (int j = 0; j < 3; ++j) feats[(size_t)e * 12 + 3 * c + j] = fmax(-8.0, fmin(8.0, f[j]));
+    }
+    if (gamma_out) gamma_out[e] = gamma[e];
+    if (norm_out) norm_out[e] = norm0[e];
+  }
+  free(T); free(beta); free(Tstar); free(gamma); free(nu); free(norm0);
+  or_mesh_free(&m);
+  return st;
+}
+
 /* HWENO limiter of a DG scalar state (see or_limit_m); all_cells = 1 limits every
  * cell regardless of the sensor. */
 int or_limit(const or_desc* d, const double* u, int all_cells, double* out, int* troubled) {

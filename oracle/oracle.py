@@ -94,6 +94,7 @@ def _load():
                 "or_residual_given": [d, dp, dp, dp, dp, dp],
                 "or_sc_weights": [d, dp, dp, dp, ip],
                 "or_limit": [d, dp, ctypes.c_int, dp, ip],
+                "or_features": [d, dp, dp, dp, dp],
                 "or_max_wavespeed": [d, dp, dp],
                 "or_ssprk3": [d, dp, ctypes.c_double, ctypes.c_int],
                 "or_mass_total": [d, dp, dp],
@@ -249,6 +250,17 @@ def limit(d: dict, u, all_cells: bool = False):
     tr = np.zeros(c["ncell"], np.int32)
     _check(_load().or_limit(ctypes.byref(_cdesc(d)), _dp(uu), 1 if all_cells else 0, _dp(out), _ip(tr)), "limit")
     return out.reshape(np.shape(u)), tr
+
+
+def features(d: dict, u):
+    """Surrogate-sensor inputs (ncell, 12), the computed sensor gamma (ncell) and the
+    element semi-norms ||u^e||_e (ncell); see or_features."""
+    c = counts(d)
+    f = np.zeros((c["ncell"], 12))
+    g = np.zeros(c["ncell"])
+    nrm = np.zeros(c["ncell"])
+    _check(_load().or_features(ctypes.byref(_cdesc(d)), _dp(_u(u)), _dp(f), _dp(g), _dp(nrm)), "features")
+    return f, g, nrm
 
 
 def max_wavespeed(d: dict, u) -> float:

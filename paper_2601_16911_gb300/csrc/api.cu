@@ -229,6 +229,7 @@ StageArgs base_args(const cvweno_mesh_s* m) {
   a.lambda_const = (float)p.lambda_const;
   a.sc = p.sc_quadrature;
   a.sensor_mode = p.sensor_mode;
+  a.limit_all = 0;
   a.adv_vx = (float)p.adv_vx;
   a.adv_vy = (float)p.adv_vy;
   a.gas_gamma = (float)p.gas_gamma;
@@ -244,8 +245,10 @@ StageArgs base_args(const cvweno_mesh_s* m) {
 }
 
 cudaError_t launch(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
-  if (m->kind == CVWENO_CG) return launch_stage_cg(m, a, s);
-  return m->desc.system == CVWENO_EULER ? launch_stage_euler(m, a, s) : launch_stage(m, a, s);
+  if (m->kind == CVWENO_CG) return launch_stage_cg(m, a, s);  // marks after each kernel itself
+  cudaError_t e = m->desc.system == CVWENO_EULER ? launch_stage_euler(m, a, s) : launch_stage(m, a, s);
+  kernel_mark(m, s);
+  return e;
 }
 
 cvweno_status read_status(cvweno_mesh m, cudaStream_t s) {
@@ -276,7 +279,30 @@ cvweno_status rk_stage(cvweno_mesh m, const float* in, const float* un, float* o
   return cuda_status(launch(m, a, s));
 }
 
+cvweno_status limit_stage(cvweno_mesh m, const float* in, float* out, cudaStream_t s) {
+  StageArgs a = base_args(m);
+  a.u_in = in;
+  a.u_out = out;
+  a.mode = kModeLimit;
+  return cuda_status(launch(m, a, s));
+}
+
 cvweno_status enqueue_step(cvweno_mesh m, float* u, float dt, cudaStream_t s) {
+  if (m->timing) {
+    m->tcount = 0;
+    kernel_mark(m, s);
+  }
+  if (m->desc.params.hweno_limiter) {
+    // every stage result is limited (reading A27); the limiter reads neighbours, so it
+    // runs out of place: stages write d_u1, the limiter writes d_u2 (the last one u)
+    cvweno_status st = rk_stage(m, u, u, m->d_u1, 0.0f, 1.0f, dt, s);
+    if (st == CVWENO_OK) st = limit_stage(m, m->d_u1, m->d_u2, s);
+    if (st == CVWENO_OK) st = rk_stage(m, m->d_u2, u, m->d_u1, 0.75f, 0.25f, dt, s);
+    if (st == CVWENO_OK) st = limit_stage(m, m->d_u1, m->d_u2, s);
+    if (st == CVWENO_OK) st = rk_stage(m, m->d_u2, u, m->d_u1, 1.0f / 3.0f, 2.0f / 3.0f, dt, s);
+    if (st == CVWENO_OK) st = limit_stage(m, m->d_u1, u, s);
+    return st;
+  }
   cvweno_status st = rk_stage(m, u, u, m->d_u1, 0.0f, 1.0f, dt, s);
   if (st == CVWENO_OK) st = rk_stage(m, m->d_u1, u, m->d_u2, 0.75f, 0.25f, dt, s);
   if (st == CVWENO_OK) st = rk_stage(m, m->d_u2, u, u, 1.0f / 3.0f, 2.0f / 3.0f, dt, s);
@@ -287,6 +313,16 @@ cvweno_status enqueue_step(cvweno_mesh m, float* u, float dt, cudaStream_t s) {
 
 namespace cvw {
 StageArgs stage_base_args(const cvweno_mesh_s* m) { return base_args(m); }
+
+void kernel_mark(const cvweno_mesh_s* mc, cudaStream_t s) {
+  cvweno_mesh_s* m = const_cast<cvweno_mesh_s*>(mc);
+  if (!m->timing || m->tcount >= kMaxMarks) return;
+  // inside stream capture the record becomes an event-record node of the graph, so the
+  // events time every replay
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  cudaEventRecordWithFlags(m->tev[m->tcount++], s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0);
+}
 }  // namespace cvw
 
 extern "C" {
@@ -337,6 +373,8 @@ cvweno_status cvweno_mesh_destroy(cvweno_mesh m) {
   cudaFree(m->d_cg_ml);
   cudaFreeHost(m->h_status);
   cudaFreeHost(m->h_red);
+  for (int i = 0; i < kMaxMarks; ++i)
+    if (m->tev[i]) cudaEventDestroy(m->tev[i]);
   free(m->cell_vertices);
   free(m->vertex_cells);
   free(m->colour);
@@ -362,6 +400,8 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   if (!(p.eps > 0.0) || !(p.q >= 1.0) || !(p.gamma_vertex > 0.0) || (1 << d->dim) * p.gamma_vertex >= 1.0)
     return CVWENO_ERR_ARG;
   if (p.sensor_mode < 0 || p.sensor_mode > 2) return CVWENO_ERR_ARG;
+  if (p.hweno_limiter != 0 && p.hweno_limiter != 1) return CVWENO_ERR_ARG;
+  if (p.hweno_limiter && (d->kind != CVWENO_DG || d->system == CVWENO_EULER)) return CVWENO_ERR_UNSUPPORTED;
   if (d->kind != CVWENO_DG && d->kind != CVWENO_CG) return CVWENO_ERR_ARG;
   // CG: scalar laws on periodic meshes (no boundary flux term is implemented)
   if (d->kind == CVWENO_CG && (d->system == CVWENO_EULER || d->bc[0] != CVWENO_PERIODIC ||
@@ -530,6 +570,19 @@ cvweno_status cvweno_sensor(cvweno_mesh m, const float* u, float* gamma, float* 
   return cuda_status(launch(m, a, S(stream)));
 }
 
+cvweno_status cvweno_limit(cvweno_mesh m, const float* u, float* out, int all_cells, int32_t* troubled,
+                           void* stream) {
+  if (!m || !u || !out || u == out) return CVWENO_ERR_ARG;
+  if (m->kind != CVWENO_DG || m->desc.system == CVWENO_EULER) return CVWENO_ERR_UNSUPPORTED;
+  StageArgs a = base_args(m);
+  a.u_in = u;
+  a.u_out = out;
+  a.troubled_out = troubled;
+  a.limit_all = all_cells ? 1 : 0;
+  a.mode = kModeLimit;
+  return cuda_status(launch(m, a, S(stream)));
+}
+
 cvweno_status cvweno_residual_ex(cvweno_mesh m, const float* u, const int32_t* troubled_override, float* dudt,
                                  float* gamma, float* nu, float* alpha, int32_t* troubled, void* stream) {
   if (!m || !u || !dudt || u == dudt) return CVWENO_ERR_ARG;
@@ -624,6 +677,28 @@ cvweno_status cvweno_mass_total(cvweno_mesh m, const float* u, double* totals, v
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return CVWENO_ERR_CUDA;
   for (int v = 0; v < m->nvar; ++v) totals[v] = m->h_red[v] * vol;
+  return CVWENO_OK;
+}
+
+cvweno_status cvweno_mesh_set_kernel_timing(cvweno_mesh m, int enable) {
+  if (!m) return CVWENO_ERR_ARG;
+  if (enable && !m->tev[0])
+    for (int i = 0; i < kMaxMarks; ++i)
+      if (cudaEventCreate(&m->tev[i]) != cudaSuccess) return CVWENO_ERR_CUDA;
+  m->timing = enable ? 1 : 0;
+  if (enable) m->tcount = 0;  // disabling keeps the last step's events readable
+  return CVWENO_OK;
+}
+
+cvweno_status cvweno_kernel_times(cvweno_mesh m, float* ms, int capacity, int* count) {
+  if (!m || !count || capacity < 0 || (capacity > 0 && !ms)) return CVWENO_ERR_ARG;
+  *count = 0;
+  if (!m->tev[0] || m->tcount < 2) return CVWENO_OK;
+  if (cudaEventSynchronize(m->tev[m->tcount - 1]) != cudaSuccess) return CVWENO_ERR_CUDA;
+  const int n = m->tcount - 1 < capacity ? m->tcount - 1 : capacity;
+  for (int i = 0; i < n; ++i)
+    if (cudaEventElapsedTime(&ms[i], m->tev[i], m->tev[i + 1]) != cudaSuccess) return CVWENO_ERR_CUDA;
+  *count = n;
   return CVWENO_OK;
 }
 

@@ -408,7 +408,7 @@ cvweno_status cvweno_batch_create(const cvweno_mesh_desc* descs, int count, cvwe
   for (int k = 0; k < count; ++k) {
     const cvweno_mesh_desc& d = descs[k];
     if (d.dim != 2 || d.kind != CVWENO_DG) return CVWENO_ERR_UNSUPPORTED;
-    if (d.system != CVWENO_BURGERS) return CVWENO_ERR_UNSUPPORTED;
+    if (d.system != CVWENO_BURGERS || d.params.hweno_limiter) return CVWENO_ERR_UNSUPPORTED;
     if (d.nx < 1 || d.ny < 1) return CVWENO_ERR_ARG;
     const double dx = (d.x1 - d.x0) / d.nx, dy = (d.y1 - d.y0) / d.ny;
     if (!(fabs(dx - dy) <= 1e-12 * fabs(dx))) return CVWENO_ERR_ARG;

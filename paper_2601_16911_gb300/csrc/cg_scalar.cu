@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
 #pragma unroll
   for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + hc];
   float n0;
-  const float gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0);
+  float wstar[DgTables<DIM, P>::NS];  // unused: CG has no limiter mode
+  const float gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
   const Law law(a, c[0]);
 
   // lambda_e over the volume and face Gauss nodes of the cell polynomial
@@ -525,13 +526,17 @@ cudaError_t launch_cg_t(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t
   dim3 grid((a.nx + TX - 1) / TX, DIM == 2 ? (a.ny + TY - 1) / TY : 1);
   k1<<<grid, TX * TY, smem, s>>>(a, T, C);
   if (a.mode & kModeSensorOnly) return cudaGetLastError();
+  kernel_mark(m, s);
   const int64_t nn = m->nnode, nc = m->ncell;
   const int bn = (int)((nn + 255) / 256 < 4096 ? (nn + 255) / 256 : 4096);
   const int bc = (int)((nc + 255) / 256 < 4096 ? (nc + 255) / 256 : 4096);
   cg_node_rhs<DIM, P, SYS><<<bn, 256, 0, s>>>(a, C);
+  kernel_mark(m, s);
   for (int sweep = 0; sweep < 2; ++sweep) {
     cg_cell_mass<DIM, P><<<bc, 256, 0, s>>>(a, C);
+    kernel_mark(m, s);
     cg_node_correct<DIM, P><<<bn, 256, 0, s>>>(a, C, sweep == 1);
+    kernel_mark(m, s);
   }
   return cudaGetLastError();
 }

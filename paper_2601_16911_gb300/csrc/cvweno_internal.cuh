@@ -9,6 +9,7 @@
 namespace cvw {
 
 constexpr int kMaxP = 4;
+constexpr int kMaxMarks = 24;  // timing events per step: 3 stages x (up to 6 kernels + 1) + 1
 
 // Status bits raised by kernels in the mesh's device status word.
 enum : int { kStatNonfinite = 1, kStatPositivity = 2 };
@@ -87,6 +88,7 @@ struct StageArgs {
   float eps, gamma_vertex, c_gamma, q, lambda_const;
   int r;
   int sc, sensor_mode;
+  int limit_all;       // kModeLimit: limit every cell, not only gamma_e < c_gamma
   float adv_vx, adv_vy;
   float gas_gamma;
   // CG only: nodal lattice and the per-stage work arrays
@@ -102,6 +104,7 @@ enum : int {
   kModeResidual = 1,   // write dudt to u_out
   kModeRK = 2,         // write u_n + rk_b (u_in + dt L - u_n) (or u_in + dt L) to u_out
   kModeSensorOnly = 4, // stop after stage (c) (gamma, nu, lambda outputs)
+  kModeLimit = 8,      // HWENO limiter: write u_in or its reconstruction u^{e,*} to u_out
 };
 
 }  // namespace cvw
@@ -142,6 +145,11 @@ struct cvweno_mesh_s {
   double* d_red;           // reduction scratch
   int* d_status;
   int* h_status;           // pinned
+  // optional per-launch timing (cvweno_mesh_set_kernel_timing): events recorded
+  // between the kernels of one step, read back by cvweno_kernel_times
+  int timing;
+  int tcount;
+  cudaEvent_t tev[cvw::kMaxMarks];
   double* h_red;           // pinned
 };
 
@@ -157,4 +165,6 @@ cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaS
 cudaError_t launch_stage_cg(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 // api.cu: the stage arguments common to every launch on mesh m (no state pointers, no RK)
 StageArgs stage_base_args(const cvweno_mesh_s* m);
+// api.cu: with kernel timing on, records the next timing event of the step on s
+void kernel_mark(const cvweno_mesh_s* m, cudaStream_t s);
 }  // namespace cvw

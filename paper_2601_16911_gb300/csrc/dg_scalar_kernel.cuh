@@ -269,7 +269,8 @@ __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTa
 // and the sensor gamma_e (eq. gamma); n0 returns ||u^e||_e.
 template <int DIM, int P, int TX, int TY>
 __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<DIM, P>& T, const float* st,
-                                             const float* sA, const float* c, int tx, int ty, float& n0) {
+                                             const float* sA, const float* c, int tx, int ty, float& n0,
+                                             float* wstar) {
   using L = TileLayout<DIM, P, TX, TY>;
   constexpr int NS = L::NS, NC = L::NC, NSP = L::NSP, VXT = L::VXT, NVT = L::NVT;
   float w0[NS];
@@ -322,10 +323,12 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     float df = w0[i] - S[i] * inv;
+    wstar[i] = S[i] * inv;  // semi-norm coordinates of u^{e,*} (dead unless the limiter reads it)
     d2 = fmaf(df, df, d2);
   }
-  if (a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
-  if (a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
+  const bool forced = !(a.mode & kModeLimit);  // the limiter always uses the computed sensor
+  if (forced && a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
+  if (forced && a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
   if (n0 <= 1e-30f) return 1.0f;
   return 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
 }
@@ -387,7 +390,38 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 
   // ---- (c) cell-vertex reconstruction and sensor --------------------------------------
   float n0;
-  const float gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0);
+  float wstar[L::NS];
+  const float gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
+
+  // ---- HWENO limiter (Sec. 3): u^{e,*} = mean of u^e + R^{-1} w* on the other modes ----
+  if (a.mode & kModeLimit) {
+    const bool lim = a.limit_all || (gam < a.c_gamma && n0 > 1e-30f);
+    float* o = a.u_out + cell * ND;
+    if (!lim) {
+#pragma unroll
+      for (int m = 0; m < ND; ++m) o[m] = c[m];
+    } else {
+      constexpr int NS = L::NS;
+      float x[NS];
+#pragma unroll
+      for (int i = NS - 1; i >= 0; --i) {  // back substitution with the upper-triangular R
+        float acc = wstar[i];
+#pragma unroll
+        for (int j = i + 1; j < NS; ++j) acc = fmaf(-T.R[i][j], x[j], acc);
+        x[i] = acc / T.R[i][i];
+      }
+      o[0] = c[0];
+      bool bad = !isfinite(c[0]);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        o[i + 1] = x[i];
+        bad |= !isfinite(x[i]);
+      }
+      if (bad) atomicOr(a.status, kStatNonfinite);
+    }
+    if (a.troubled_out) a.troubled_out[cell] = lim ? 1 : 0;
+    return;
+  }
 
   // ---- own trace polynomials along each face, as deviations from the mean -------------------
   // u(x) = ubar + (non-mean modes): rounding stays relative to the in-cell variation.

@@ -40,6 +40,7 @@ class cvweno_params(ctypes.Structure):
         ("sc_quadrature", ctypes.c_int), ("sensor_mode", ctypes.c_int),
         ("lambda_const", ctypes.c_double), ("gas_gamma", ctypes.c_double),
         ("adv_vx", ctypes.c_double), ("adv_vy", ctypes.c_double),
+        ("hweno_limiter", ctypes.c_int),
     ]
 
 
@@ -87,6 +88,9 @@ _SIGNATURES = {
     "cvweno_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cvweno_step_static": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), _VP, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int32), _VP]),
+    "cvweno_limit": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "cvweno_mesh_set_kernel_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "cvweno_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _IP]),
     "cvweno_batch_create": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), ctypes.c_int, ctypes.POINTER(_VP)]),
     "cvweno_batch_destroy": (ctypes.c_int, [_VP]),
     "cvweno_batch_offsets": (ctypes.c_int, [_VP, _I64P]),
@@ -275,6 +279,24 @@ class Mesh:
         _check(load().cvweno_max_wavespeed(self._h, _ptr(u), ctypes.byref(lam), _stream(stream)),
                "cvweno_max_wavespeed")
         return lam.value
+
+    def limit(self, u, all_cells: bool = False, out=None, stream=None):
+        """HWENO limiter (Sec. 3): (limited state, int32 flags of the limited cells)."""
+        out = torch.empty_like(u) if out is None else out
+        tr = torch.empty(self.ncells, dtype=torch.int32, device=u.device)
+        _check(load().cvweno_limit(self._h, _ptr(u), _ptr(out), 1 if all_cells else 0, _ptr(tr), _stream(stream)),
+               "cvweno_limit")
+        return out, tr
+
+    def set_kernel_timing(self, enable: bool = True):
+        _check(load().cvweno_mesh_set_kernel_timing(self._h, 1 if enable else 0), "cvweno_mesh_set_kernel_timing")
+
+    def kernel_times(self):
+        """Durations (ms) of the kernels of the most recent step, in launch order."""
+        buf = (ctypes.c_float * 64)()
+        n = ctypes.c_int(0)
+        _check(load().cvweno_kernel_times(self._h, buf, 64, ctypes.byref(n)), "cvweno_kernel_times")
+        return [buf[i] for i in range(n.value)]
 
     def status_check(self, stream=None):
         _check(load().cvweno_status_check(self._h, _stream(stream)), "cvweno_status_check")
@@ -481,3 +503,16 @@ def cvweno_batch_advance(batch: Batch, u, dt, nsteps: int, stream=None):
 
 def cvweno_batch_status_check(batch: Batch, stream=None) -> int:
     return batch.status_check(stream)
+
+
+def cvweno_mesh_set_kernel_timing(mesh: Mesh, enable: bool = True):
+    mesh.set_kernel_timing(enable)
+
+
+def cvweno_kernel_times(mesh: Mesh):
+    return mesh.kernel_times()
+
+
+def cvweno_limit(mesh: Mesh, u, out, all_cells: bool = False, troubled=None, stream=None):
+    _check(load().cvweno_limit(mesh.handle, _ptr(u), _ptr(out), 1 if all_cells else 0, _ptr(troubled),
+                               _stream(stream)), "cvweno_limit")

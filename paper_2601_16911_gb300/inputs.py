@@ -125,3 +125,16 @@ def burgers2d_batch(seed: int, count: int = 64, nmin: int = 64, nmax: int = 512)
         p = g.randint(1, 4)
         out.append((mesh(2, n, n, degree=p, system=BURGERS), (IC_FOURIER, fourier_modes(g))))
     return out
+
+
+def mlp_init(seed: int) -> "list[float]":
+    """Initial parameters of the 12 -> 64 -> 64 -> 2 surrogate network in its flat layout
+    (W1 (64,12), b1, W2 (64,64), b2, W3 (2,64), b3): weights uniform in +-sqrt(6/(fan_in +
+    fan_out)), biases zero.  Both the oracle and the GPU training start from these."""
+    g = SplitMix64(seed)
+    out = []
+    for rows, cols in ((64, 12), (64, 64), (2, 64)):
+        a = math.sqrt(6.0 / (rows + cols))
+        out += [g.uniform(-a, a) for _ in range(rows * cols)]
+        out += [0.0] * rows
+    return out
