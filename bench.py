@@ -58,6 +58,10 @@ def problems(workload: str, n_scale: int | None = None):
     elif workload == "burgers1d":
         d, ic = I.burgers1d_step(SEED, nx=128, degree=2)
         out.append(("DG-P2", d, ic, 0.1 * (1.0 / 128) / 1.5))
+    elif workload == "surrogate":
+        n = n_scale or 1024
+        d, ic = I.kpp(4, n=n, degree=2)
+        out.append(("DG-Q2-surrogate", d, ic, cfl_dt(2, n)))
     elif workload == "batched":
         seen = set()
         for k, (d, ic) in enumerate(I.burgers2d_batch(SEED)):
@@ -81,6 +85,10 @@ WORKLOADS = {
     "euler": "2D Euler (gamma=1.4), four seeded constant quadrants, [0,1]^2 transmissive, 512x512 quads, DG Q3 "
              "(one SSP-RK3 step), FP32",
     "burgers1d": "1D Burgers, u0 = sin(2 pi x) + 0.5 H(x - x0), periodic [0,1], 128 cells, DG P2 (one SSP-RK3 step), FP32",
+    "surrogate": "KPP 2D, f=(sin u, cos u), [-2,2]^2 periodic, 1024x1024 quads, DG Q2, seeded circle datum, one "
+                 "SSP-RK3 step per benchmark step with the surrogate sensor network (12-64-64-2, bf16 tensor-core "
+                 "inference fused into stage c, plain sensor below confidence 0.5), trained on the GPU on KPP 256^2 "
+                 "Q2 runs of other seeds; FP32",
     "batched": "64 independent 2D Burgers problems, periodic [0,1]^2, N^2 quads with N ~ U{64..512}, DG Q_p with "
                "p ~ U{1..4}, seeded sums of 4 Fourier modes; one SSP-RK3 step of all 64 per benchmark step, FP32",
 }
@@ -204,6 +212,7 @@ KERNEL_SOURCES = {
     "dg_scalar_stage_p2_burgers1d": ["dg_scalar_kernel.cuh", "dg_scalar_launch.cuh", "dg_scalar_1d.cu"],
     "dg_euler_stage_q3_euler512": ["dg_scalar_kernel.cuh", "dg_euler.cu"],
     "dg_scalar_batch_burgers64": ["dg_scalar_kernel.cuh", "batch.cu"],
+    "dg_scalar_stage_q2_surrogate_kpp1024": ["dg_scalar_kernel.cuh", "mlp_mma.cuh", "dg_scalar_2d_mlp.cu"],
     "cg_stage_cells_q3_kpp256": ["dg_scalar_kernel.cuh", "cg_scalar.cu"],
 }
 
@@ -275,7 +284,7 @@ def cpu_baseline_sample(workload: str):
 
     from oracle import oracle as O
 
-    n = {"kpp": 128, "euler": 64, "burgers1d": None, "batched": 48}[workload]
+    n = {"kpp": 128, "euler": 64, "burgers1d": None, "batched": 48, "surrogate": 96}[workload]
     work = [(d, O.project(d, *ic), dt) for _, d, ic, dt in problems(workload, n)]
     t0 = time.perf_counter()
     units = 0
@@ -347,6 +356,8 @@ def run_gpu(args):
     cv.load()
     if args.workload == "batched":
         return run_gpu_batched(args, ws, rank, local, dev)
+    if args.workload == "surrogate":
+        return run_gpu_surrogate(args, ws, rank, local, dev)
 
     meshes, states, dts, graphs, inits, labels = [], [], [], [], [], []
     for label, d, ic, dt in problems(args.workload):
@@ -694,6 +705,220 @@ def run_gpu_batched(args, ws, rank, local, dev):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def surrogate_training_set(n=256, seeds=(0, 1, 2, 3), snapshots=12, steps_between=150, max_samples=1_000_000):
+    """Inputs and plain-sensor targets from KPP n^2 DG Q2 runs of the given seeds (not the
+    evaluation seed), sampled every steps_between steps; the troubled-side cells
+    (gamma < 0.999) are all kept and the rest subsampled to at most max_samples in all,
+    in a seeded shuffled order."""
+    import torch
+
+    from paper_2601_16911_gb300 import cvweno as cv
+    from paper_2601_16911_gb300 import inputs as I
+    X, y = [], []
+    for seed in seeds:
+        d, ic = I.kpp(seed, n=n, degree=2)
+        m = cv.Mesh(d)
+        u = m.project(*ic)
+        for _ in range(snapshots):
+            f, g = m.features(u)
+            X.append(f)
+            y.append(g)
+            m.advance(u, cfl_dt(2, n), steps_between)
+        m.status_check()
+        m.close()
+    X = torch.cat(X)
+    y = torch.cat(y)
+    gen = torch.Generator(device="cpu").manual_seed(1234)
+    rough = torch.nonzero(y < 0.999).flatten().cpu()
+    smooth = torch.nonzero(y >= 0.999).flatten().cpu()
+    keep_smooth = max(0, min(len(smooth), max_samples - len(rough), 3 * len(rough)))
+    idx = torch.cat([rough, smooth[torch.randperm(len(smooth), generator=gen)[:keep_smooth]]])
+    idx = idx[torch.randperm(len(idx), generator=gen)][:max_samples].to(X.device)
+    return X[idx].contiguous(), y[idx].contiguous(), {"total_cells": int(y.numel()), "rough": int(len(rough)),
+                                                      "samples": int(idx.numel())}
+
+
+def run_gpu_surrogate(args, ws, rank, local, dev):
+    """Config 5: the plain KPP 1024^2 Q2 step against the same step with the surrogate
+    sensor fused into stage (c), after training the network on the GPU."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2601_16911_gb300 import cvweno as cv
+    from paper_2601_16911_gb300 import inputs as I
+
+    t0 = time.perf_counter()
+    X, y, tinfo = surrogate_training_set()
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = cv.Mlp(I.mlp_init(0))
+    t0 = time.perf_counter()
+    epochs = 12
+    last_loss = net.train(X, y, batch=4096, epochs=epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # held-out quality: a seed not trained on, at the evaluation state
+    (label, d, ic, dt), = problems("surrogate")
+    m_plain = cv.Mesh(d)
+    m_surr = cv.Mesh(d)
+    m_surr.set_surrogate(net, 0.5)
+    u0 = m_plain.project(*ic)
+    torch.cuda.synchronize()
+    f, g_plain = m_plain.features(u0)
+    o = net.infer(f)
+    g_hat = torch.sigmoid(o[:, 0])
+    conf = torch.sigmoid(o[:, 1])
+    confident = conf >= 0.5
+    dg = (g_hat - g_plain).abs()
+    quality = {"confident_fraction": float(confident.float().mean()),
+               "mean_abs_gamma_err_confident": float(dg[confident].mean()) if bool(confident.any()) else None,
+               "max_abs_gamma_err_confident": float(dg[confident].max()) if bool(confident.any()) else None,
+               "sc_decision_disagreements": int(((g_hat < d["c_gamma"]) != (g_plain < d["c_gamma"]))[confident].sum()),
+               "troubled_cells_plain": int((g_plain < d["c_gamma"]).sum())}
+    # graphs of one step, plain and surrogate
+    u_p, u_s = u0.clone(), u0.clone()
+    for m, u in ((m_plain, u_p), (m_surr, u_s)):
+        m.advance(u, dt, 1)
+    torch.cuda.synchronize()
+    graphs = []
+    for m, u in ((m_plain, u_p), (m_surr, u_s)):
+        gph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gph):
+            m.advance(u, dt, 1)
+        graphs.append(gph)
+    m_surr.set_kernel_timing(True)
+    g_dom = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_dom):
+        m_surr.advance(u_s, dt, 1)
+    m_surr.set_kernel_timing(False)
+    u_p.copy_(u0)
+    u_s.copy_(u0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(gph, nsteps, sampler=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        for i in range(nsteps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            gph.replay()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk = sampler.stop() if sampler else None
+        return [a.elapsed_time(z) for a, z in ev], clk
+
+    for gph in graphs:
+        timed(gph, max(args.warmup, 3))
+    u_p.copy_(u0)
+    u_s.copy_(u0)
+    net.fallbacks(reset=True)
+    ms_s, clocks = timed(graphs[1], args.steps, ClockSampler(local))
+    fallbacks = net.fallbacks(reset=True)
+    ms_p, _ = timed(graphs[0], args.steps)
+    m_plain.status_check()
+    m_surr.status_check()
+    units = 3 * m_plain.nstate
+    step_s = statistics.mean(ms_s)
+    step_p = statistics.mean(ms_p)
+    value = units / (step_s / 1000.0)
+    plain_value = units / (step_p / 1000.0)
+    # the two runs after the same steps (warm-up + timed) from the same start
+    l1_full = O.l1_diff(d, u_s.cpu().numpy().astype(np.float64), u_p.cpu().numpy().astype(np.float64)) / \
+        O.l1_diff(d, u_p.cpu().numpy().astype(np.float64), np.zeros(tuple(u_p.shape)))
+    dom_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        g_dom.replay()
+        kt = m_surr.kernel_times()
+        dom_ms += kt if len(kt) == 3 else []
+    launch_ms = statistics.mean(dom_ms)
+    tf = float(m_plain.residual_ex(u0)["troubled"].float().mean().item())
+    flops = 2.0 * fma_per_cell(2, tf) * m_plain.ncells
+    peaks, peak_kind = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": measured_traffic("dg_scalar_stage_q2_surrogate_kpp1024"),
+                "kernel": "dg_scalar_stage<2,2,KPP,16,8,surrogate> (stages a-e + RK, network in stage c)",
+                "launch_ms": launch_ms, "launches_timed": len(dom_ms),
+                "timing": "CUDA events recorded as graph nodes around each launch, in a replay after the timed loop",
+                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
+                "flops_per_launch": flops, "flops_model": "the plain method's count (the work the surrogate replaces)",
+                "hbm_algorithmic_gbs": bytes_per_dof_stage() * m_plain.nstate / (launch_ms * 1e-3) / 1e9}
+    # e2e through the public API
+    host_in = u0.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    nbytes = host_in.numel() * host_in.element_size()
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        u_s.copy_(host_in, non_blocking=True)
+        cv.cvweno_advance(m_surr, u_s, dt, 1)
+        host_out.copy_(u_s, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_value = units * e2e_steps / (time.perf_counter() - e0)
+    m_surr.status_check()
+    cpu = l1 = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample("surrogate")
+        cpu["sample"] += "; plain sensor (the oracle runs the method, not the network)"
+        l1 = surrogate_l1_vs_fp64(net)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["surrogate"], "cells": m_plain.ncells, "dofs_per_step_stage": m_plain.nstate,
+                       "plain": {"value": plain_value, "ms_per_step": step_p},
+                       "surrogate_over_plain": value / plain_value,
+                       "fallback_fraction": fallbacks / (3.0 * args.steps * m_plain.ncells),
+                       "training": dict(tinfo, epochs=epochs, batch=4096, lr=1e-3, last_minibatch_loss=last_loss,
+                                        data_s=t_data, train_s=t_train),
+                       "held_out_quality": quality,
+                       "l1_rel_surrogate_vs_plain_gpu_after_timed_steps": l1_full,
+                       "l1_rel_vs_fp64_reduced_mesh_10steps": l1,
+                       "l2": "flushed (512 MB write) between timed steps, outside the timed events"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "steps": e2e_steps, "api": "cvweno_advance with the surrogate attached, pinned host buffers"},
+            "gpu_launches": 3 * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    m_plain.close()
+    m_surr.close()
+    net.close()
+    return 0
+
+
+def surrogate_l1_vs_fp64(net):
+    """Relative L1 against the FP64 oracle (plain method) after 10 steps at 32^2 on the
+    evaluation seed: the plain FP32 path and the path with the surrogate."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2601_16911_gb300 import cvweno as cv
+    (label, d, ic, dt), = problems("surrogate", 32)
+    u = O.project(d, *ic).astype(np.float32).astype(np.float64)
+    ref = O.ssprk3(d, u, dt, 10)
+    norm = O.l1_diff(d, ref, np.zeros_like(ref))
+    out = {}
+    for name, use in (("plain", False), ("surrogate", True)):
+        m = cv.Mesh(d)
+        if use:
+            m.set_surrogate(net, 0.5)
+        ug = torch.from_numpy(u.astype(np.float32)).cuda()
+        m.advance(ug, dt, 10)
+        m.status_check()
+        out[name] = O.l1_diff(d, ug.cpu().numpy().astype(np.float64), ref) / norm
+        m.close()
+    return out
 
 
 def main():

@@ -282,6 +282,64 @@ cvweno_status cvweno_batch_advance(cvweno_batch b, float* u, const double* dt, i
  * NULL) receives the lowest instance index with a raised status, or -1. */
 cvweno_status cvweno_batch_status_check(cvweno_batch b, int* first_bad, void* stream);
 
+/* ---- surrogate sensor ---------------------------------------------------------------
+ * A small network estimates the sensor gamma_e (eq. gamma) from cell-vertex data.  The
+ * paper has no learned component; the plain sensor is both its fallback and its judge.
+ * Network: x (12) -> GELU(W1 x + b1) (64) -> GELU(W2 . + b2) (64) -> o = W3 . + b3 (2),
+ * GELU in its tanh form; gamma_hat = sigmoid(o0), confidence = sigmoid(o1).
+ * Parameters: one FP32 vector of 5,122 values, row-major W1 (64,12), b1 (64), W2 (64,64),
+ * b2 (64), W3 (2,64), b3 (2).  Training reads inputs and weights rounded to bfloat16 and
+ * computes in FP32; the loss per sample is (gamma_hat - gamma)^2 + 0.1 BCE(confidence, t)
+ * with t = 1 iff |gamma_hat - gamma| < 0.05, averaged over the batch; Adam (0.9, 0.999,
+ * 1e-8, bias-corrected).  Inference (stand-alone and fused into the stage kernel) runs
+ * on the tensor cores with bfloat16 operands and activations, FP32 accumulation.
+ * Inputs of a cell (2D DG scalar meshes), for its corners SW, SE, NW, NE in that order:
+ * the vertex candidate's cell mean minus the cell mean, and h d_x, h d_y of the
+ * candidate at the vertex, all over ||u^e||_e + eps (eq. snorm), clamped to [-8, 8]. */
+typedef struct cvweno_mlp_s* cvweno_mlp;
+
+/* params: host [5122] initial parameters (NULL: zeros).  Records the current device. */
+cvweno_status cvweno_mlp_create(const float* params, cvweno_mlp* out);
+cvweno_status cvweno_mlp_destroy(cvweno_mlp n);
+
+/* The FP32 master parameters into params (host [5122]).  Synchronous. */
+cvweno_status cvweno_mlp_get_params(cvweno_mlp n, float* params);
+
+/* Mean loss and gradient over the count samples X (device [count][12]), gamma targets y
+ * (device [count]).  loss and grad (host, [1] and [5122]) may be NULL; when either is
+ * given the call synchronises.  The sum over samples runs in a fixed order. */
+cvweno_status cvweno_mlp_loss_grad(cvweno_mlp n, const float* X, const float* y, int64_t count, float* loss,
+                                   float* grad, void* stream);
+
+/* One Adam step with the gradient of the last cvweno_mlp_loss_grad, learning rate lr. */
+cvweno_status cvweno_mlp_adam_step(cvweno_mlp n, float lr, void* stream);
+
+/* epochs passes over (X, y) in consecutive minibatches of `batch` samples (the caller
+ * shuffles), one Adam step each.  last_loss (host, may be NULL) receives the mean loss of
+ * the last minibatch (the call then synchronises). */
+cvweno_status cvweno_mlp_train(cvweno_mlp n, const float* X, const float* y, int64_t count, int64_t batch,
+                               int epochs, float lr, float* last_loss, void* stream);
+
+/* Network outputs (o0, o1) before the sigmoids into out (device [count][2]), on the tensor
+ * cores exactly as the fused stage kernel evaluates them. */
+cvweno_status cvweno_mlp_infer(cvweno_mlp n, const float* X, int64_t count, float* out, void* stream);
+
+/* The network inputs of every cell of u into feats (device [ncells][12]) and the computed
+ * sensor gamma_e (whatever sensor_mode says) into gamma (device [ncells], may be NULL).
+ * 2D DG scalar meshes; ERR_UNSUPPORTED otherwise. */
+cvweno_status cvweno_features(cvweno_mesh m, const float* u, float* feats, float* gamma, void* stream);
+
+/* Attach network n (NULL detaches) to mesh m: from then on the stage kernels of m take
+ * gamma_e = gamma_hat where confidence >= conf_min, and the plain sensor elsewhere (and
+ * in flat cells gamma_e = 1, as the plain sensor does).  The mesh reads n's weights at
+ * every launch: n must outlive its use by m.  Training n after attaching takes effect at
+ * the next launch.  2D DG scalar meshes. */
+cvweno_status cvweno_mesh_set_surrogate(cvweno_mesh m, cvweno_mlp n, float conf_min);
+
+/* Cells that fell back to the plain sensor since the last reset, over every mesh n is
+ * attached to (device counter read back: synchronises); reset != 0 zeroes it. */
+cvweno_status cvweno_mlp_fallbacks(cvweno_mlp n, uint64_t* count, int reset, void* stream);
+
 /* One SSP-RK3 step of fixed size dt > 0, in place on the caller's state u (device,
  * state layout of desc), that allocates nothing -- for callers that cannot allocate
  * device or host memory (a library running inside an arena or memory pool it does not

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcvweno.so")
 SOURCES = ["tables.cpp", "api.cu", "dg_scalar_1d.cu", "dg_scalar_2d.cu", "dg_euler.cu", "cg_scalar.cu", "noalloc.cu",
-           "batch.cu"]
+           "batch.cu", "dg_scalar_2d_mlp.cu", "surrogate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

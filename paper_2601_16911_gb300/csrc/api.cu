@@ -221,6 +221,10 @@ StageArgs base_args(const cvweno_mesh_s* m) {
   a.two_dx = (float)(2.0 / m->dx);
   a.two_dy = (float)(2.0 / m->dy);
   a.nu_scale = (float)(m->h / (2.0 * m->p));
+  a.h_e = (float)m->h;
+  a.mlp = m->surrogate;
+  a.mlp_conf_min = m->surrogate_conf_min;
+  a.mlp_fallbacks = m->surrogate_fallbacks;
   a.eps = (float)p.eps;
   a.r = (int)p.r;
   a.q = (float)p.q;

@@ -89,6 +89,14 @@ struct StageArgs {
   int r;
   int sc, sensor_mode;
   int limit_all;       // kModeLimit: limit every cell, not only gamma_e < c_gamma
+  // surrogate sensor (2D DG scalar): packed network weights (MlpPacked) or null, the
+  // confidence below which the plain sensor decides, a fallback counter (may be null),
+  // and the features output of kModeFeatures ([ncell][12])
+  const void* mlp;
+  float mlp_conf_min;
+  unsigned int* mlp_fallbacks;
+  float* feat_out;
+  float h_e;           // cell diameter
   float adv_vx, adv_vy;
   float gas_gamma;
   // CG only: nodal lattice and the per-stage work arrays
@@ -105,6 +113,7 @@ enum : int {
   kModeRK = 2,         // write u_n + rk_b (u_in + dt L - u_n) (or u_in + dt L) to u_out
   kModeSensorOnly = 4, // stop after stage (c) (gamma, nu, lambda outputs)
   kModeLimit = 8,      // HWENO limiter: write u_in or its reconstruction u^{e,*} to u_out
+  kModeFeatures = 16,  // surrogate inputs to feat_out and the computed gamma_e to gamma_out
 };
 
 }  // namespace cvw
@@ -145,6 +154,11 @@ struct cvweno_mesh_s {
   double* d_red;           // reduction scratch
   int* d_status;
   int* h_status;           // pinned
+  // surrogate sensor (cvweno_mesh_set_surrogate): packed weights owned by the network
+  // object, the confidence threshold and an optional device fallback counter
+  const void* surrogate;
+  float surrogate_conf_min;
+  unsigned int* surrogate_fallbacks;
   // optional per-launch timing (cvweno_mesh_set_kernel_timing): events recorded
   // between the kernels of one step, read back by cvweno_kernel_times
   int timing;

@@ -4,9 +4,11 @@
 namespace cvw {
 
 cudaError_t launch_stage_1d(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_surrogate(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 
 cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
   if (m->dim == 1) return launch_stage_1d(m, a, s);
+  if ((a.mlp && !(a.mode & kModeLimit)) || (a.mode & kModeFeatures)) return launch_stage_surrogate(m, a, s);
   constexpr int TX = 16, TY = 8;
   switch (m->p * 10 + m->desc.system) {
     case 10 + CVWENO_BURGERS: return launch_scalar<2, 1, CVWENO_BURGERS, TX, TY>(m, a, s);

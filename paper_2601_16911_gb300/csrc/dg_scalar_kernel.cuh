@@ -29,6 +29,7 @@
 #pragma once
 
 #include "cvweno_internal.cuh"
+#include "mlp_mma.cuh"
 
 namespace cvw {
 
@@ -193,7 +194,77 @@ struct TileLayout {
   static constexpr int OFF_NQ = OFF_W + N;                        // [ND][NT] pointwise indicators
   static constexpr int FLOATS = OFF_NQ + ND * NT;
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
+  // with the surrogate sensor: packed weights, then one 32 x 16 bf16 input block per warp
+  static constexpr int OFF_MLP = (FLOATS + 3) / 4 * 4;
+  static constexpr int OFF_XS = OFF_MLP + (int)(sizeof(MlpPacked) / sizeof(float));
+  static constexpr size_t BYTES_MLP = sizeof(float) * (size_t)OFF_XS + (size_t)(NT / 32) * 32 * 16 * 2;
 };
+
+// Copies the packed surrogate weights into shared memory (uint4 copies).
+template <int DIM, int P, int TX, int TY>
+__device__ __forceinline__ void stage_mlp_to_smem(const void* mlp, float* smem) {
+  using L = TileLayout<DIM, P, TX, TY>;
+  const uint4* src = static_cast<const uint4*>(mlp);
+  uint4* dst = reinterpret_cast<uint4*>(smem + L::OFF_MLP);
+  for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 16); i += L::NT) dst[i] = __ldg(src + i);
+}
+
+// Surrogate inputs of one cell (2D): per corner l, the vertex candidate's cell mean minus
+// the cell mean, and its h-scaled gradient at the vertex, over ||u^e||_e + eps, clamped to
+// [-8, 8].  st holds reference-coordinate Taylor data; the cell mean of the Taylor
+// monomial (xi - s)^k / k! over [-1, 1] is (-s)^k 2^k / (k+1)!.
+template <int P, int TX, int TY>
+__device__ __forceinline__ void cell_features(const StageArgs& a, const float* st, float c0, float n0, int tx,
+                                              int ty, float (&f)[kMlpIn]) {
+  using L = TileLayout<2, P, TX, TY>;
+  constexpr int N = L::N, VXT = L::VXT, NVT = L::NVT;
+  float mom[N];
+  {
+    float v = 1.0f, fact = 1.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {  // 2^k / (k+1)!
+      fact *= (float)(k + 1);
+      mom[k] = v / fact;
+      v *= 2.0f;
+    }
+  }
+  const float inv_s = 1.0f / (n0 + a.eps);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int vi = (tx + (l & 1)) + (ty + (l >> 1)) * VXT;
+    const float sx = (l & 1) ? -1.0f : 1.0f, sy = (l & 2) ? -1.0f : 1.0f;
+    float mean = 0.0f;
+#pragma unroll
+    for (int ky = 0; ky < N; ++ky) {
+      float row = 0.0f;
+      float px = 1.0f;
+#pragma unroll
+      for (int kx = 0; kx < N; ++kx) {
+        row = fmaf(st[(kx + N * ky) * NVT + vi] * px, mom[kx], row);
+        px *= sx;
+      }
+      mean = fmaf(row, mom[ky] * ((ky & 1) ? sy : 1.0f), mean);
+    }
+    const float gx = a.h_e * a.two_dx * st[1 * NVT + vi], gy = a.h_e * a.two_dy * st[N * NVT + vi];
+    f[3 * l + 0] = fminf(8.0f, fmaxf(-8.0f, (mean - c0) * inv_s));
+    f[3 * l + 1] = fminf(8.0f, fmaxf(-8.0f, gx * inv_s));
+    f[3 * l + 2] = fminf(8.0f, fmaxf(-8.0f, gy * inv_s));
+  }
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ float cell_norm0(const DgTables<DIM, P>& T, const float* c) {
+  constexpr int NS = DgTables<DIM, P>::NS;
+  float n2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = i; j < NS; ++j) acc = fmaf(T.R[i][j], c[j + 1], acc);
+    n2 = fmaf(acc, acc, n2);
+  }
+  return sqrtf(n2);
+}
 
 // Copies the tabulations read with run-time indices into shared memory.
 template <int DIM, int P, int TX, int TY>
@@ -326,7 +397,8 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
     wstar[i] = S[i] * inv;  // semi-norm coordinates of u^{e,*} (dead unless the limiter reads it)
     d2 = fmaf(df, df, d2);
   }
-  const bool forced = !(a.mode & kModeLimit);  // the limiter always uses the computed sensor
+  // the limiter, the surrogate's inputs and its fallback always use the computed sensor
+  const bool forced = !(a.mode & (kModeLimit | kModeFeatures));
   if (forced && a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
   if (forced && a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
   if (n0 <= 1e-30f) return 1.0f;
@@ -334,10 +406,12 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
 }
 
 // One tile of one stage: the whole path (a)-(e) for the cells [i0, i0+TX) x [j0, j0+TY)
+// (SURR: the instantiation that also runs the surrogate sensor and the features mode; the
+// plain instantiation carries none of that code, so its registers are unaffected)
 // of the mesh described by a.  The tabulations must already be staged in smem
 // (stage_tables_to_smem) and visible to the CTA; the function contains its own barriers
 // and is called by every thread of the CTA.
-template <int DIM, int P, int SYS, int TX, int TY>
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false>
 __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<DIM, P>& T, int i0, int j0,
                                             float* smem) {
   using L = TileLayout<DIM, P, TX, TY>;
@@ -381,7 +455,12 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   // ---- one thread per cell from here on (no further barriers in this tile) -----------------
   const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
   const int gi = i0 + tx, gj = j0 + ty;
-  if (gi >= nx || gj >= ny) return;
+  const bool active = gi < nx && gj < ny;
+  // the surrogate runs warp-wide on the tensor cores: cells outside the mesh take part
+  // (on the tile's zero-filled halo data) and leave after it
+  bool use_mlp = false;
+  if constexpr (DIM == 2 && SURR) use_mlp = a.mlp != nullptr && !(a.mode & (kModeLimit | kModeFeatures));
+  if (!active && !use_mlp) return;
   const int hc = (DIM == 2 ? (ty + 1) * HX : 0) + tx + 1;
   const size_t cell = (size_t)gj * nx + gi;
   float c[ND];
@@ -391,7 +470,43 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   // ---- (c) cell-vertex reconstruction and sensor --------------------------------------
   float n0;
   float wstar[L::NS];
-  const float gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
+  float gam;
+  if constexpr (DIM == 2 && SURR) {
+    if (a.mode & kModeFeatures) {
+      gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
+      float f[kMlpIn];
+      cell_features<P, TX, TY>(a, st, c[0], n0, tx, ty, f);
+#pragma unroll
+      for (int j = 0; j < kMlpIn; ++j) a.feat_out[cell * kMlpIn + j] = f[j];
+      if (a.gamma_out) a.gamma_out[cell] = gam;
+      return;
+    }
+    if (use_mlp) {
+      n0 = cell_norm0<DIM, P>(T, c);
+      float f[kMlpIn];
+      cell_features<P, TX, TY>(a, st, c[0], n0, tx, ty, f);
+      float o0, o1;
+      const int warp = threadIdx.x >> 5;
+      mlp_warp(*reinterpret_cast<const MlpPacked*>(smem + L::OFF_MLP), f,
+               reinterpret_cast<__nv_bfloat16*>(smem + L::OFF_XS) + warp * 32 * 16, o0, o1);
+      if (!active) return;
+      const float conf = 1.0f / (1.0f + __expf(-o1));
+      if (!(n0 > 1e-30f)) {
+        gam = 1.0f;  // flat cell (reading A7)
+      } else if (conf >= a.mlp_conf_min) {
+        gam = 1.0f / (1.0f + __expf(-o0));
+      } else {
+        gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
+        if (a.mlp_fallbacks) atomicAdd(a.mlp_fallbacks, 1u);
+      }
+      if (a.sensor_mode == CVWENO_SENSOR_SMOOTH) gam = 1.0f;
+      if (a.sensor_mode == CVWENO_SENSOR_TROUBLED) gam = 0.0f;
+    } else {
+      gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
+    }
+  } else {
+    gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
+  }
 
   // ---- HWENO limiter (Sec. 3): u^{e,*} = mean of u^e + R^{-1} w* on the other modes ----
   if (a.mode & kModeLimit) {
@@ -737,12 +852,15 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   if (bad) atomicOr(a.status, kStatNonfinite);
 }
 
-template <int DIM, int P, int SYS, int TX, int TY>
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false>
 __global__ void __launch_bounds__(TX* TY)
     dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
   extern __shared__ __align__(16) float smem[];
   stage_tables_to_smem<DIM, P, TX, TY>(T, smem);  // made visible by the tile's first barrier
-  scalar_tile<DIM, P, SYS, TX, TY>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
+  if constexpr (SURR && DIM == 2) {
+    if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY>(a.mlp, smem);
+  }
+  scalar_tile<DIM, P, SYS, TX, TY, SURR>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
 }
 
 }  // namespace cvw

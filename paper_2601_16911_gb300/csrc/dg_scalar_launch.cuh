@@ -5,12 +5,13 @@
 
 namespace cvw {
 
-template <int DIM, int P, int SYS, int TX, int TY>
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false>
 cudaError_t launch_scalar(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
   using Tb = DgTables<DIM, P>;
-  constexpr size_t smem = TileLayout<DIM, P, TX, TY>::BYTES;
-  static_assert(smem <= 200 * 1024, "tile too large for shared memory");
-  auto kern = dg_scalar_stage<DIM, P, SYS, TX, TY>;
+  using Lay = TileLayout<DIM, P, TX, TY>;
+  static_assert(Lay::BYTES_MLP <= 200 * 1024, "tile too large for shared memory");
+  const size_t smem = (SURR && a.mlp) ? Lay::BYTES_MLP : Lay::BYTES;
+  auto kern = dg_scalar_stage<DIM, P, SYS, TX, TY, SURR>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

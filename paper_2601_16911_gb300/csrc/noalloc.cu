@@ -317,6 +317,7 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   a.two_dx = (float)(2.0 / m.dx);
   a.two_dy = (float)(2.0 / m.dy);
   a.nu_scale = (float)(m.h / (2.0 * m.p));
+  a.h_e = (float)m.h;
   a.eps = (float)p.eps;
   a.r = (int)p.r;
   a.q = (float)p.q;

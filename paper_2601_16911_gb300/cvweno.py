@@ -91,6 +91,18 @@ _SIGNATURES = {
     "cvweno_limit": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "cvweno_mesh_set_kernel_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cvweno_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _IP]),
+    "cvweno_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_VP)]),
+    "cvweno_mlp_destroy": (ctypes.c_int, [_VP]),
+    "cvweno_mlp_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "cvweno_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_float), _VP]),
+    "cvweno_mlp_adam_step": (ctypes.c_int, [_VP, ctypes.c_float, _VP]),
+    "cvweno_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_float,
+                                        ctypes.POINTER(ctypes.c_float), _VP]),
+    "cvweno_mlp_infer": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
+    "cvweno_features": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "cvweno_mesh_set_surrogate": (ctypes.c_int, [_VP, _VP, ctypes.c_float]),
+    "cvweno_mlp_fallbacks": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, _VP]),
     "cvweno_batch_create": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), ctypes.c_int, ctypes.POINTER(_VP)]),
     "cvweno_batch_destroy": (ctypes.c_int, [_VP]),
     "cvweno_batch_offsets": (ctypes.c_int, [_VP, _I64P]),
@@ -287,6 +299,19 @@ class Mesh:
         _check(load().cvweno_limit(self._h, _ptr(u), _ptr(out), 1 if all_cells else 0, _ptr(tr), _stream(stream)),
                "cvweno_limit")
         return out, tr
+
+    def features(self, u, stream=None):
+        """Surrogate inputs (ncells, 12) and the computed sensor gamma (ncells)."""
+        f = torch.empty((self.ncells, 12), dtype=torch.float32, device=u.device)
+        g = torch.empty(self.ncells, dtype=torch.float32, device=u.device)
+        _check(load().cvweno_features(self._h, _ptr(u), _ptr(f), _ptr(g), _stream(stream)), "cvweno_features")
+        return f, g
+
+    def set_surrogate(self, net, conf_min: float = 0.5):
+        """Attach a trained Mlp (None detaches); keep `net` alive while attached."""
+        self._surrogate = net
+        _check(load().cvweno_mesh_set_surrogate(self._h, net.handle if net is not None else None, float(conf_min)),
+               "cvweno_mesh_set_surrogate")
 
     def set_kernel_timing(self, enable: bool = True):
         _check(load().cvweno_mesh_set_kernel_timing(self._h, 1 if enable else 0), "cvweno_mesh_set_kernel_timing")
@@ -516,3 +541,105 @@ def cvweno_kernel_times(mesh: Mesh):
 def cvweno_limit(mesh: Mesh, u, out, all_cells: bool = False, troubled=None, stream=None):
     _check(load().cvweno_limit(mesh.handle, _ptr(u), _ptr(out), 1 if all_cells else 0, _ptr(troubled),
                                _stream(stream)), "cvweno_limit")
+
+
+NPARAM_MLP = 5122
+
+
+class Mlp:
+    """Owning handle of the surrogate network (cvweno_mlp)."""
+
+    def __init__(self, params=None):
+        self._h = _VP()
+        buf = None
+        if params is not None:
+            buf = (ctypes.c_float * NPARAM_MLP)(*[float(v) for v in params])
+        _check(load().cvweno_mlp_create(buf, ctypes.byref(self._h)), "cvweno_mlp_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().cvweno_mlp_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        buf = (ctypes.c_float * NPARAM_MLP)()
+        _check(load().cvweno_mlp_get_params(self._h, buf), "cvweno_mlp_get_params")
+        return [buf[i] for i in range(NPARAM_MLP)]
+
+    def loss_grad(self, X, y, stream=None):
+        loss = ctypes.c_float()
+        grad = (ctypes.c_float * NPARAM_MLP)()
+        _check(load().cvweno_mlp_loss_grad(self._h, _ptr(X), _ptr(y), int(X.shape[0]), ctypes.byref(loss), grad,
+                                           _stream(stream)), "cvweno_mlp_loss_grad")
+        return loss.value, [grad[i] for i in range(NPARAM_MLP)]
+
+    def adam_step(self, lr: float, stream=None):
+        _check(load().cvweno_mlp_adam_step(self._h, float(lr), _stream(stream)), "cvweno_mlp_adam_step")
+
+    def train(self, X, y, batch: int, epochs: int, lr: float, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(load().cvweno_mlp_train(self._h, _ptr(X), _ptr(y), int(X.shape[0]), int(batch), int(epochs),
+                                       float(lr), ctypes.byref(loss), _stream(stream)), "cvweno_mlp_train")
+        return loss.value
+
+    def infer(self, X, stream=None):
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _check(load().cvweno_mlp_infer(self._h, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)),
+               "cvweno_mlp_infer")
+        return out
+
+    def fallbacks(self, reset: bool = False, stream=None) -> int:
+        c = ctypes.c_uint64()
+        _check(load().cvweno_mlp_fallbacks(self._h, ctypes.byref(c), 1 if reset else 0, _stream(stream)),
+               "cvweno_mlp_fallbacks")
+        return c.value
+
+
+def cvweno_mlp_create(params=None) -> Mlp:
+    return Mlp(params)
+
+
+def cvweno_mlp_destroy(net: Mlp):
+    net.close()
+
+
+def cvweno_mlp_get_params(net: Mlp):
+    return net.params()
+
+
+def cvweno_mlp_loss_grad(net: Mlp, X, y, stream=None):
+    return net.loss_grad(X, y, stream)
+
+
+def cvweno_mlp_adam_step(net: Mlp, lr: float, stream=None):
+    net.adam_step(lr, stream)
+
+
+def cvweno_mlp_train(net: Mlp, X, y, batch: int, epochs: int, lr: float, stream=None) -> float:
+    return net.train(X, y, batch, epochs, lr, stream)
+
+
+def cvweno_mlp_infer(net: Mlp, X, stream=None):
+    return net.infer(X, stream)
+
+
+def cvweno_features(mesh: Mesh, u, stream=None):
+    return mesh.features(u, stream)
+
+
+def cvweno_mesh_set_surrogate(mesh: Mesh, net, conf_min: float = 0.5):
+    mesh.set_surrogate(net, conf_min)
+
+
+def cvweno_mlp_fallbacks(net: Mlp, reset: bool = False, stream=None) -> int:
+    return net.fallbacks(reset, stream)

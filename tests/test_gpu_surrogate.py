@@ -1,0 +1,210 @@
+"""Surrogate sensor on the GPU against the FP64 oracle (oracle/surrogate.py, or_features):
+the cell-vertex inputs, the training gradient and loss, the Adam step, a short training
+run, the tensor-core inference, and the stage kernel with the network fused into (c)
+(all cells from the network, all cells falling back, against the oracle's residual for
+the same gamma)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import surrogate as S
+from paper_2601_16911_gb300 import cvweno as cv
+from paper_2601_16911_gb300 import inputs as I
+from tests.gpu_common import RES_TOL, rounded, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def kpp_state(seed=1, n=24, p=2):
+    d, ic = I.kpp(seed, n=n, degree=p)
+    return d, rounded(O.project(d, *ic))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_features_match_oracle(p):
+    d, u = kpp_state(p=p)
+    f_ref, g_ref, nrm = O.features(d, u)
+    mesh = cv.Mesh(d)
+    f, g = mesh.features(to_gpu(u))
+    torch.cuda.synchronize()
+    mesh.status_check()
+    f, g = f.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+    mesh.close()
+    nonflat = nrm > 1e-6 * nrm.max()
+    assert nonflat.sum() > 20
+    err = np.abs(f - f_ref)[nonflat]
+    assert err.max() <= 1e-4 * (1.0 + np.abs(f_ref[nonflat]).max()), err.max()
+    assert np.abs(g - g_ref)[nonflat].max() <= 2e-4
+
+
+def random_training_set(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-2, 2, (n, 12)).astype(np.float32).astype(np.float64)
+    y = rng.uniform(0, 1, n).astype(np.float32).astype(np.float64)
+    return X, y
+
+
+def away_from_threshold(theta, X, y):
+    """Samples whose confidence target (|gamma_hat - y| < tau) is not decided by rounding."""
+    gh = S.forward(theta, X)["gamma_hat"]
+    return np.abs(np.abs(gh - y) - S.TAU) > 1e-4
+
+
+@pytest.mark.parametrize("n", [1, 63, 4096, 20000])
+def test_loss_and_gradient_match_oracle(n):
+    theta = np.array(I.mlp_init(3), dtype=np.float32).astype(np.float64)
+    X, y = random_training_set(n, n)
+    keep = away_from_threshold(theta, X, y)
+    X, y = X[keep], y[keep]
+    L_ref, g_ref = S.loss_and_grad(theta, X, y)
+    net = cv.Mlp(theta)
+    L, g = net.loss_grad(to_gpu(X), to_gpu(y))
+    net.close()
+    g = np.array(g)
+    assert abs(L - L_ref) <= 1e-5 * abs(L_ref)
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), np.abs(g - g_ref).max() / np.abs(g_ref).max()
+
+
+def test_adam_step_matches_oracle():
+    theta = np.array(I.mlp_init(5), dtype=np.float32).astype(np.float64)
+    X, y = random_training_set(9, 1000)
+    net = cv.Mlp(theta)
+    _, g = net.loss_grad(to_gpu(X), to_gpu(y))
+    net.adam_step(1e-3)
+    got = np.array(net.params())
+    net.close()
+    ref, _, _ = S.adam(theta, np.zeros_like(theta), np.zeros_like(theta), np.array(g), 1, 1e-3)
+    assert np.abs(got - ref).max() <= 1e-6
+
+
+def test_training_follows_the_oracle_and_fits():
+    """Twenty Adam steps on minibatches of a smooth target: the GPU parameters follow the
+    oracle's FP64 training loop (same batches, same start) and the loss falls."""
+    rng = np.random.default_rng(11)
+    X = rng.uniform(-1, 1, (2048, 12)).astype(np.float32).astype(np.float64)
+    y = S.sigmoid(2.0 * X[:, 0] - X[:, 5]).astype(np.float32).astype(np.float64)
+    theta = np.array(I.mlp_init(7), dtype=np.float32).astype(np.float64)
+    net = cv.Mlp(theta)
+    last = net.train(to_gpu(X), to_gpu(y), batch=512, epochs=5, lr=2e-3)
+    got = np.array(net.params())
+    net.close()
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    th = theta.copy()
+    step = 0
+    for _ in range(5):
+        for b0 in range(0, 2048, 512):
+            step += 1
+            L, g = S.loss_and_grad(th, X[b0:b0 + 512], y[b0:b0 + 512])
+            th, m, v = S.adam(th, m, v, g, step, 2e-3)
+    assert np.abs(got - th).max() <= 2e-3 * np.abs(th).max(), np.abs(got - th).max()
+    assert abs(last - L) <= 1e-2 * L + 1e-4
+    assert S.loss(th, X, y)[0] < S.loss(theta, X, y)[0]
+
+
+@pytest.mark.parametrize("n", [5, 32, 1000, 70001])
+def test_tensor_core_inference_matches_oracle(n):
+    rng = np.random.default_rng(n)
+    theta = np.array(I.mlp_init(13)) + 0.1 * rng.standard_normal(S.NPARAM)
+    theta = theta.astype(np.float32).astype(np.float64)
+    X = rng.uniform(-3, 3, (n, 12)).astype(np.float32).astype(np.float64)
+    ref = S.forward(theta, X, act_bf16=True)["o"]
+    net = cv.Mlp(theta)
+    out = net.infer(to_gpu(X)).cpu().numpy().astype(np.float64)
+    net.close()
+    err = np.abs(out - ref)
+    assert err.max() <= 5e-3 * (1.0 + np.abs(ref).max()), err.max()
+    assert np.median(err) <= 5e-4 * (1.0 + np.abs(ref).max())
+
+
+def trained_like_net(seed=17):
+    """A network with non-trivial outputs (random, not trained): enough to exercise the
+    fused path; its gamma_hat is whatever it is, and the tests compare like with like."""
+    rng = np.random.default_rng(seed)
+    theta = np.array(I.mlp_init(seed)) + 0.05 * rng.standard_normal(S.NPARAM)
+    return theta.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_fused_all_cells_from_the_network(p):
+    """conf_min = 0: every non-flat cell takes gamma_e = sigmoid(o0) of the network.  The
+    GPU residual equals the oracle's stage (e) for exactly that gamma (the GPU's own
+    inputs and outputs, read back through cvweno_features and cvweno_mlp_infer), with
+    the SC weights of stage (d) for it."""
+    d, u = kpp_state(seed=2, n=21, p=p)
+    theta = trained_like_net()
+    net = cv.Mlp(theta)
+    mesh = cv.Mesh(d)
+    ug = to_gpu(u)
+    f, _ = mesh.features(ug)
+    o = net.infer(f)
+    gam = (1.0 / (1.0 + torch.exp(-o[:, 0].double()))).cpu().numpy()
+    mesh.set_surrogate(net, conf_min=0.0)
+    r = mesh.residual(ug)
+    torch.cuda.synchronize()
+    mesh.status_check()
+    got = r.cpu().numpy().astype(np.float64)
+    assert net.fallbacks() == 0
+    mesh.set_surrogate(None)
+    mesh.close()
+    net.close()
+    _, _, nrm = O.features(d, u)
+    gam = np.where(nrm > 1e-30, gam, 1.0)
+    ref0 = O.residual(d, u)
+    alpha, tr = O.sc_weights(d, u, gam)
+    ref = O.residual_given(d, u, gam, ref0["nu"], alpha)
+    # cells whose SC decision (gamma vs C_gamma) or flatness is taken by rounding
+    keep = (np.abs(gam - d["c_gamma"]) > 1e-4) & ((nrm > 1e-6 * nrm.max()) | (nrm <= 1e-30))
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref)[:, keep].max() / scale
+    assert err <= 1e-4, err
+
+
+def test_fused_all_cells_fall_back_to_the_plain_sensor():
+    """conf_min = 1: no confidence reaches it, so every non-flat cell runs the plain
+    sensor; the residual equals the plain kernel's and the fallback count is the
+    number of non-flat cells."""
+    d, u = kpp_state(seed=3, n=40, p=2)
+    net = cv.Mlp(trained_like_net(19))
+    mesh = cv.Mesh(d)
+    ug = to_gpu(u)
+    plain = mesh.residual(ug).clone()
+    mesh.set_surrogate(net, conf_min=1.0)
+    net.fallbacks(reset=True)
+    surr = mesh.residual(ug)
+    torch.cuda.synchronize()
+    nfb = net.fallbacks()
+    mesh.set_surrogate(None)
+    mesh.close()
+    net.close()
+    _, _, nrm = O.features(d, u)
+    assert nfb == int((nrm > 1e-30).sum())
+    diff = (surr - plain).abs().max().item()
+    assert diff <= 1e-6 * plain.abs().max().item(), diff
+
+
+def test_surrogate_argument_errors():
+    d1, _ = I.burgers1d_step(0, nx=16, degree=2)
+    net = cv.Mlp()
+    for d in (d1, I.kpp(0, n=8, degree=2, kind=I.CG)[0], I.euler_quadrants(0, n=8, degree=1)[0]):
+        m = cv.Mesh(d)
+        with pytest.raises(cv.CvwenoError) as e:
+            m.set_surrogate(net)
+        assert e.value.code == cv.ERR_UNSUPPORTED
+        with pytest.raises(cv.CvwenoError) as e:
+            m.features(m.empty_state().zero_())
+        assert e.value.code == cv.ERR_UNSUPPORTED
+        m.close()
+    d, _ = I.kpp(0, n=8, degree=2)
+    m = cv.Mesh(d)
+    for bad in (-0.1, 1.5):
+        with pytest.raises(cv.CvwenoError) as e:
+            m.set_surrogate(net, conf_min=bad)
+        assert e.value.code == cv.ERR_ARG
+    m.close()
+    X = torch.zeros((4, 12), device="cuda")
+    with pytest.raises(cv.CvwenoError) as e:
+        net.train(X, torch.zeros(4, device="cuda"), batch=0, epochs=1, lr=1e-3)
+    assert e.value.code == cv.ERR_ARG
+    net.close()
