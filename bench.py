@@ -37,6 +37,7 @@ VARIANTS = [(k, p) for k in KINDS for p in DEGREES]
 WORKLOAD = ("KPP 2D, f=(sin u, cos u), [-2,2]^2 periodic, 256x256 quads, DG and CG Q1+Q2+Q3 "
             "(one SSP-RK3 step each), FP32")
 SEED = 0
+SURROGATE_P = 2  # degree of the surrogate workload (--surrogate-degree)
 
 
 def problems(workload: str, n_scale: int | None = None):
@@ -60,8 +61,8 @@ def problems(workload: str, n_scale: int | None = None):
         out.append(("DG-P2", d, ic, 0.1 * (1.0 / 128) / 1.5))
     elif workload == "surrogate":
         n = n_scale or 1024
-        d, ic = I.kpp(4, n=n, degree=2)
-        out.append(("DG-Q2-surrogate", d, ic, cfl_dt(2, n)))
+        d, ic = I.kpp(4, n=n, degree=SURROGATE_P)
+        out.append((f"DG-Q{SURROGATE_P}-surrogate", d, ic, cfl_dt(SURROGATE_P, n)))
     elif workload == "batched":
         seen = set()
         for k, (d, ic) in enumerate(I.burgers2d_batch(SEED)):
@@ -707,25 +708,32 @@ def run_gpu_batched(args, ws, rank, local, dev):
     return 0
 
 
-def surrogate_training_set(n=256, seeds=(0, 1, 2, 3), snapshots=12, steps_between=150, max_samples=1_000_000):
+def surrogate_training_set(p=2, n=512, seeds=(0, 1, 2, 3), snapshots=16, max_samples=1_000_000):
     """Inputs and plain-sensor targets from KPP n^2 DG Q2 runs of the given seeds (not the
-    evaluation seed), sampled every steps_between steps; the troubled-side cells
-    (gamma < 0.999) are all kept and the rest subsampled to at most max_samples in all,
-    in a seeded shuffled order."""
+    evaluation seed), sampled at `snapshots` times evenly spread over t in [0, 1).  Cells
+    flat to rounding (reading S7) are left out; every cell with gamma < 0.999 is kept,
+    and the smooth rest is subsampled to at most twice their number, in a seeded
+    shuffled order."""
     import torch
 
     from paper_2601_16911_gb300 import cvweno as cv
     from paper_2601_16911_gb300 import inputs as I
     X, y = [], []
+    dropped = 0
+    dt = cfl_dt(p, n)
+    steps_between = int(round(1.0 / dt / snapshots))
     for seed in seeds:
-        d, ic = I.kpp(seed, n=n, degree=2)
+        d, ic = I.kpp(seed, n=n, degree=p)
         m = cv.Mesh(d)
         u = m.project(*ic)
         for _ in range(snapshots):
-            f, g = m.features(u)
-            X.append(f)
-            y.append(g)
-            m.advance(u, cfl_dt(2, n), steps_between)
+            f, g, nrm = m.features(u, with_norm=True)
+            mean = u.view(-1, (p + 1) ** 2)[:, 0]
+            live = nrm > 1e-5 * (mean.abs() + 1.0)
+            dropped += int((~live).sum())
+            X.append(f[live])
+            y.append(g[live])
+            m.advance(u, dt, steps_between)
         m.status_check()
         m.close()
     X = torch.cat(X)
@@ -733,11 +741,12 @@ def surrogate_training_set(n=256, seeds=(0, 1, 2, 3), snapshots=12, steps_betwee
     gen = torch.Generator(device="cpu").manual_seed(1234)
     rough = torch.nonzero(y < 0.999).flatten().cpu()
     smooth = torch.nonzero(y >= 0.999).flatten().cpu()
-    keep_smooth = max(0, min(len(smooth), max_samples - len(rough), 3 * len(rough)))
+    keep_smooth = max(0, min(len(smooth), 2 * len(rough), max_samples - len(rough)))
     idx = torch.cat([rough, smooth[torch.randperm(len(smooth), generator=gen)[:keep_smooth]]])
     idx = idx[torch.randperm(len(idx), generator=gen)][:max_samples].to(X.device)
-    return X[idx].contiguous(), y[idx].contiguous(), {"total_cells": int(y.numel()), "rough": int(len(rough)),
-                                                      "samples": int(idx.numel())}
+    return X[idx].contiguous(), y[idx].contiguous(), {
+        "mesh": f"KPP {n}^2 Q{p}, seeds {list(seeds)}, {snapshots} snapshots each", "flat_cells_dropped": dropped,
+        "rough": int(len(rough)), "troubled": int((y < 0.9).sum()), "samples": int(idx.numel())}
 
 
 def run_gpu_surrogate(args, ws, rank, local, dev):
@@ -751,7 +760,7 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
     from paper_2601_16911_gb300 import inputs as I
 
     t0 = time.perf_counter()
-    X, y, tinfo = surrogate_training_set()
+    X, y, tinfo = surrogate_training_set(SURROGATE_P)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     net = cv.Mlp(I.mlp_init(0))
@@ -767,13 +776,19 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
     m_surr.set_surrogate(net, 0.5)
     u0 = m_plain.project(*ic)
     torch.cuda.synchronize()
-    f, g_plain = m_plain.features(u0)
+    # held-out quality on a later state of the evaluation run, where the wave has formed
+    u_eval = u0.clone()
+    m_plain.advance(u_eval, dt, 400)
+    f, g_plain, nrm = m_plain.features(u_eval, with_norm=True)
+    live = nrm > 1e-5 * (u_eval.view(-1, (SURROGATE_P + 1) ** 2)[:, 0].abs() + 1.0)
+    f, g_plain = f[live], g_plain[live]
     o = net.infer(f)
     g_hat = torch.sigmoid(o[:, 0])
     conf = torch.sigmoid(o[:, 1])
     confident = conf >= 0.5
     dg = (g_hat - g_plain).abs()
-    quality = {"confident_fraction": float(confident.float().mean()),
+    quality = {"state": "evaluation seed after 400 steps, cells not flat to rounding",
+               "cells": int(live.sum()), "confident_fraction": float(confident.float().mean()),
                "mean_abs_gamma_err_confident": float(dg[confident].mean()) if bool(confident.any()) else None,
                "max_abs_gamma_err_confident": float(dg[confident].max()) if bool(confident.any()) else None,
                "sc_decision_disagreements": int(((g_hat < d["c_gamma"]) != (g_plain < d["c_gamma"]))[confident].sum()),
@@ -840,14 +855,14 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
         dom_ms += kt if len(kt) == 3 else []
     launch_ms = statistics.mean(dom_ms)
     tf = float(m_plain.residual_ex(u0)["troubled"].float().mean().item())
-    flops = 2.0 * fma_per_cell(2, tf) * m_plain.ncells
+    flops = 2.0 * fma_per_cell(SURROGATE_P, tf) * m_plain.ncells
     peaks, peak_kind = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (launch_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                 "traffic": measured_traffic("dg_scalar_stage_q2_surrogate_kpp1024"),
-                "kernel": "dg_scalar_stage<2,2,KPP,16,8,surrogate> (stages a-e + RK, network in stage c)",
+                "kernel": f"dg_scalar_stage<2,{SURROGATE_P},KPP,16,8,surrogate> (stages a-e + RK, network in stage c)",
                 "launch_ms": launch_ms, "launches_timed": len(dom_ms),
                 "timing": "CUDA events recorded as graph nodes around each launch, in a replay after the timed loop",
                 "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
@@ -875,7 +890,9 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS["surrogate"], "cells": m_plain.ncells, "dofs_per_step_stage": m_plain.nstate,
+            "config": {"workload": WORKLOADS["surrogate"].replace("Q2", f"Q{SURROGATE_P}"), "cells": m_plain.ncells,
+                       "note": "warps whose cells are all flat to rounding skip both the network and the "
+                               "plain sensor (reading S7); the plain kernel runs its sensor in every cell", "dofs_per_step_stage": m_plain.nstate,
                        "plain": {"value": plain_value, "ms_per_step": step_p},
                        "surrogate_over_plain": value / plain_value,
                        "fallback_fraction": fallbacks / (3.0 * args.steps * m_plain.ncells),
@@ -928,10 +945,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--surrogate-degree", type=int, default=2, choices=[1, 2, 3, 4],
+                    help="degree of the surrogate workload (configs[4] is Q2)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kpp",
                     help="kpp (default): the 2D KPP configuration the metric is quoted on; euler, burgers1d and "
                          "batched measure the other configurations")
     args = ap.parse_args()
+    global SURROGATE_P
+    SURROGATE_P = args.surrogate_degree
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

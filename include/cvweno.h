@@ -324,14 +324,17 @@ cvweno_status cvweno_mlp_train(cvweno_mlp n, const float* X, const float* y, int
  * cores exactly as the fused stage kernel evaluates them. */
 cvweno_status cvweno_mlp_infer(cvweno_mlp n, const float* X, int64_t count, float* out, void* stream);
 
-/* The network inputs of every cell of u into feats (device [ncells][12]) and the computed
- * sensor gamma_e (whatever sensor_mode says) into gamma (device [ncells], may be NULL).
- * 2D DG scalar meshes; ERR_UNSUPPORTED otherwise. */
-cvweno_status cvweno_features(cvweno_mesh m, const float* u, float* feats, float* gamma, void* stream);
+/* The network inputs of every cell of u into feats (device [ncells][12]), the computed
+ * sensor gamma_e (whatever sensor_mode says) into gamma and the semi-norm ||u^e||_e into
+ * norm (device [ncells] each, may be NULL).  2D DG scalar meshes; ERR_UNSUPPORTED
+ * otherwise. */
+cvweno_status cvweno_features(cvweno_mesh m, const float* u, float* feats, float* gamma, float* norm,
+                              void* stream);
 
 /* Attach network n (NULL detaches) to mesh m: from then on the stage kernels of m take
- * gamma_e = gamma_hat where confidence >= conf_min, and the plain sensor elsewhere (and
- * in flat cells gamma_e = 1, as the plain sensor does).  The mesh reads n's weights at
+ * gamma_e = gamma_hat where confidence >= conf_min, and the plain sensor elsewhere; cells
+ * whose ||u^e||_e is at most 1e-5 (|cell mean| + 1) (rounding-level variation) take
+ * gamma_e = 1 without the network.  The mesh reads n's weights at
  * every launch: n must outlive its use by m.  Training n after attaching takes effect at
  * the next launch.  2D DG scalar meshes. */
 cvweno_status cvweno_mesh_set_surrogate(cvweno_mesh m, cvweno_mlp n, float conf_min);

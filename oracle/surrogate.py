@@ -16,7 +16,9 @@ Definitions (readings S1-S6, restated where the GPU path implements them):
       tau = 0.05, averaged over the batch;
   S6  BF16 storage: the forward pass reads the inputs and the weights rounded to
       bfloat16 (round to nearest even); gradients are taken with respect to the
-      rounded weights and applied to the FP32 master copy; sums in FP32 or better.
+      rounded weights and applied to the FP32 master copy; sums in FP32 or better;
+  S7  a cell with ||u^e||_e <= 1e-5 (|cell mean| + 1) holds rounding-level variation
+      only: it takes gamma_e = 1 without the network and is left out of training.
 Everything here is FP64 numpy; bf16 rounding is emulated where S6 places it.
 """
 from __future__ import annotations
@@ -28,6 +30,14 @@ SHAPES = [("W1", (NH, NIN)), ("b1", (NH,)), ("W2", (NH, NH)), ("b2", (NH,)), ("W
 NPARAM = sum(int(np.prod(s)) for _, s in SHAPES)
 LAM, TAU = 0.1, 0.05
 _C = np.sqrt(2.0 / np.pi)
+
+
+NEAR_FLAT = 1e-5
+
+
+def near_flat(norm, mean):
+    """Reading S7: cells whose semi-norm is rounding-level next to their mean."""
+    return np.asarray(norm) <= NEAR_FLAT * (np.abs(np.asarray(mean)) + 1.0)
 
 
 def unpack(theta):

@@ -96,6 +96,7 @@ struct StageArgs {
   float mlp_conf_min;
   unsigned int* mlp_fallbacks;
   float* feat_out;
+  float* norm_out;     // kModeFeatures: ||u^e||_e per cell (may be null)
   float h_e;           // cell diameter
   float adv_vx, adv_vy;
   float gas_gamma;

@@ -65,16 +65,40 @@ struct ScalarLaw<CVWENO_BURGERS, DIM> {
   __device__ __forceinline__ float nspeed(float u, int) const { return fabsf(u); }
 };
 
+// sin d and cos d - 1 for |d| <= 1 from their Maclaurin series, Horner in d^2, to the
+// d^11 and d^12 terms: the first omitted terms are below 2e-10 at |d| = 1, far under one
+// FP32 ulp, and cos d - 1 comes without cancellation.
+__device__ __forceinline__ void sin_cosm1_small(float d, float& s, float& cm1) {
+  const float z = d * d;
+  float ps = fmaf(z, -1.0f / 39916800.0f, 1.0f / 362880.0f);
+  ps = fmaf(z, ps, -1.0f / 5040.0f);
+  ps = fmaf(z, ps, 1.0f / 120.0f);
+  ps = fmaf(z, ps, -1.0f / 6.0f);
+  s = fmaf(d * z, ps, d);
+  float pc = fmaf(z, 1.0f / 479001600.0f, -1.0f / 3628800.0f);
+  pc = fmaf(z, pc, 1.0f / 40320.0f);
+  pc = fmaf(z, pc, -1.0f / 720.0f);
+  pc = fmaf(z, pc, 1.0f / 24.0f);
+  pc = fmaf(z, pc, -0.5f);
+  cm1 = z * pc;
+}
+
 template <int DIM>
 struct ScalarLaw<CVWENO_KPP, DIM> {
   float sb, cb;  // sin(ubar), cos(ubar)
   __device__ __forceinline__ ScalarLaw(const StageArgs&, float ub) { sincosf(ub, &sb, &cb); }
-  // sin(ub + d) - sin(ub) = sin(ub)(cos d - 1) + cos(ub) sin d, and likewise for cos;
-  // cos d - 1 = -sin^2 d / (1 + cos d) avoids the cancellation where cos d > 0
+  // sin(ub + d) - sin(ub) = sin(ub)(cos d - 1) + cos(ub) sin d, and likewise for cos.
+  // Deviations inside a cell are mostly small: the series above; otherwise sincosf with
+  // cos d - 1 = -sin^2 d / (1 + cos d), which avoids the cancellation where cos d > 0.
   __device__ __forceinline__ void flux_dev(float d, float& fx, float& fy) const {
-    float s, c;
-    sincosf(d, &s, &c);
-    const float cm1 = c > 0.0f ? -(s * s) / (1.0f + c) : c - 1.0f;
+    float s, cm1;
+    if (fabsf(d) <= 1.0f) {
+      sin_cosm1_small(d, s, cm1);
+    } else {
+      float c;
+      sincosf(d, &s, &c);
+      cm1 = c > 0.0f ? -(s * s) / (1.0f + c) : c - 1.0f;
+    }
     fx = fmaf(sb, cm1, cb * s);
     fy = fmaf(cb, cm1, -sb * s);
   }
@@ -251,6 +275,10 @@ __device__ __forceinline__ void cell_features(const StageArgs& a, const float* s
     f[3 * l + 2] = fminf(8.0f, fmaxf(-8.0f, gy * inv_s));
   }
 }
+
+// Reading S7: with the surrogate, a cell whose semi-norm is below this fraction of
+// (|mean| + 1) holds rounding-level variation only; it takes gamma_e = 1 directly.
+constexpr float kNearFlat = 1e-5f;
 
 template <int DIM, int P>
 __device__ __forceinline__ float cell_norm0(const DgTables<DIM, P>& T, const float* c) {
@@ -479,20 +507,24 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 #pragma unroll
       for (int j = 0; j < kMlpIn; ++j) a.feat_out[cell * kMlpIn + j] = f[j];
       if (a.gamma_out) a.gamma_out[cell] = gam;
+      if (a.norm_out) a.norm_out[cell] = n0;
       return;
     }
     if (use_mlp) {
       n0 = cell_norm0<DIM, P>(T, c);
       float f[kMlpIn];
       cell_features<P, TX, TY>(a, st, c[0], n0, tx, ty, f);
-      float o0, o1;
+      float o0 = 0.0f, o1 = 0.0f;
+      const bool live = active && n0 > kNearFlat * (fabsf(c[0]) + 1.0f);
       const int warp = threadIdx.x >> 5;
-      mlp_warp(*reinterpret_cast<const MlpPacked*>(smem + L::OFF_MLP), f,
-               reinterpret_cast<__nv_bfloat16*>(smem + L::OFF_XS) + warp * 32 * 16, o0, o1);
+      // a warp whose cells are all flat to rounding (S7) skips the network
+      if (__any_sync(0xffffffffu, live))
+        mlp_warp(*reinterpret_cast<const MlpPacked*>(smem + L::OFF_MLP), f,
+                 reinterpret_cast<__nv_bfloat16*>(smem + L::OFF_XS) + warp * 32 * 16, o0, o1);
       if (!active) return;
       const float conf = 1.0f / (1.0f + __expf(-o1));
-      if (!(n0 > 1e-30f)) {
-        gam = 1.0f;  // flat cell (reading A7)
+      if (!live) {
+        gam = 1.0f;  // flat to rounding (readings A7, S7): no network, no fallback
       } else if (conf >= a.mlp_conf_min) {
         gam = 1.0f / (1.0f + __expf(-o0));
       } else {
@@ -852,15 +884,28 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   if (bad) atomicOr(a.status, kStatNonfinite);
 }
 
-template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false>
-__global__ void __launch_bounds__(TX* TY)
-    dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR>
+__device__ __forceinline__ void stage_body(const StageArgs& a, const DgTables<DIM, P>& T) {
   extern __shared__ __align__(16) float smem[];
   stage_tables_to_smem<DIM, P, TX, TY>(T, smem);  // made visible by the tile's first barrier
   if constexpr (SURR && DIM == 2) {
     if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY>(a.mlp, smem);
   }
   scalar_tile<DIM, P, SYS, TX, TY, SURR>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
+}
+
+template <int DIM, int P, int SYS, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+    dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
+  stage_body<DIM, P, SYS, TX, TY, false>(a, T);
+}
+
+// The surrogate instantiation is held to the register budget of 4 resident CTAs (3 at
+// p = 4), which the network's fragments would otherwise exceed.
+template <int DIM, int P, int SYS, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, (P >= 4 ? 3 : 4) * (128 / (TX * TY)))
+    dg_scalar_stage_surrogate(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
+  stage_body<DIM, P, SYS, TX, TY, true>(a, T);
 }
 
 }  // namespace cvw

@@ -5,13 +5,21 @@
 
 namespace cvw {
 
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR>
+constexpr auto stage_kernel() {
+  if constexpr (SURR)
+    return dg_scalar_stage_surrogate<DIM, P, SYS, TX, TY>;
+  else
+    return dg_scalar_stage<DIM, P, SYS, TX, TY>;
+}
+
 template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false>
 cudaError_t launch_scalar(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
   using Tb = DgTables<DIM, P>;
   using Lay = TileLayout<DIM, P, TX, TY>;
   static_assert(Lay::BYTES_MLP <= 200 * 1024, "tile too large for shared memory");
   const size_t smem = (SURR && a.mlp) ? Lay::BYTES_MLP : Lay::BYTES;
-  auto kern = dg_scalar_stage<DIM, P, SYS, TX, TY, SURR>;
+  auto kern = stage_kernel<DIM, P, SYS, TX, TY, SURR>();
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -451,13 +451,15 @@ cvweno_status cvweno_mlp_infer(cvweno_mlp n, const float* X, int64_t count, floa
   return cuda_status(cudaGetLastError());
 }
 
-cvweno_status cvweno_features(cvweno_mesh m, const float* u, float* feats, float* gamma, void* stream) {
+cvweno_status cvweno_features(cvweno_mesh m, const float* u, float* feats, float* gamma, float* norm,
+                              void* stream) {
   if (!m || !u || !feats) return CVWENO_ERR_ARG;
   if (m->dim != 2 || m->kind != CVWENO_DG || m->desc.system == CVWENO_EULER) return CVWENO_ERR_UNSUPPORTED;
   StageArgs a = stage_base_args(m);
   a.u_in = u;
   a.feat_out = feats;
   a.gamma_out = gamma;
+  a.norm_out = norm;
   a.mlp = nullptr;
   a.mode = kModeFeatures;
   return cuda_status(launch_stage(m, a, S(stream)));

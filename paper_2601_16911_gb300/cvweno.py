@@ -100,7 +100,7 @@ _SIGNATURES = {
     "cvweno_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_float,
                                         ctypes.POINTER(ctypes.c_float), _VP]),
     "cvweno_mlp_infer": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
-    "cvweno_features": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "cvweno_features": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "cvweno_mesh_set_surrogate": (ctypes.c_int, [_VP, _VP, ctypes.c_float]),
     "cvweno_mlp_fallbacks": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, _VP]),
     "cvweno_batch_create": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), ctypes.c_int, ctypes.POINTER(_VP)]),
@@ -300,12 +300,15 @@ class Mesh:
                "cvweno_limit")
         return out, tr
 
-    def features(self, u, stream=None):
-        """Surrogate inputs (ncells, 12) and the computed sensor gamma (ncells)."""
+    def features(self, u, with_norm: bool = False, stream=None):
+        """Surrogate inputs (ncells, 12), the computed sensor gamma (ncells) and, with
+        with_norm, the semi-norms ||u^e||_e (ncells)."""
         f = torch.empty((self.ncells, 12), dtype=torch.float32, device=u.device)
         g = torch.empty(self.ncells, dtype=torch.float32, device=u.device)
-        _check(load().cvweno_features(self._h, _ptr(u), _ptr(f), _ptr(g), _stream(stream)), "cvweno_features")
-        return f, g
+        n = torch.empty(self.ncells, dtype=torch.float32, device=u.device) if with_norm else None
+        _check(load().cvweno_features(self._h, _ptr(u), _ptr(f), _ptr(g), _ptr(n), _stream(stream)),
+               "cvweno_features")
+        return (f, g, n) if with_norm else (f, g)
 
     def set_surrogate(self, net, conf_min: float = 0.5):
         """Attach a trained Mlp (None detaches); keep `net` alive while attached."""
@@ -633,8 +636,8 @@ def cvweno_mlp_infer(net: Mlp, X, stream=None):
     return net.infer(X, stream)
 
 
-def cvweno_features(mesh: Mesh, u, stream=None):
-    return mesh.features(u, stream)
+def cvweno_features(mesh: Mesh, u, with_norm: bool = False, stream=None):
+    return mesh.features(u, with_norm, stream)
 
 
 def cvweno_mesh_set_surrogate(mesh: Mesh, net, conf_min: float = 0.5):

@@ -137,9 +137,10 @@ def test_fused_all_cells_from_the_network(p):
     net = cv.Mlp(theta)
     mesh = cv.Mesh(d)
     ug = to_gpu(u)
-    f, _ = mesh.features(ug)
+    f, _, n0 = mesh.features(ug, with_norm=True)
     o = net.infer(f)
     gam = (1.0 / (1.0 + torch.exp(-o[:, 0].double()))).cpu().numpy()
+    n0 = n0.cpu().numpy().astype(np.float64)
     mesh.set_surrogate(net, conf_min=0.0)
     r = mesh.residual(ug)
     torch.cuda.synchronize()
@@ -150,12 +151,13 @@ def test_fused_all_cells_from_the_network(p):
     mesh.close()
     net.close()
     _, _, nrm = O.features(d, u)
-    gam = np.where(nrm > 1e-30, gam, 1.0)
+    thr = S.NEAR_FLAT * (np.abs(u[0, :, 0]) + 1.0)
+    gam = np.where(n0 > thr, gam, 1.0)  # S7, decided as the GPU decided it
     ref0 = O.residual(d, u)
     alpha, tr = O.sc_weights(d, u, gam)
     ref = O.residual_given(d, u, gam, ref0["nu"], alpha)
     # cells whose SC decision (gamma vs C_gamma) or flatness is taken by rounding
-    keep = (np.abs(gam - d["c_gamma"]) > 1e-4) & ((nrm > 1e-6 * nrm.max()) | (nrm <= 1e-30))
+    keep = (np.abs(gam - d["c_gamma"]) > 1e-4) & (np.abs(n0 - thr) > 1e-2 * thr)
     scale = np.abs(ref).max()
     err = np.abs(got - ref)[:, keep].max() / scale
     assert err <= 1e-4, err
@@ -170,6 +172,7 @@ def test_fused_all_cells_fall_back_to_the_plain_sensor():
     mesh = cv.Mesh(d)
     ug = to_gpu(u)
     plain = mesh.residual(ug).clone()
+    n0 = mesh.features(ug, with_norm=True)[2].cpu().numpy().astype(np.float64)
     mesh.set_surrogate(net, conf_min=1.0)
     net.fallbacks(reset=True)
     surr = mesh.residual(ug)
@@ -178,10 +181,12 @@ def test_fused_all_cells_fall_back_to_the_plain_sensor():
     mesh.set_surrogate(None)
     mesh.close()
     net.close()
-    _, _, nrm = O.features(d, u)
-    assert nfb == int((nrm > 1e-30).sum())
+    nonflat = n0 > S.NEAR_FLAT * (np.abs(u[0, :, 0]) + 1.0)
+    assert nfb == int(nonflat.sum())
+    # near-flat cells take gamma = 1 (S7) where the plain sensor takes its rounding-level
+    # value; their viscous term multiplies rounding-level gradients
     diff = (surr - plain).abs().max().item()
-    assert diff <= 1e-6 * plain.abs().max().item(), diff
+    assert diff <= 1e-5 * plain.abs().max().item(), diff
 
 
 def test_surrogate_argument_errors():
