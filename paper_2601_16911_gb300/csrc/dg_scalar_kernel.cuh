@@ -216,13 +216,22 @@ struct TileLayout {
   static constexpr int OFF_BK = OFF_BD + N * N;                   // [N][N][N] Bk[k][q][m]
   static constexpr int OFF_W = OFF_BK + N * N * N;                // [N]
   static constexpr int OFF_NQ = OFF_W + N;                        // [ND][NT] pointwise indicators
-  static constexpr int FLOATS = OFF_NQ + ND * NT;
+  static constexpr int OFF_UN = OFF_NQ + ND * NT;                 // [ND][NT] u_n of the tile's cells
+  static constexpr int FLOATS = OFF_UN + ND * NT;
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
   // with the surrogate sensor: packed weights, then one 32 x 16 bf16 input block per warp
   static constexpr int OFF_MLP = (FLOATS + 3) / 4 * 4;
   static constexpr int OFF_XS = OFF_MLP + (int)(sizeof(MlpPacked) / sizeof(float));
   static constexpr size_t BYTES_MLP = sizeof(float) * (size_t)OFF_XS + (size_t)(NT / 32) * 32 * 16 * 2;
 };
+
+// 4-byte asynchronous global -> shared copy (zero-filled when src_bytes == 0), so that a
+// thread keeps all of its tile loads in flight at once instead of waiting on each.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Copies the packed surrogate weights into shared memory (uint4 copies).
 template <int DIM, int P, int TX, int TY>
@@ -458,7 +467,8 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 
   const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
 
-  // ---- load tile + halo --------------------------------------------------------------------
+  // ---- load tile + halo (and u_n of the tile's cells for the RK combination) ------------
+  // asynchronous copies: every load of the thread is in flight before the first wait
   for (int f = threadIdx.x; f < NH * ND; f += NT) {
     int r = f / (HX * ND);
     int rem = f - r * (HX * ND);
@@ -472,8 +482,19 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     if (DIM == 2 && (gj < 0 || gj >= ny)) {
       if (a.pery) gj = (gj + ny) % ny; else ok = false;
     }
-    sc[mm * NH + r * HX + cc] = ok ? __ldg(a.u_in + ((size_t)gj * nx + gi) * ND + mm) : 0.0f;
+    cp_async4(sc + mm * NH + r * HX + cc, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + mm : a.u_in, ok ? 4 : 0);
   }
+  const bool pre_un = (a.mode & kModeRK) && a.rk_a != 0.0f;
+  if (pre_un) {
+    float* sUn = smem + L::OFF_UN;
+    for (int f = threadIdx.x; f < NT * ND; f += NT) {
+      const int cl = f / ND, mm = f - cl * ND;
+      const int gi = i0 + cl % TX, gj = DIM == 2 ? j0 + cl / TX : 0;
+      const bool ok = gi < nx && gj < ny;
+      cp_async4(sUn + mm * NT + cl, ok ? a.u_n + ((size_t)gj * nx + gi) * ND + mm : a.u_n, ok ? 4 : 0);
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
 
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
@@ -866,7 +887,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   // M^{-1} and output
   bool bad = false;
   float* out = a.u_out + cell * ND;
-  const float* un = a.u_n + cell * ND;
+  const float* sUn = smem + L::OFF_UN;  // u_n of this cell, copied before any write
 #pragma unroll
   for (int m = 0; m < ND; ++m) {
     const int mx = m % N, my = DIM == 2 ? m / N : 0;
@@ -875,7 +896,10 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     bad |= !isfinite(d);
     if (a.mode & kModeRK) {
       float v = fmaf(a.dt, d, c[m]);
-      if (a.rk_a != 0.0f) v = fmaf(a.rk_b, v - un[m], un[m]);  // plain load: u_n may alias u_out
+      if (pre_un) {
+        const float un = sUn[m * NT + threadIdx.x];
+        v = fmaf(a.rk_b, v - un, un);
+      }
       out[m] = v;
     } else {
       out[m] = d;
