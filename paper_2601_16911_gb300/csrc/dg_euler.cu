@@ -128,23 +128,54 @@ __device__ __forceinline__ void hll_dev(float g, const EulerMean& M, const float
   }
 }
 
+// Shared-memory layout of the Euler stage tile (floats).
 template <int P, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
+struct EulerLayout {
+  static constexpr int N = P + 1, ND = N * N, NT = TX * TY;
+  static constexpr int HX = TX + 2, HY = TY + 2, NH = HX * HY;
+  static constexpr int NVT = (TX + 1) * (TY + 1);
+  static constexpr int OFF_SC = 0;                    // [NV][ND][NH] tile + halo, mode-major
+  static constexpr int OFF_ST = OFF_SC + NV * ND * NH; // [ND][NVT] density vertex candidates
+  static constexpr int OFF_NQ = OFF_ST + ND * NVT;     // [ND][NT] pointwise density indicator
+  static constexpr int FLOATS = OFF_NQ + ND * NT;
+  static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
+};
+
+// One thread per cell after the vertex phase.  The work is ordered so that nothing
+// larger than one face's traces or one row of volume nodes is held at a time:
+//   faces (rolled over faces and nodes): own and neighbour traces, HLL, projection onto
+//     the tangential modes, and lambda_e over the face nodes;
+//   volume pass A (rolled over node rows): flux deviation projected into r, lambda_e
+//     over the volume nodes, and the two sums of stage (d) per variable;
+//   volume pass B, only where the viscosity (1 - gamma_e) nu_e is non-zero: the
+//     alpha-weighted viscous term.
+// Minimum resident CTAs the register allocation must allow, from a sweep on the 512^2
+// quadrants (stage time, ms: p = 2: 0.21 uncapped, 0.20 at 4 CTAs; p = 3: 0.45 uncapped,
+// 0.41 at 3 CTAs; p = 4 (8x8 tiles): 0.97 uncapped, 1.15 at 6 CTAs).
+template <int P, int TX, int TY>
+constexpr int euler_min_ctas() {
+  return P <= 2 ? 4 * (128 / (TX * TY)) : P == 3 ? 3 * (128 / (TX * TY)) : 1;
+}
+
+template <int P, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
     dg_euler_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<2, P> T) {
   using Tb = DgTables<2, P>;
+  using L = EulerLayout<P, TX, TY>;
   constexpr int N = P + 1, ND = Tb::ND, NS = Tb::NS, NC = 4;
   constexpr int NT = TX * TY;
-  constexpr int HX = TX + 2, HY = TY + 2, NH = HX * HY;
-  constexpr int VXT = TX + 1, VYT = TY + 1, NVT = VXT * VYT;
-  extern __shared__ float smem[];
-  float* sc = smem;                 // [NV][ND][NH]
-  float* st = smem + NV * ND * NH;  // [ND][NVT] density vertex candidates
+  constexpr int HX = TX + 2, NH = HX * (TY + 2);
+  constexpr int VXT = TX + 1, NVT = VXT * (TY + 1);
+  extern __shared__ __align__(16) float smem[];
+  float* sc = smem + L::OFF_SC;
+  float* st = smem + L::OFF_ST;
+  float* sNq = smem + L::OFF_NQ;
   const int nx = a.nx, ny = a.ny;
   const size_t ncell = (size_t)nx * ny;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const float g = a.gas_gamma;
 
-  // ---- load tile + halo of all variables ------------------------------------------------
+  // ---- load tile + halo of all variables (asynchronous copies) ---------------------------
   for (int f = threadIdx.x; f < NV * NH * ND; f += NT) {
     int v = f / (NH * ND);
     int rem0 = f - v * (NH * ND);
@@ -160,9 +191,10 @@ __global__ void __launch_bounds__(TX* TY)
     if (gj < 0 || gj >= ny) {
       if (a.pery) gj = (gj + ny) % ny; else ok = false;
     }
-    sc[(v * ND + mm) * NH + r * HX + cc] =
-        ok ? __ldg(a.u_in + ((size_t)v * ncell + (size_t)gj * nx + gi) * ND + mm) : 0.0f;
+    cp_async4(sc + (v * ND + mm) * NH + r * HX + cc,
+              ok ? a.u_in + ((size_t)v * ncell + (size_t)gj * nx + gi) * ND + mm : a.u_in, ok ? 4 : 0);
   }
+  cp_async_wait_all();
   __syncthreads();
 
   // ---- (a)+(b): density vertex candidates ---------------------------------------------------
@@ -276,124 +308,114 @@ __global__ void __launch_bounds__(TX* TY)
       gam = 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
   }
 
-  // ---- own traces at the face nodes (deviations from the cell mean), lambda_e ---------------
+
+  // ---- faces: traces, HLL, projection; lambda_e over the face nodes ----------------------------
   bool bad = false;
   float Ubar[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) Ubar[v] = C(v, 0, hc);
   const EulerMean M = euler_mean(g, Ubar);
-  float oR[NV][N], oL[NV][N], oT[NV][N], oB[NV][N];
+  const bool sensor_only = (a.mode & kModeSensorOnly) != 0;
+  float r[NV][ND];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    float trR[N], trL[N], trT[N], trB[N];
+  for (int v = 0; v < NV; ++v)
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      float r = 0.0f, l = 0.0f, t = 0.0f, b = 0.0f;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const float cr = (i + N * j) ? C(v, i + N * j, hc) : 0.0f, ct = (j + N * i) ? C(v, j + N * i, hc) : 0.0f;
-        r += cr;
-        l += (i & 1) ? -cr : cr;
-        t += ct;
-        b += (i & 1) ? -ct : ct;
-      }
-      trR[j] = r;
-      trL[j] = l;
-      trT[j] = t;
-      trB[j] = b;
-    }
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-      float r = 0.0f, l = 0.0f, t = 0.0f, b = 0.0f;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        r = fmaf(T.B[q][j], trR[j], r);
-        l = fmaf(T.B[q][j], trL[j], l);
-        t = fmaf(T.B[q][j], trT[j], t);
-        b = fmaf(T.B[q][j], trB[j], b);
-      }
-      oR[v][q] = r;
-      oL[v][q] = l;
-      oT[v][q] = t;
-      oB[v][q] = b;
-    }
-  }
+    for (int m = 0; m < ND; ++m) r[v][m] = 0.0f;
   float lam = 0.0f;
-#pragma unroll
-  for (int q = 0; q < N; ++q) {
-    float U[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oR[v][q];
-    lam = fmaxf(lam, euler_speed(g, U, bad));
-#pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oL[v][q];
-    lam = fmaxf(lam, euler_speed(g, U, bad));
-#pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oT[v][q];
-    lam = fmaxf(lam, euler_speed(g, U, bad));
-#pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + oB[v][q];
-    lam = fmaxf(lam, euler_speed(g, U, bad));
-  }
-  // volume nodes: values, and the gradient data needed by stage (d)
-  float gsq[NV][ND];  // |grad U_v|^2 at the volume nodes (physical)
-#pragma unroll
-  for (int qx = 0; qx < N; ++qx) {
-    float tb[NV][N], td[NV][N];
+  // face f: 0 right (+x), 1 left, 2 top (+y), 3 bottom
+#pragma unroll 1
+  for (int f = 0; f < 4; ++f) {
+    const int dirn = f >> 1;
+    const bool upper = (f & 1) == 0;
+    const int off = dirn == 0 ? (upper ? 1 : -1) : (upper ? HX : -HX);
+    const bool has = dirn == 0 ? (a.perx || (upper ? gi + 1 < nx : gi > 0))
+                               : (a.pery || (upper ? gj + 1 < ny : gj > 0));
+    // tangential trace coefficients of the own and the neighbouring cell along this face
+    // (non-mean modes; the neighbour meets the face with its opposite side)
+    float tro[NV][N], trn[NV][N];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int my = 0; my < N; ++my) {
-        float s0 = 0.0f, s1 = 0.0f;
+      for (int j = 0; j < N; ++j) {
+        float so = 0.0f, sn = 0.0f;
 #pragma unroll
-        for (int mx = 0; mx < N; ++mx) {
-          s0 = fmaf(T.B[qx][mx], C(v, mx + N * my, hc), s0);
-          s1 = fmaf(T.Bd[qx][mx], C(v, mx + N * my, hc), s1);
+        for (int i = 0; i < N; ++i) {
+          const int m = dirn == 0 ? i + N * j : j + N * i;
+          if (m == 0) continue;
+          const float co = C(v, m, hc), cn = C(v, m, hc + off);
+          so += (!upper && (i & 1)) ? -co : co;
+          sn += (upper && (i & 1)) ? -cn : cn;
         }
-        tb[v][my] = s0;
-        td[v][my] = s1;
+        tro[v][j] = so;
+        trn[v][j] = sn;
       }
+    float dmean[NV];
 #pragma unroll
-    for (int qy = 0; qy < N; ++qy) {
-      float U[NV];
+    for (int v = 0; v < NV; ++v) dmean[v] = C(v, 0, hc + off) - Ubar[v];
+    float h[NV][N];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int j = 0; j < N; ++j) h[v][j] = 0.0f;
+#pragma unroll 1
+    for (int q = 0; q < N; ++q) {
+      float dO[NV], dN[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        float u = 0.0f, ux = 0.0f, uy = 0.0f;
+        float so = 0.0f, sn = 0.0f;
 #pragma unroll
-        for (int my = 0; my < N; ++my) {
-          u = fmaf(T.B[qy][my], tb[v][my], u);
-          ux = fmaf(T.B[qy][my], td[v][my], ux);
-          uy = fmaf(T.Bd[qy][my], tb[v][my], uy);
+        for (int j = 0; j < N; ++j) {
+          const float bq = T.B[q][j];
+          so = fmaf(bq, tro[v][j], so);
+          sn = fmaf(bq, trn[v][j], sn);
         }
-        U[v] = u;
-        ux *= a.two_dx;
-        uy *= a.two_dy;
-        gsq[v][qx + N * qy] = fmaf(ux, ux, uy * uy);
+        dO[v] = so;
+        dN[v] = has ? dmean[v] + sn : so;  // transmissive side: ghost = own trace
       }
-      lam = fmaxf(lam, euler_speed(g, U, bad));
+      {
+        float U[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + dO[v];
+        lam = fmaxf(lam, euler_speed(g, U, bad));
+      }
+      if (sensor_only) continue;
+      float F[NV];
+      if (upper)
+        hll_dev(g, M, dO, dN, dirn, F, bad);
+      else
+        hll_dev(g, M, dN, dO, dirn, F, bad);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float wf = T.w[q] * F[v];
+#pragma unroll
+        for (int j = 0; j < N; ++j) h[v][j] = fmaf(wf, T.B[q][j], h[v][j]);
+      }
     }
-  }
-  const float nu = lam * a.nu_scale;
-  if (a.gamma_out) a.gamma_out[cell] = gam;
-  if (a.nu_out) a.nu_out[cell] = nu;
-  if (a.lambda_out) a.lambda_out[cell] = lam;
-  if (a.mode & kModeSensorOnly) {
-    if (bad) atomicOr(a.status, kStatPositivity);
-    return;
+    if (sensor_only) continue;
+    // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
+    const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int my = 0; my < N; ++my)
+#pragma unroll
+        for (int mx = 0; mx < N; ++mx) {
+          const int nrm = dirn == 0 ? mx : my;
+          const float hv = dirn == 0 ? h[v][my] : h[v][mx];
+          r[v][mx + N * my] = upper ? fmaf(-s2d, hv, r[v][mx + N * my])
+                                    : fmaf(s2d, (nrm & 1) ? -hv : hv, r[v][mx + N * my]);
+        }
   }
 
-  // ---- (d) SC weights: alpha~ from the density, f_q per variable -----------------------------
+  // ---- troubled cells: the density's pointwise indicator Nq at the volume nodes -------------
   bool troubled = a.sc && gam < a.c_gamma && n0 > 1e-30f;
-  if (a.troubled_override) {
-    int ov = a.troubled_override[cell];
+  if (!sensor_only && a.troubled_override) {
+    const int ov = a.troubled_override[cell];
     if (ov >= 0) troubled = ov && n0 > 1e-30f;
   }
-  float Nq[ND];
-  float afac[NV];  // alpha_{v,q} = Nq[q] * afac[v]; afac < 0 marks alpha = 1
-#pragma unroll
-  for (int v = 0; v < NV; ++v) afac[v] = -1.0f;
-  if (troubled && gam < 1.0f) {
-#pragma unroll
+  const bool need_sc = !sensor_only && troubled && gam < 1.0f;
+  if (need_sc) {
+#pragma unroll 1
     for (int qx = 0; qx < N; ++qx) {
       float X[N][N];
 #pragma unroll
@@ -405,7 +427,7 @@ __global__ void __launch_bounds__(TX* TY)
           for (int mx = 0; mx < N; ++mx) acc = fmaf(T.Bk[kx][qx][mx], C(0, mx + N * my, hc), acc);
           X[kx][my] = acc;
         }
-#pragma unroll
+#pragma unroll 1
       for (int qy = 0; qy < N; ++qy) {
         float s2 = 0.0f;
 #pragma unroll
@@ -418,202 +440,177 @@ __global__ void __launch_bounds__(TX* TY)
             for (int my = 0; my < N; ++my) d = fmaf(T.Bk[ky][qy][my], X[kx][my], d);
             s2 = fmaf(T.sigma[kx + N * ky] * d, d, s2);
           }
-        Nq[qx + N * qy] = sqrtf(s2);
+        sNq[(qx + N * qy) * NT + threadIdx.x] = sqrtf(s2);
       }
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float s1 = 0.0f, s2 = 0.0f;
-#pragma unroll
-      for (int q = 0; q < ND; ++q) {
-        const float W = T.w[q % N] * T.w[q / N];
-        s1 = fmaf(W, gsq[v][q], s1);
-        s2 = fmaf(W * Nq[q], gsq[v][q], s2);
-      }
-      if (s2 > 0.0f) afac[v] = s1 / s2;
-    }
-  }
-  if (a.troubled_out) a.troubled_out[cell] = troubled ? 1 : 0;
-  if (a.alpha_out) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-      for (int q = 0; q < ND; ++q) a.alpha_out[(cell * NV + v) * ND + q] = afac[v] >= 0.0f ? Nq[q] * afac[v] : 1.0f;
   }
 
-  // ---- (e) residual ------------------------------------------------------------------------------
-  float r[NV][ND];
-  const float mu = (1.0f - gam) * nu;
-  {
-    const bool hasR = a.perx || gi + 1 < nx, hasL = a.perx || gi > 0;
-    const bool hasT = a.pery || gj + 1 < ny, hasB = a.pery || gj > 0;
-    // neighbour traces, projected to the face nodes one variable at a time
-    float FR[NV][N], FL[NV][N], FT[NV][N], FB[NV][N];
-    float vR[NV][N], vL[NV][N], vT[NV][N], vB[NV][N];
+  // ---- volume pass A: flux deviation into r, lambda_e, the sums of stage (d) ----------------
+  float s1[NV], s2[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float nR[N], nL[N], nT[N], nB[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        float r0 = 0.0f, l0 = 0.0f, t0 = 0.0f, b0 = 0.0f;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          if (i + N * j) {
-            const float cr = C(v, i + N * j, hc + 1), cl = C(v, i + N * j, hc - 1);
-            r0 += (i & 1) ? -cr : cr;
-            l0 += cl;
-          }
-          if (j + N * i) {
-            const float ct = C(v, j + N * i, hc + HX), cb = C(v, j + N * i, hc - HX);
-            t0 += (i & 1) ? -ct : ct;
-            b0 += cb;
-          }
-        }
-        nR[j] = r0;
-        nL[j] = l0;
-        nT[j] = t0;
-        nB[j] = b0;
-      }
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        float xr = 0.0f, xl = 0.0f, xt = 0.0f, xb = 0.0f;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          xr = fmaf(T.B[q][j], nR[j], xr);
-          xl = fmaf(T.B[q][j], nL[j], xl);
-          xt = fmaf(T.B[q][j], nT[j], xt);
-          xb = fmaf(T.B[q][j], nB[j], xb);
-        }
-        vR[v][q] = hasR ? (C(v, 0, hc + 1) - Ubar[v]) + xr : oR[v][q];
-        vL[v][q] = hasL ? (C(v, 0, hc - 1) - Ubar[v]) + xl : oL[v][q];
-        vT[v][q] = hasT ? (C(v, 0, hc + HX) - Ubar[v]) + xt : oT[v][q];
-        vB[v][q] = hasB ? (C(v, 0, hc - HX) - Ubar[v]) + xb : oB[v][q];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-      float UL[NV], UR[NV], F[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) { UL[v] = oR[v][q]; UR[v] = vR[v][q]; }
-      hll_dev(g, M, UL, UR, 0, F, bad);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) FR[v][q] = F[v];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) { UL[v] = vL[v][q]; UR[v] = oL[v][q]; }
-      hll_dev(g, M, UL, UR, 0, F, bad);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) FL[v][q] = F[v];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) { UL[v] = oT[v][q]; UR[v] = vT[v][q]; }
-      hll_dev(g, M, UL, UR, 1, F, bad);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) FT[v][q] = F[v];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) { UL[v] = vB[v][q]; UR[v] = oB[v][q]; }
-      hll_dev(g, M, UL, UR, 1, F, bad);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) FB[v][q] = F[v];
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float hR[N], hL[N], hT[N], hB[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-          const float wb = T.w[q] * T.B[q][j];
-          s0 = fmaf(wb, FR[v][q], s0);
-          s1 = fmaf(wb, FL[v][q], s1);
-          s2 = fmaf(wb, FT[v][q], s2);
-          s3 = fmaf(wb, FB[v][q], s3);
-        }
-        hR[j] = s0;
-        hL[j] = s1;
-        hT[j] = s2;
-        hB[j] = s3;
-      }
-#pragma unroll
-      for (int my = 0; my < N; ++my)
-#pragma unroll
-        for (int mx = 0; mx < N; ++mx) {
-          const float fxv = hR[my] - ((mx & 1) ? -hL[my] : hL[my]);
-          const float fyv = hT[mx] - ((my & 1) ? -hB[mx] : hB[mx]);
-          r[v][mx + N * my] = -(a.two_dx * fxv + a.two_dy * fyv);
-        }
-    }
-  }
-  // volume
-#pragma unroll
+  for (int v = 0; v < NV; ++v) s1[v] = s2[v] = 0.0f;
+#pragma unroll 1
   for (int qx = 0; qx < N; ++qx) {
     float tb[NV][N], td[NV][N];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int my = 0; my < N; ++my) {
-        float s0 = 0.0f, s1 = 0.0f;
+        float s0 = 0.0f, sd = 0.0f;
 #pragma unroll
         for (int mx = 0; mx < N; ++mx) {
           const float cm = (mx + N * my) ? C(v, mx + N * my, hc) : 0.0f;  // deviation: no mean mode
           s0 = fmaf(T.B[qx][mx], cm, s0);
-          s1 = fmaf(T.Bd[qx][mx], cm, s1);
+          sd = fmaf(T.Bd[qx][mx], cm, sd);
         }
         tb[v][my] = s0;
-        td[v][my] = s1;
+        td[v][my] = sd;
       }
-    float Gx[NV][N], Gy[NV][N];
+    float hx[NV][N], hy[NV][N];
 #pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int my = 0; my < N; ++my) hx[v][my] = hy[v][my] = 0.0f;
+#pragma unroll 1
     for (int qy = 0; qy < N; ++qy) {
       const int q = qx + N * qy;
-      float dU[NV], Ux[NV], Uy[NV], Fx[NV], Fy[NV];
+      const float W = T.w[qx] * T.w[qy];
+      float dU[NV];
+      const float nq = need_sc ? sNq[q * NT + threadIdx.x] : 0.0f;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         float u = 0.0f, ux = 0.0f, uy = 0.0f;
 #pragma unroll
         for (int my = 0; my < N; ++my) {
-          u = fmaf(T.B[qy][my], tb[v][my], u);
-          ux = fmaf(T.B[qy][my], td[v][my], ux);
+          const float bq = T.B[qy][my];
+          u = fmaf(bq, tb[v][my], u);
+          ux = fmaf(bq, td[v][my], ux);
           uy = fmaf(T.Bd[qy][my], tb[v][my], uy);
         }
         dU[v] = u;
-        Ux[v] = ux;
-        Uy[v] = uy;
-      }
-      euler_dflux(g, M, dU, Fx, Fy);
-      const float W = T.w[qx] * T.w[qy];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float al = afac[v] >= 0.0f ? Nq[q] * afac[v] : 1.0f;
-        Gx[v][qy] = W * (Fx[v] - mu * al * a.two_dx * Ux[v]);
-        Gy[v][qy] = W * (Fy[v] - mu * al * a.two_dy * Uy[v]);
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float hx[N], hy[N];
-#pragma unroll
-      for (int my = 0; my < N; ++my) {
-        float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-        for (int qy = 0; qy < N; ++qy) {
-          s0 = fmaf(T.B[qy][my], Gx[v][qy], s0);
-          s1 = fmaf(T.Bd[qy][my], Gy[v][qy], s1);
+        if (need_sc) {
+          ux *= a.two_dx;
+          uy *= a.two_dy;
+          const float gsq = fmaf(ux, ux, uy * uy);
+          s1[v] = fmaf(W, gsq, s1[v]);
+          s2[v] = fmaf(W * nq, gsq, s2[v]);
         }
-        hx[my] = s0;
-        hy[my] = s1;
       }
+      {
+        float U[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + dU[v];
+        lam = fmaxf(lam, euler_speed(g, U, bad));
+      }
+      if (sensor_only) continue;
+      float Fx[NV], Fy[NV];
+      euler_dflux(g, M, dU, Fx, Fy);
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int my = 0; my < N; ++my) {
+          hx[v][my] = fmaf(W * Fx[v], T.B[qy][my], hx[v][my]);
+          hy[v][my] = fmaf(W * Fy[v], T.Bd[qy][my], hy[v][my]);
+        }
+    }
+    if (sensor_only) continue;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int my = 0; my < N; ++my)
 #pragma unroll
         for (int mx = 0; mx < N; ++mx) {
           float val = r[v][mx + N * my];
-          val = fmaf(a.two_dx * T.Bd[qx][mx], hx[my], val);
-          val = fmaf(a.two_dy * T.B[qx][mx], hy[my], val);
+          val = fmaf(a.two_dx * T.Bd[qx][mx], hx[v][my], val);
+          val = fmaf(a.two_dy * T.B[qx][mx], hy[v][my], val);
           r[v][mx + N * my] = val;
         }
+  }
+  const float nu = lam * a.nu_scale;
+  if (a.gamma_out) a.gamma_out[cell] = gam;
+  if (a.nu_out) a.nu_out[cell] = nu;
+  if (a.lambda_out) a.lambda_out[cell] = lam;
+  if (sensor_only) {
+    if (bad) atomicOr(a.status, kStatPositivity);
+    return;
+  }
+
+  // ---- (d) SC weights: alpha_{v,q} = Nq[q] afac[v] (afac < 0: alpha = 1) ------------------------
+  float afac[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) afac[v] = (need_sc && s2[v] > 0.0f) ? s1[v] / s2[v] : -1.0f;
+  if (a.troubled_out) a.troubled_out[cell] = troubled ? 1 : 0;
+  if (a.alpha_out) {
+#pragma unroll 1
+    for (int q = 0; q < ND; ++q) {
+      const float nq = need_sc ? sNq[q * NT + threadIdx.x] : 0.0f;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) a.alpha_out[(cell * NV + v) * ND + q] = afac[v] >= 0.0f ? nq * afac[v] : 1.0f;
     }
   }
-  // M^{-1}, output
+
+  // ---- volume pass B: the viscous term, where (1 - gamma_e) nu_e > 0 -----------------------------
+  const float mu = (1.0f - gam) * nu;
+  if (mu > 0.0f) {
+#pragma unroll 1
+    for (int qx = 0; qx < N; ++qx) {
+      float tb[NV][N], td[NV][N];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int my = 0; my < N; ++my) {
+          float s0 = 0.0f, sd = 0.0f;
+#pragma unroll
+          for (int mx = 0; mx < N; ++mx) {
+            const float cm = (mx + N * my) ? C(v, mx + N * my, hc) : 0.0f;
+            s0 = fmaf(T.B[qx][mx], cm, s0);
+            sd = fmaf(T.Bd[qx][mx], cm, sd);
+          }
+          tb[v][my] = s0;
+          td[v][my] = sd;
+        }
+      float hx[NV][N], hy[NV][N];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int my = 0; my < N; ++my) hx[v][my] = hy[v][my] = 0.0f;
+#pragma unroll 1
+      for (int qy = 0; qy < N; ++qy) {
+        const int q = qx + N * qy;
+        const float W = T.w[qx] * T.w[qy];
+        const float nq = need_sc ? sNq[q * NT + threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          float ux = 0.0f, uy = 0.0f;
+#pragma unroll
+          for (int my = 0; my < N; ++my) {
+            ux = fmaf(T.B[qy][my], td[v][my], ux);
+            uy = fmaf(T.Bd[qy][my], tb[v][my], uy);
+          }
+          const float al = afac[v] >= 0.0f ? nq * afac[v] : 1.0f;
+          const float gx = -W * mu * al * a.two_dx * ux, gy = -W * mu * al * a.two_dy * uy;
+#pragma unroll
+          for (int my = 0; my < N; ++my) {
+            hx[v][my] = fmaf(gx, T.B[qy][my], hx[v][my]);
+            hy[v][my] = fmaf(gy, T.Bd[qy][my], hy[v][my]);
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int my = 0; my < N; ++my)
+#pragma unroll
+          for (int mx = 0; mx < N; ++mx) {
+            float val = r[v][mx + N * my];
+            val = fmaf(a.two_dx * T.Bd[qx][mx], hx[v][my], val);
+            val = fmaf(a.two_dy * T.B[qx][mx], hy[v][my], val);
+            r[v][mx + N * my] = val;
+          }
+    }
+  }
+
+  // ---- M^{-1}, output ---------------------------------------------------------------------------
   bool nonfinite = false;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -626,7 +623,7 @@ __global__ void __launch_bounds__(TX* TY)
       nonfinite |= !isfinite(d);
       if (a.mode & kModeRK) {
         float val = fmaf(a.dt, d, C(v, m, hc));
-        if (a.rk_a != 0.0f) val = fmaf(a.rk_b, val - un[m], un[m]);
+        if (a.rk_a != 0.0f) val = fmaf(a.rk_b, val - un[m], un[m]);  // plain load: u_n may alias u_out
         out[m] = val;
       } else {
         out[m] = d;
@@ -640,7 +637,7 @@ __global__ void __launch_bounds__(TX* TY)
 template <int P, int TX, int TY>
 cudaError_t launch_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
   using Tb = DgTables<2, P>;
-  constexpr size_t smem = sizeof(float) * ((size_t)NV * Tb::ND * (TX + 2) * (TY + 2) + (size_t)Tb::ND * (TX + 1) * (TY + 1));
+  constexpr size_t smem = EulerLayout<P, TX, TY>::BYTES;
   static_assert(smem <= 220 * 1024, "tile too large for shared memory");
   auto kern = dg_euler_stage<P, TX, TY>;
   if (smem > 48 * 1024) {
