@@ -30,6 +30,8 @@
  *   or_features       inputs of the surrogate sensor (not in the paper): per corner
  *                     vertex candidate (eq. taylorcand) mean minus cell mean and
  *                     h-scaled gradient at the vertex, over ||u^e||_e + eps (eq. snorm)
+ *   or_positivity     positivity-preserving scaling limiter for the Euler equations
+ *                     (Zhang and Shu's published limiter, restated; not in the paper)
  *   or_limit          Sec. 3 (HWENO limiter: u^e overwritten by u^{e,*} of eq. finalweno
  *                     built from the average-corrected candidates, the equation for
  *                     ubar*_i after Fig. stencils)
@@ -67,6 +69,15 @@
  *       sensor_mode sets it (SMOOTH gives the classical limiter-only scheme).
  *   A28 the overwrite uses the average-corrected candidates, so u^{e,*} keeps the cell
  *       mean; its weights omega_l are those of the sensor (eq. finalweno).
+ *   P1  positivity limiter points: the volume Gauss nodes and the face Gauss nodes
+ *       of the cell (where the scheme evaluates the solution).
+ *   P2  eps_e = min(1e-13, mean density, mean pressure).
+ *   P3  density first: theta_1 = min(1, (rho_bar - eps)/(rho_bar - rho_min)) when
+ *       rho_min < eps, scaling the density's non-mean modes; then pressure:
+ *       theta_2 = min over points with p < eps of the t in [0, 1] with
+ *       p(U_bar + t (U_q - U_bar)) = eps (one root: p is concave along the line),
+ *       scaling the non-mean modes of every variable.  Applied after every RK stage.
+ *   P4  a cell whose mean is not admissible is left as it is and reported.
  * CG is parity-unpinned against the paper's exact values (A12, A13 are readings); its
  * pins are conservation, the sweeps' convergence to the consistent-mass solve, the
  * shared sensor's pins and the design order / Table bur2 magnitudes.
@@ -111,6 +122,7 @@ typedef struct {
   int sc_quadrature, sensor_mode; /* sensor_mode: 0 computed, 1 gamma=1, 2 gamma=0 */
   double lambda_const, gas_gamma, adv_vx, adv_vy;
   int hweno_limiter; /* 1: or_ssprk3 applies or_limit to every stage result (A27) */
+  int positivity;    /* 1: or_ssprk3 applies or_positivity to every stage result (P1-P4) */
 } or_desc;
 
 /* ------------------------------------------------------------------------- */
@@ -1280,6 +1292,81 @@ int or_features(const or_desc* d, const double* u, double* feats, double* gamma_
   return st;
 }
 
+/* Pressure of a conserved state. */
+static double or_pressure(double g, const double* U) {
+  return (g - 1.0) * (U[3] - 0.5 * (U[1] * U[1] + U[2] * U[2]) / U[0]);
+}
+
+/* Positivity limiter (readings P1-P4) of a 2D DG Euler state, cell by cell: out = the
+ * limited coefficients; theta (may be NULL) = theta_1 theta_2 of each cell (1: unchanged);
+ * returns OR_ERR_POSITIVITY when some cell's mean is not admissible (that cell is copied).
+ * The root of p(U_bar + t dU) = eps is found by bisection on [0, 1] to 1e-15. */
+int or_positivity(const or_desc* d, const double* u, double* out, double* theta) {
+  if (d->system != OR_EULER || d->kind != OR_DG || d->dim != 2) return OR_ERR_UNSUPPORTED;
+  or_mesh m;
+  int st = or_mesh_init(d, &m);
+  if (st) return st;
+  const double g = d->gas_gamma;
+  const int nd = m.nd, n = m.n;
+  const size_t N = or_state_len(&m);
+  memcpy(out, u, sizeof(double) * N);
+  int bad = 0;
+  /* point set: volume Gauss nodes, then the n nodes of each face */
+  const int npts = m.nq + 4 * n;
+  double* px = (double*)malloc(sizeof(double) * npts);
+  double* py = (double*)malloc(sizeof(double) * npts);
+  if (!px || !py) { free(px); free(py); or_mesh_free(&m); return OR_ERR_NOMEM; }
+  for (int q = 0; q < m.nq; ++q) {
+    double W;
+    or_qpoint(&m, q, &px[q], &py[q], &W);
+  }
+  for (int k = 0; k < n; ++k) {
+    px[m.nq + k] = 1.0;          py[m.nq + k] = m.gx[k];
+    px[m.nq + n + k] = -1.0;     py[m.nq + n + k] = m.gx[k];
+    px[m.nq + 2 * n + k] = m.gx[k]; py[m.nq + 2 * n + k] = 1.0;
+    px[m.nq + 3 * n + k] = m.gx[k]; py[m.nq + 3 * n + k] = -1.0;
+  }
+  for (int e = 0; e < m.ncell; ++e) {
+    double Ub[4];
+    for (int v = 0; v < 4; ++v) Ub[v] = or_cell(&m, u, v, e)[0];
+    const double pb = or_pressure(g, Ub);
+    if (theta) theta[e] = 1.0;
+    if (!(Ub[0] > 0.0) || !(pb > 0.0)) { bad = 1; continue; }
+    const double eps = fmin(1e-13, fmin(Ub[0], pb));
+    /* density */
+    double rmin = INFINITY;
+    for (int q = 0; q < npts; ++q) rmin = fmin(rmin, or_du(&m, or_cell(&m, u, 0, e), 0, 0, px[q], py[q]));
+    double th1 = 1.0;
+    if (rmin < eps) th1 = fmin(1.0, (Ub[0] - eps) / (Ub[0] - rmin));
+    /* pressure along the segments from the mean to each (density-limited) point */
+    double th2 = 1.0;
+    for (int q = 0; q < npts; ++q) {
+      double Uq[4];
+      for (int v = 0; v < 4; ++v) Uq[v] = or_du(&m, or_cell(&m, u, v, e), 0, 0, px[q], py[q]);
+      Uq[0] = Ub[0] + th1 * (Uq[0] - Ub[0]);
+      if (or_pressure(g, Uq) >= eps) continue;
+      double lo = 0.0, hi = 1.0; /* p(lo) >= eps > p(hi) */
+      for (int it = 0; it < 200 && hi - lo > 1e-15; ++it) {
+        const double t = 0.5 * (lo + hi);
+        double Ut[4];
+        for (int v = 0; v < 4; ++v) Ut[v] = Ub[v] + t * (Uq[v] - Ub[v]);
+        if (or_pressure(g, Ut) >= eps) lo = t; else hi = t;
+      }
+      th2 = fmin(th2, lo);
+    }
+    for (int v = 0; v < 4; ++v) {
+      const double f = (v == 0 ? th1 : 1.0) * th2;
+      double* c = out + ((size_t)v * m.ncell + e) * nd;
+      for (int mi = 1; mi < nd; ++mi) c[mi] *= f;
+    }
+    if (theta) theta[e] = th1 * th2;
+  }
+  free(px);
+  free(py);
+  or_mesh_free(&m);
+  return bad ? OR_ERR_POSITIVITY : OR_OK;
+}
+
 /* HWENO limiter of a DG scalar state (see or_limit_m); all_cells = 1 limits every
  * cell regardless of the sensor. */
 int or_limit(const or_desc* d, const double* u, int all_cells, double* out, int* troubled) {
@@ -1329,6 +1416,13 @@ int or_ssprk3(const or_desc* d, double* u, double dt, int nsteps) {
   if (d->hweno_limiter && !st) {                                       \
     st = or_limit(d, x, 0, lim, NULL);                                 \
     if (!st) memcpy(x, lim, sizeof(double) * N);                       \
+  }                                                                    \
+  OR_POS_STAGE(x)
+  /* P3: with the positivity limiter on, every stage result is limited too */
+#define OR_POS_STAGE(x)                                                \
+  if (d->positivity && !st) {                                          \
+    st = or_positivity(d, x, lim, NULL);                               \
+    if (!st) memcpy(x, lim, sizeof(double) * N);                       \
   }
   for (int s = 0; s < nsteps && !st; ++s) {
     st = or_residual(d, u, NULL, L, NULL, NULL, NULL, NULL);
@@ -1347,6 +1441,7 @@ int or_ssprk3(const or_desc* d, double* u, double dt, int nsteps) {
     OR_LIMIT_STAGE(u)
   }
 #undef OR_LIMIT_STAGE
+#undef OR_POS_STAGE
   free(L);
   free(u1);
   free(u2);

@@ -49,7 +49,7 @@ class _Desc(ctypes.Structure):
         ("sc_quadrature", ctypes.c_int), ("sensor_mode", ctypes.c_int),
         ("lambda_const", ctypes.c_double), ("gas_gamma", ctypes.c_double),
         ("adv_vx", ctypes.c_double), ("adv_vy", ctypes.c_double),
-        ("hweno_limiter", ctypes.c_int),
+        ("hweno_limiter", ctypes.c_int), ("positivity", ctypes.c_int),
     ]
 
 
@@ -59,7 +59,7 @@ DEFAULTS = dict(
     dim=2, nx=8, ny=8, degree=2, kind=DG, system=BURGERS, bc=(PERIODIC,) * 4,
     x0=0.0, x1=1.0, y0=0.0, y1=1.0, eps=1e-6, r=2.0, q=1.0, gamma_vertex=1e-3,
     c_gamma=0.9, sc_quadrature=1, sensor_mode=0, lambda_const=0.0, gas_gamma=1.4,
-    adv_vx=1.0, adv_vy=0.0, hweno_limiter=0,
+    adv_vx=1.0, adv_vy=0.0, hweno_limiter=0, positivity=0,
 )
 
 
@@ -95,6 +95,7 @@ def _load():
                 "or_sc_weights": [d, dp, dp, dp, ip],
                 "or_limit": [d, dp, ctypes.c_int, dp, ip],
                 "or_features": [d, dp, dp, dp, dp],
+                "or_positivity": [d, dp, dp, dp],
                 "or_max_wavespeed": [d, dp, dp],
                 "or_ssprk3": [d, dp, ctypes.c_double, ctypes.c_int],
                 "or_mass_total": [d, dp, dp],
@@ -250,6 +251,19 @@ def limit(d: dict, u, all_cells: bool = False):
     tr = np.zeros(c["ncell"], np.int32)
     _check(_load().or_limit(ctypes.byref(_cdesc(d)), _dp(uu), 1 if all_cells else 0, _dp(out), _ip(tr)), "limit")
     return out.reshape(np.shape(u)), tr
+
+
+def positivity(d: dict, u):
+    """Positivity limiter (readings P1-P4): (limited state, theta per cell, status code:
+    0, or 4 when some cell mean is not admissible)."""
+    c = counts(d)
+    uu = _u(u)
+    out = np.zeros_like(uu)
+    th = np.zeros(c["ncell"])
+    code = _load().or_positivity(ctypes.byref(_cdesc(d)), _dp(uu), _dp(out), _dp(th))
+    if code not in (0, 4):
+        _check(code, "positivity")
+    return out.reshape(np.shape(u)), th, code
 
 
 def features(d: dict, u):

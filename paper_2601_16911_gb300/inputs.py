@@ -60,7 +60,7 @@ def mesh(dim, nx, ny=1, degree=2, system=BURGERS, domain=(0.0, 1.0, 0.0, 1.0), b
     d = dict(dim=dim, nx=nx, ny=ny if dim == 2 else 1, degree=degree, kind=kind, system=system, bc=bcs,
              x0=domain[0], x1=domain[1], y0=domain[2], y1=domain[3], eps=1e-6, r=2.0, q=1.0,
              gamma_vertex=1e-3, c_gamma=0.9, sc_quadrature=1, sensor_mode=0, lambda_const=0.0,
-             gas_gamma=1.4, adv_vx=1.0, adv_vy=0.0, hweno_limiter=0)
+             gas_gamma=1.4, adv_vx=1.0, adv_vy=0.0, hweno_limiter=0, positivity=0)
     d.update(params)
     return d
 
