@@ -71,7 +71,10 @@
  *       mean; its weights omega_l are those of the sensor (eq. finalweno).
  *   P1  positivity limiter points: the volume Gauss nodes and the face Gauss nodes
  *       of the cell (where the scheme evaluates the solution).
- *   P2  eps_e = min(1e-13, mean density, mean pressure).
+ *   P2  eps_e = 1e-3 min(mean density, mean pressure): Zhang and Shu take
+ *       min(1e-13, ...) for FP64 arithmetic; the GPU path computes pressures in FP32,
+ *       where a node's pressure is only known to about 1e-7 of the energy, so the
+ *       floor is relative to the cell's own scale.
  *   P3  density first: theta_1 = min(1, (rho_bar - eps)/(rho_bar - rho_min)) when
  *       rho_min < eps, scaling the density's non-mean modes; then pressure:
  *       theta_2 = min over points with p < eps of the t in [0, 1] with
@@ -1301,6 +1304,7 @@ static double or_pressure(double g, const double* U) {
  * limited coefficients; theta (may be NULL) = theta_1 theta_2 of each cell (1: unchanged);
  * returns OR_ERR_POSITIVITY when some cell's mean is not admissible (that cell is copied).
  * The root of p(U_bar + t dU) = eps is found by bisection on [0, 1] to 1e-15. */
+/* (eps_e of reading P2) */
 int or_positivity(const or_desc* d, const double* u, double* out, double* theta) {
   if (d->system != OR_EULER || d->kind != OR_DG || d->dim != 2) return OR_ERR_UNSUPPORTED;
   or_mesh m;
@@ -1332,7 +1336,7 @@ int or_positivity(const or_desc* d, const double* u, double* out, double* theta)
     const double pb = or_pressure(g, Ub);
     if (theta) theta[e] = 1.0;
     if (!(Ub[0] > 0.0) || !(pb > 0.0)) { bad = 1; continue; }
-    const double eps = fmin(1e-13, fmin(Ub[0], pb));
+    const double eps = 1e-3 * fmin(Ub[0], pb);
     /* density */
     double rmin = INFINITY;
     for (int q = 0; q < npts; ++q) rmin = fmin(rmin, or_du(&m, or_cell(&m, u, 0, e), 0, 0, px[q], py[q]));

@@ -1,5 +1,5 @@
 """Pins of the oracle's positivity limiter for the Euler equations (readings P1-P4; the
-scaling limiter of Zhang and Shu restated, not part of the paper): admissible data pass
+scaling limiter of Zhang and Shu restated with a relative floor, not part of the paper): admissible data pass
 unchanged, limited data are admissible at every volume and face Gauss node and keep
 their cell means, the limiting is tight (the pressure touches eps at the binding node),
 and an inadmissible mean is reported."""
@@ -69,15 +69,15 @@ def test_limited_state_is_admissible_tight_and_conservative(p):
     assert np.array_equal(out[:, :, 0], u[:, :, 0])  # means kept
     V = point_values(d, out)
     rho, pr = V[0], pressure(V)
-    eps = np.minimum(1e-13, np.minimum(u[0, :, 0], pressure(u[:, :, 0])))
+    eps = 1e-3 * np.minimum(u[0, :, 0], pressure(u[:, :, 0]))
     assert np.all(rho >= eps[:, None] * (1 - 1e-9) - 1e-12)
     assert np.all(pr >= eps[:, None] - 1e-9)
     limited = th < 1.0
     assert limited.sum() >= 3
     # tight: in each cell limited for pressure, the binding node sits at p = eps
     for e in np.nonzero(limited)[0]:
-        if (pressure(V0[:, e, :]) < eps[e]).any() and pr[e].min() < 1e-6:
-            assert abs(pr[e].min() - eps[e]) < 1e-8
+        if (pressure(V0[:, e, :]) < eps[e]).any() and pr[e].min() < 1.001 * eps[e]:
+            assert abs(pr[e].min() - eps[e]) < 1e-9
     # cells whose nodes were admissible are untouched
     ok = (V0[0] >= eps[:, None]).all(1) & (pressure(V0) >= eps[:, None]).all(1)
     assert np.array_equal(out[:, ok], u[:, ok])
@@ -93,7 +93,7 @@ def test_density_only_violation_scales_only_the_density():
     u[3, 0, 0] = 2.5
     out, th, code = O.positivity(d, u)
     V = point_values(d, out)
-    eps = 1e-13
+    eps = 1e-3 * min(1.0, 0.4 * 2.5)
     assert abs(V[0].min() - eps) < 1e-12
     assert np.array_equal(out[1:], u[1:])
     th1 = (1.0 - eps) / (1.0 - (1.0 - 1.3))  # rho_min = 1 - 1.3 at the face xi = -1
