@@ -95,6 +95,8 @@ typedef struct {
   int hweno_limiter;    /* 1: after every RK stage, cells with computed gamma_e < c_gamma are
                            overwritten by their average-preserving cell-vertex WENO
                            reconstruction (Sec. 3; DG scalar laws only); 0: off */
+  int positivity;       /* 1: after every RK stage, the positivity limiter (cvweno_positivity;
+                           Euler DG only); 0: off */
 } cvweno_params;
 
 typedef struct {
@@ -204,6 +206,16 @@ cvweno_status cvweno_status_check(cvweno_mesh m, void* stream);
  * laws (ERR_UNSUPPORTED otherwise).  Enqueued without synchronisation. */
 cvweno_status cvweno_limit(cvweno_mesh m, const float* u, float* out, int all_cells, int32_t* troubled,
                            void* stream);
+
+/* Positivity limiter for the Euler equations (Zhang and Shu's scaling limiter; the paper
+ * defers positivity to cited work).  Per cell, at the volume and face Gauss nodes: the
+ * density's non-mean modes are scaled by theta_1 so that rho >= eps_e, then the non-mean
+ * modes of all variables by theta_2 so that p >= eps_e, eps_e = 1e-3 min(mean density,
+ * mean pressure); cell means are kept.  u, out: device Euler states (may be the same
+ * array: the limiter is cell-local); theta (device [ncells], may be NULL) receives
+ * theta_1 theta_2.  A cell whose mean is not admissible is copied and raises status bit
+ * 2 (CVWENO_ERR_POSITIVITY at the next status check).  2D Euler DG meshes. */
+cvweno_status cvweno_positivity(cvweno_mesh m, const float* u, float* out, float* theta, void* stream);
 
 /* Per-launch device times, a measurement aid (the paper has no counterpart).
  * cvweno_mesh_set_kernel_timing(m, 1) makes every following step of m (cvweno_step,

@@ -291,7 +291,30 @@ cvweno_status limit_stage(cvweno_mesh m, const float* in, float* out, cudaStream
   return cuda_status(launch(m, a, s));
 }
 
+cvweno_status positivity_stage(cvweno_mesh m, float* x, cudaStream_t s) {
+  StageArgs a = base_args(m);
+  a.u_in = x;
+  a.u_out = x;
+  cudaError_t e = launch_positivity(m, a, nullptr, s);
+  kernel_mark(m, s);
+  return cuda_status(e);
+}
+
 cvweno_status enqueue_step(cvweno_mesh m, float* u, float dt, cudaStream_t s) {
+  if (m->desc.params.positivity) {
+    // every stage result is limited in place (reading P3): the limiter is cell-local
+    if (m->timing) {
+      m->tcount = 0;
+      kernel_mark(m, s);
+    }
+    cvweno_status st = rk_stage(m, u, u, m->d_u1, 0.0f, 1.0f, dt, s);
+    if (st == CVWENO_OK) st = positivity_stage(m, m->d_u1, s);
+    if (st == CVWENO_OK) st = rk_stage(m, m->d_u1, u, m->d_u2, 0.75f, 0.25f, dt, s);
+    if (st == CVWENO_OK) st = positivity_stage(m, m->d_u2, s);
+    if (st == CVWENO_OK) st = rk_stage(m, m->d_u2, u, u, 1.0f / 3.0f, 2.0f / 3.0f, dt, s);
+    if (st == CVWENO_OK) st = positivity_stage(m, u, s);
+    return st;
+  }
   if (m->timing) {
     m->tcount = 0;
     kernel_mark(m, s);
@@ -406,6 +429,8 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   if (p.sensor_mode < 0 || p.sensor_mode > 2) return CVWENO_ERR_ARG;
   if (p.hweno_limiter != 0 && p.hweno_limiter != 1) return CVWENO_ERR_ARG;
   if (p.hweno_limiter && (d->kind != CVWENO_DG || d->system == CVWENO_EULER)) return CVWENO_ERR_UNSUPPORTED;
+  if (p.positivity != 0 && p.positivity != 1) return CVWENO_ERR_ARG;
+  if (p.positivity && (d->kind != CVWENO_DG || d->system != CVWENO_EULER)) return CVWENO_ERR_UNSUPPORTED;
   if (d->kind != CVWENO_DG && d->kind != CVWENO_CG) return CVWENO_ERR_ARG;
   // CG: scalar laws on periodic meshes (no boundary flux term is implemented)
   if (d->kind == CVWENO_CG && (d->system == CVWENO_EULER || d->bc[0] != CVWENO_PERIODIC ||
@@ -572,6 +597,15 @@ cvweno_status cvweno_sensor(cvweno_mesh m, const float* u, float* gamma, float* 
   a.nu_out = nu;
   a.mode = kModeSensorOnly;
   return cuda_status(launch(m, a, S(stream)));
+}
+
+cvweno_status cvweno_positivity(cvweno_mesh m, const float* u, float* out, float* theta, void* stream) {
+  if (!m || !u || !out) return CVWENO_ERR_ARG;
+  if (m->kind != CVWENO_DG || m->desc.system != CVWENO_EULER || m->dim != 2) return CVWENO_ERR_UNSUPPORTED;
+  StageArgs a = base_args(m);
+  a.u_in = u;
+  a.u_out = out;
+  return cuda_status(launch_positivity(m, a, theta, S(stream)));
 }
 
 cvweno_status cvweno_limit(cvweno_mesh m, const float* u, float* out, int all_cells, int32_t* troubled,

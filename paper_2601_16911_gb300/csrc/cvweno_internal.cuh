@@ -176,6 +176,8 @@ void legendre_values(double x, int mmax, double* out);  // P_0..P_mmax at x
 // dg_scalar.cu / dg_euler.cu
 cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
+// dg_euler.cu: the positivity limiter on a.u_in -> a.u_out (may alias), theta per cell
+cudaError_t launch_positivity(const cvweno_mesh_s* m, const StageArgs& a, float* theta, cudaStream_t s);
 // cg_scalar.cu
 cudaError_t launch_stage_cg(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 // api.cu: the stage arguments common to every launch on mesh m (no state pointers, no RK)

@@ -650,6 +650,112 @@ cudaError_t launch_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_
   return cudaGetLastError();
 }
 
+
+// ---- positivity limiter (readings P1-P4; Zhang and Shu's scaling limiter) --------------------
+// One thread per cell, cell-local (no neighbours, so it may run in place).  The cell's
+// coefficients of all four variables are staged in shared memory (mode-major per
+// thread); every volume and face Gauss node is evaluated from them, the density's
+// non-mean modes are scaled to keep rho >= eps_e, then all non-mean modes to keep
+// p >= eps_e, the root of p(U_bar + t dU) = eps_e found by 40 bisection steps.
+template <int P>
+struct PosThreads {
+  static constexpr int value = P >= 4 ? 64 : 128;  // the staged coefficients stay under 48 KB
+};
+
+template <int P>
+__global__ void __launch_bounds__(PosThreads<P>::value)
+    euler_positivity_kernel(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<2, P> T,
+                            float* __restrict__ theta_out) {
+  constexpr int N = P + 1, ND = N * N, NTH = PosThreads<P>::value;
+  __shared__ float sc[NV * ND][NTH];
+  const int64_t ncell = (int64_t)a.nx * a.ny;
+  const int64_t cell = (int64_t)blockIdx.x * NTH + threadIdx.x;
+  if (cell >= ncell) return;
+  const float g = a.gas_gamma;
+#pragma unroll 1
+  for (int k = 0; k < NV * ND; ++k) {
+    const int v = k / ND, m = k - v * ND;
+    sc[k][threadIdx.x] = a.u_in[((int64_t)v * ncell + cell) * ND + m];
+  }
+  float Ub[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Ub[v] = sc[v * ND][threadIdx.x];
+  const float pb = (g - 1.0f) * (Ub[3] - 0.5f * (Ub[1] * Ub[1] + Ub[2] * Ub[2]) / Ub[0]);
+  float th1 = 1.0f, th2 = 1.0f;
+  const bool admissible = Ub[0] > 0.0f && pb > 0.0f;
+  if (admissible) {
+    const float eps = 1e-3f * fminf(Ub[0], pb);
+    // node q: volume (q < N^2: qx + N qy), then faces x = +1, x = -1, y = +1, y = -1
+    auto value = [&](int v, int q) -> float {
+      float s = 0.0f;
+#pragma unroll 1
+      for (int my = 0; my < N; ++my) {
+        float row = 0.0f;
+#pragma unroll
+        for (int mx = 0; mx < N; ++mx) {
+          float bx;
+          if (q < ND) bx = T.B[q % N][mx];
+          else if (q < ND + 2 * N) bx = (q < ND + N || !(mx & 1)) ? 1.0f : -1.0f;
+          else bx = T.B[(q - ND) % N][mx];
+          row = fmaf(bx, sc[v * ND + mx + N * my][threadIdx.x], row);
+        }
+        float by;
+        if (q < ND) by = T.B[q / N][my];
+        else if (q < ND + 2 * N) by = T.B[(q - ND) % N][my];
+        else by = (q < ND + 3 * N || !(my & 1)) ? 1.0f : -1.0f;
+        s = fmaf(by, row, s);
+      }
+      return s;
+    };
+    constexpr int NPT = ND + 4 * N;
+    float rmin = Ub[0];
+#pragma unroll 1
+    for (int q = 0; q < NPT; ++q) rmin = fminf(rmin, value(0, q));
+    if (rmin < eps) th1 = fminf(1.0f, (Ub[0] - eps) / (Ub[0] - rmin));
+    auto pres = [&](const float* U) {
+      return (g - 1.0f) * (U[3] - 0.5f * (U[1] * U[1] + U[2] * U[2]) / U[0]);
+    };
+#pragma unroll 1
+    for (int q = 0; q < NPT; ++q) {
+      float Uq[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uq[v] = value(v, q);
+      Uq[0] = fmaf(th1, Uq[0] - Ub[0], Ub[0]);
+      if (!(pres(Uq) < eps)) continue;
+      float lo = 0.0f, hi = 1.0f;  // p(lo) >= eps > p(hi)
+#pragma unroll 1
+      for (int it = 0; it < 40; ++it) {
+        const float t = 0.5f * (lo + hi);
+        float Ut[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ut[v] = fmaf(t, Uq[v] - Ub[v], Ub[v]);
+        if (pres(Ut) >= eps) lo = t; else hi = t;
+      }
+      th2 = fminf(th2, lo);
+    }
+  } else {
+    atomicOr(a.status, kStatPositivity);
+  }
+#pragma unroll 1
+  for (int k = 0; k < NV * ND; ++k) {
+    const int v = k / ND, m = k - v * ND;
+    const float f = m == 0 ? 1.0f : (v == 0 ? th1 : 1.0f) * th2;
+    a.u_out[((int64_t)v * ncell + cell) * ND + m] = sc[k][threadIdx.x] * f;
+  }
+  if (theta_out) theta_out[cell] = th1 * th2;
+}
+
+template <int P>
+cudaError_t launch_positivity_p(const cvweno_mesh_s* m, const StageArgs& a, float* theta, cudaStream_t s) {
+  using Tb = DgTables<2, P>;
+  if (m->tables_bytes != sizeof(Tb)) return cudaErrorInvalidValue;
+  const int64_t ncell = (int64_t)a.nx * a.ny;
+  constexpr int nth = PosThreads<P>::value;
+  euler_positivity_kernel<P><<<(unsigned)((ncell + nth - 1) / nth), nth, 0, s>>>(a, *static_cast<const Tb*>(m->tables),
+                                                                                  theta);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s) {
@@ -659,6 +765,17 @@ cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaS
     case 2: return launch_euler<2, 16, 8>(m, a, s);
     case 3: return launch_euler<3, 16, 8>(m, a, s);
     case 4: return launch_euler<4, 8, 8>(m, a, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+cudaError_t launch_positivity(const cvweno_mesh_s* m, const StageArgs& a, float* theta, cudaStream_t s) {
+  if (m->dim != 2 || m->desc.system != CVWENO_EULER || m->kind != CVWENO_DG) return cudaErrorNotSupported;
+  switch (m->p) {
+    case 1: return launch_positivity_p<1>(m, a, theta, s);
+    case 2: return launch_positivity_p<2>(m, a, theta, s);
+    case 3: return launch_positivity_p<3>(m, a, theta, s);
+    case 4: return launch_positivity_p<4>(m, a, theta, s);
     default: return cudaErrorNotSupported;
   }
 }

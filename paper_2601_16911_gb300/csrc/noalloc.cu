@@ -253,7 +253,7 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   if (!(p.eps > 0.0) || !(p.q >= 1.0) || !(p.gamma_vertex > 0.0) || (1 << d->dim) * p.gamma_vertex >= 1.0)
     return CVWENO_ERR_ARG;
   if (p.sensor_mode < 0 || p.sensor_mode > 2) return CVWENO_ERR_ARG;
-  if (p.hweno_limiter) return CVWENO_ERR_UNSUPPORTED;  // the limited step needs a third buffer
+  if (p.hweno_limiter || p.positivity) return CVWENO_ERR_UNSUPPORTED;  // limited steps are not in this variant
   if (d->kind != CVWENO_DG || d->degree < 1 || d->degree > kMaxP) return CVWENO_ERR_UNSUPPORTED;
   if (p.r != floor(p.r) || p.r < 1.0 || p.r > 8.0) return CVWENO_ERR_UNSUPPORTED;
   if ((d->system == CVWENO_KPP || d->system == CVWENO_EULER) && d->dim != 2) return CVWENO_ERR_UNSUPPORTED;

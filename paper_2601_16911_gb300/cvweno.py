@@ -40,7 +40,7 @@ class cvweno_params(ctypes.Structure):
         ("sc_quadrature", ctypes.c_int), ("sensor_mode", ctypes.c_int),
         ("lambda_const", ctypes.c_double), ("gas_gamma", ctypes.c_double),
         ("adv_vx", ctypes.c_double), ("adv_vy", ctypes.c_double),
-        ("hweno_limiter", ctypes.c_int),
+        ("hweno_limiter", ctypes.c_int), ("positivity", ctypes.c_int),
     ]
 
 
@@ -89,6 +89,7 @@ _SIGNATURES = {
     "cvweno_step_static": (ctypes.c_int, [ctypes.POINTER(cvweno_mesh_desc), _VP, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_int32), _VP]),
     "cvweno_limit": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "cvweno_positivity": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "cvweno_mesh_set_kernel_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cvweno_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _IP]),
     "cvweno_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_VP)]),
@@ -291,6 +292,13 @@ class Mesh:
         _check(load().cvweno_max_wavespeed(self._h, _ptr(u), ctypes.byref(lam), _stream(stream)),
                "cvweno_max_wavespeed")
         return lam.value
+
+    def positivity(self, u, out=None, stream=None):
+        """Positivity limiter (Euler): (limited state, theta per cell)."""
+        out = torch.empty_like(u) if out is None else out
+        th = torch.empty(self.ncells, dtype=torch.float32, device=u.device)
+        _check(load().cvweno_positivity(self._h, _ptr(u), _ptr(out), _ptr(th), _stream(stream)), "cvweno_positivity")
+        return out, th
 
     def limit(self, u, all_cells: bool = False, out=None, stream=None):
         """HWENO limiter (Sec. 3): (limited state, int32 flags of the limited cells)."""
@@ -646,3 +654,8 @@ def cvweno_mesh_set_surrogate(mesh: Mesh, net, conf_min: float = 0.5):
 
 def cvweno_mlp_fallbacks(net: Mlp, reset: bool = False, stream=None) -> int:
     return net.fallbacks(reset, stream)
+
+
+def cvweno_positivity(mesh: Mesh, u, out, theta=None, stream=None):
+    _check(load().cvweno_positivity(mesh.handle, _ptr(u), _ptr(out), _ptr(theta), _stream(stream)),
+           "cvweno_positivity")
