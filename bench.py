@@ -38,6 +38,8 @@ WORKLOAD = ("KPP 2D, f=(sin u, cos u), [-2,2]^2 periodic, 256x256 quads, DG and 
             "(one SSP-RK3 step each), FP32")
 SEED = 0
 SURROGATE_P = 2  # degree of the surrogate workload (--surrogate-degree)
+# --impl reference: mesh size of the bounded sample each reference step runs (None: full)
+REFERENCE_SAMPLE_N = {"kpp": 16, "euler": 16, "burgers1d": None, "batched": 16, "surrogate": 16}
 
 
 def problems(workload: str, n_scale: int | None = None):
@@ -98,6 +100,25 @@ WORKLOADS = {
 DOMINANT = {"kpp": ("CG-Q3", "cg_stage_cells<2,3,KPP,16,8>", 0, 6),
             "euler": ("DG-Q3", "dg_euler_stage<3,16,8>", 0, 1),
             "burgers1d": ("DG-P2", "dg_scalar_stage<1,2,BURGERS,128,1>", 0, 1)}
+
+
+def max_over_ranks(t_local: float, device) -> float:
+    """The slowest rank's time (a MAX all-reduce; the identity on one process).  device:
+    where the reduction tensor lives (the rank's GPU under NCCL, the CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local
+    t = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_step: int, steps: int, world_size: int, t_max: float) -> float:
+    """Whole-job throughput: every rank advances the same workload (replicas, weak
+    scaling), so the job processed world_size x the units of one rank in the slowest
+    rank's time."""
+    return units_per_step * steps * world_size / t_max
 
 
 def dist_env():
@@ -251,7 +272,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     work = [(d, O.project(d, *ic).astype(np.float32).astype(np.float64), dt)
-            for _, d, ic, dt in problems(args.workload, 32 if args.workload != "burgers1d" else None)]
+            for _, d, ic, dt in problems(args.workload, REFERENCE_SAMPLE_N.get(args.workload))]
     units = sum(3 * int(np.prod(O.state_shape(d))) for d, _, _ in work)
 
     def step():
@@ -265,8 +286,9 @@ def run_reference(args):
         step()
     dt = time.perf_counter() - t0
     value = units * args.steps / dt
+    nsamp = REFERENCE_SAMPLE_N.get(args.workload)
     sample = ("one SSP-RK3 step of every discretisation of the workload per benchmark step"
-              + (", at 32x32 cells" if args.workload != "burgers1d" else ""))
+              + (f", at {nsamp}x{nsamp} cells" if nsamp else ""))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -447,13 +469,8 @@ def run_gpu(args):
     per_degree = [[events[i][k].elapsed_time(events[i][k + 1]) for i in range(args.steps)] for k in range(len(graphs))]
     step_ms = sum(sum(x) for x in per_degree) / args.steps
     t_local = step_ms * args.steps / 1000.0
-    if ws > 1:
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = units_per_step * args.steps * ws / t_max
+    t_max = max_over_ranks(t_local, dev)
+    value = whole_job_value(units_per_step, args.steps, ws, t_max)
 
     # ---- end to end through the public API: pinned host -> device, step, device -> host ----
     host_in = [u0.cpu().pin_memory() for u0 in inits]
@@ -623,13 +640,8 @@ def run_gpu_batched(args, ws, rank, local, dev):
         m.status_check()
     step_ms = statistics.mean(ms_b)
     t_local = sum(ms_b) / 1000.0
-    if ws > 1:
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = units_per_step * args.steps * ws / t_max
+    t_max = max_over_ranks(t_local, dev)
+    value = whole_job_value(units_per_step, args.steps, ws, t_max)
     plain_value = units_per_step / (statistics.mean(ms_p) / 1000.0)
 
     # end to end: pinned host state in, one batched step, state out
