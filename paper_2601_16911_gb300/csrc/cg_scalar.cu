@@ -74,10 +74,11 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
       const int ix = f % NNX, iy = f / NNX;
       const int I = ((I0 + ix) % nnx + nnx) % nnx;
       const int J = DIM == 2 ? ((J0 + iy) % nny + nny) % nny : 0;
-      snode[f] = __ldg(a.u_in + (size_t)J * nnx + I);
+      cp_async4(snode + f, a.u_in + (size_t)J * nnx + I, 4);
     }
   }
   stage_tables_to_smem<DIM, P, TX, TY>(T, smem);
+  cp_async_wait_all();
   __syncthreads();
   // ---- every halo cell: nodal -> Legendre modes c = (V x V) u_loc -------------------------
   // The transform is applied to u_loc - u_ref (u_ref = the cell's first node): every mode
@@ -238,19 +239,30 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
 #pragma unroll
           for (int j = 0; j < N; ++j) v = fmaf(T.B[q][j], tr[f][j], v);
         }
-        lam = fmaxf(lam, law.speed(v));
+      lam = fmaxf(lam, law.speed(v));
       }
     }
+    // volume nodes, by sum factorisation
 #pragma unroll 1
-    for (int q = 0; q < ND; ++q) {
-      const int qx = q % N, qy = DIM == 2 ? q / N : 0;
-      float u = 0.0f;
+    for (int qx = 0; qx < N; ++qx) {
+      float tb[NY1];
 #pragma unroll
-      for (int m = 0; m < ND; ++m) {
-        const int mx = m % N, my = DIM == 2 ? m / N : 0;
-        u = fmaf(sB[qx * N + mx] * (DIM == 2 ? sB[qy * N + my] : 1.0f), c[m], u);
+      for (int my = 0; my < NY1; ++my) {
+        float s0 = 0.0f;
+#pragma unroll
+        for (int mx = 0; mx < N; ++mx) s0 = fmaf(sB[qx * N + mx], c[mx + N * my], s0);
+        tb[my] = s0;
       }
-      lam = fmaxf(lam, law.speed(u));
+#pragma unroll
+      for (int qy = 0; qy < NY1; ++qy) {
+        float u = tb[0];
+        if constexpr (DIM == 2) {
+          u = 0.0f;
+#pragma unroll
+          for (int my = 0; my < N; ++my) u = fmaf(sB[qy * N + my], tb[my], u);
+        }
+        lam = fmaxf(lam, law.speed(u));
+      }
     }
   }
   const float nu = lam * a.nu_scale;
@@ -287,55 +299,102 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
       phy[aa + N * bb] = sy / ml;
     }
 
-  // (d) SC weights (A24) and (e) local residual over the volume Gauss nodes
+  // (d) SC weights (A24) and (e) local residual over the volume Gauss nodes, by sum
+  // factorisation: per row qx the x-contractions of c (values, x-derivatives) and of the
+  // nodal P_h grad u, then the nodes of the row; the residual is projected back the same way
   bool troubled = a.sc && gam < a.c_gamma && n0 > 1e-30f;
   if (a.troubled_override) {
     const int ov = a.troubled_override[cell];
     if (ov >= 0) troubled = ov && n0 > 1e-30f;
   }
   float afac = -1.0f;
-  // per node values: u, physical gradient, P_h grad u
-  auto point = [&](int qx, int qy, float& u, float& gx, float& gy, float& px, float& py) {
-    u = gx = gy = px = py = 0.0f;
+  const bool need_sc = troubled && gam < 1.0f;
+  // x-contractions of row qx: tb = B c, td = Bd c (modes), tpx/tpy = Lq ph (nodal)
+  auto row = [&](int qx, float (&tb)[NY1], float (&td)[NY1], float (&tpx)[NY1], float (&tpy)[NY1]) {
 #pragma unroll
-    for (int m = 0; m < ND; ++m) {
-      const int mx = m % N, my = DIM == 2 ? m / N : 0;
-      const float bx_ = sB[qx * N + mx], by_ = DIM == 2 ? sB[qy * N + my] : 1.0f;
-      u = fmaf(bx_ * by_, c[m], u);
-      gx = fmaf(sBd[qx * N + mx] * by_, c[m], gx);
-      if constexpr (DIM == 2) gy = fmaf(bx_ * sBd[qy * N + my], c[m], gy);
-      const float lx = (&C.Lq[0][0])[qx * N + mx], ly = DIM == 2 ? (&C.Lq[0][0])[qy * N + my] : 1.0f;
-      px = fmaf(lx * ly, phx[m], px);
-      py = fmaf(lx * ly, phy[m], py);
+    for (int my = 0; my < NY1; ++my) {
+      float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+      for (int mx = 0; mx < N; ++mx) {
+        const float cm = c[mx + N * my];
+        s0 = fmaf(sB[qx * N + mx], cm, s0);
+        s1 = fmaf(sBd[qx * N + mx], cm, s1);
+        const float lx = (&C.Lq[0][0])[qx * N + mx];
+        s2 = fmaf(lx, phx[mx + N * my], s2);
+        s3 = fmaf(lx, phy[mx + N * my], s3);
+      }
+      tb[my] = s0;
+      td[my] = s1;
+      tpx[my] = s2;
+      tpy[my] = s3;
     }
-    gx *= a.two_dx;
-    gy *= a.two_dy;
   };
-  if (troubled && gam < 1.0f) {
+  // node (qx, qy) of the row: value, physical gradient, P_h grad u
+  auto node = [&](int qy, const float (&tb)[NY1], const float (&td)[NY1], const float (&tpx)[NY1],
+                  const float (&tpy)[NY1], float& u, float& gx, float& gy, float& px, float& py) {
+    if constexpr (DIM == 1) {
+      u = tb[0];
+      gx = td[0] * a.two_dx;
+      gy = 0.0f;
+      px = tpx[0];
+      py = 0.0f;
+    } else {
+      u = gx = gy = px = py = 0.0f;
+#pragma unroll
+      for (int my = 0; my < N; ++my) {
+        const float by = sB[qy * N + my], ly = (&C.Lq[0][0])[qy * N + my];
+        u = fmaf(by, tb[my], u);
+        gx = fmaf(by, td[my], gx);
+        gy = fmaf(sBd[qy * N + my], tb[my], gy);
+        px = fmaf(ly, tpx[my], px);
+        py = fmaf(ly, tpy[my], py);
+      }
+      gx *= a.two_dx;
+      gy *= a.two_dy;
+    }
+  };
+  if (need_sc) {
     float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll 1
-    for (int q = 0; q < ND; ++q) {
-      const int qx = q % N, qy = DIM == 2 ? q / N : 0;
-      float u, gx, gy, px, py;
-      point(qx, qy, u, gx, gy, px, py);
-      float n2 = 0.0f;
+    for (int qx = 0; qx < N; ++qx) {
+      float tb[NY1], td[NY1], tpx[NY1], tpy[NY1];
+      row(qx, tb, td, tpx, tpy);
+      float X[N][NY1];  // X[kx][my] = sum_mx Bk[kx][qx][mx] c[mx, my]
 #pragma unroll
-      for (int k = 1; k < ND; ++k) {
-        const int kx = k % N, ky = DIM == 2 ? k / N : 0;
-        float dk = 0.0f;
+      for (int kx = 0; kx < N; ++kx)
 #pragma unroll
-        for (int m = 0; m < ND; ++m) {
-          const int mx = m % N, my = DIM == 2 ? m / N : 0;
-          dk = fmaf(sBk[(kx * N + qx) * N + mx] * (DIM == 2 ? sBk[(ky * N + qy) * N + my] : 1.0f), c[m], dk);
+        for (int my = 0; my < NY1; ++my) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int mx = 0; mx < N; ++mx) acc = fmaf(sBk[(kx * N + qx) * N + mx], c[mx + N * my], acc);
+          X[kx][my] = acc;
         }
-        n2 = fmaf(T.sigma[k] * dk, dk, n2);
+#pragma unroll 1
+      for (int qy = 0; qy < NY1; ++qy) {
+        float u, gx, gy, px, py;
+        node(qy, tb, td, tpx, tpy, u, gx, gy, px, py);
+        float n2 = 0.0f;
+#pragma unroll
+        for (int ky = 0; ky < NY1; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < N; ++kx) {
+            if (kx + ky == 0) continue;
+            float dk = X[kx][0];
+            if constexpr (DIM == 2) {
+              dk = 0.0f;
+#pragma unroll
+              for (int my = 0; my < N; ++my) dk = fmaf(sBk[(ky * N + qy) * N + my], X[kx][my], dk);
+            }
+            n2 = fmaf(T.sigma[kx + N * ky] * dk, dk, n2);
+          }
+        const float nq = sqrtf(n2);
+        const int q = qx + N * qy;
+        sNq[q * NT + threadIdx.x] = nq;
+        const float f = fmaf(gx, gx, gy * gy) - gam * (gx * px + gy * py);
+        const float W = sW[qx] * (DIM == 2 ? sW[qy] : 1.0f);
+        s1 = fmaf(W, f, s1);
+        s2 = fmaf(W * nq, f, s2);
       }
-      const float nq = sqrtf(n2);
-      sNq[q * NT + threadIdx.x] = nq;
-      const float f = fmaf(gx, gx, gy * gy) - gam * (gx * px + gy * py);
-      const float W = sW[qx] * (DIM == 2 ? sW[qy] : 1.0f);
-      s1 = fmaf(W, f, s1);
-      s2 = fmaf(W * nq, f, s2);
     }
     if (s1 > 0.0f && s2 > 0.0f) afac = s1 / s2;
   }
@@ -348,31 +407,45 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
 #pragma unroll
   for (int m = 0; m < ND; ++m) r[m] = 0.0f;
 #pragma unroll 1
-  for (int q = 0; q < ND; ++q) {
-    const int qx = q % N, qy = DIM == 2 ? q / N : 0;
-    float u, gx, gy, px, py;
-    point(qx, qy, u, gx, gy, px, py);
-    // f(u) - f(ubar): the cell constant f(ubar) contributes f(ubar) int_K grad phi_a,
-    // which lives on the cell's edges and telescopes between neighbours; cg_node_rhs adds
-    // it as differences f(ubar_R) - f(ubar_L) of neighbouring means
-    float fx, fy;
-    law.flux_dev(u - c[0], fx, fy);
-    const float al = afac >= 0.0f ? sNq[q * NT + threadIdx.x] * afac : 1.0f;
-    const float W = sW[qx] * (DIM == 2 ? sW[qy] : 1.0f) * hdx * hdy;
-    const float Gx = W * (fx - nu * al * (gx - gam * px));
-    const float Gy = W * (fy - nu * al * (gy - gam * py));
+  for (int qx = 0; qx < N; ++qx) {
+    float tb[NY1], td[NY1], tpx[NY1], tpy[NY1];
+    row(qx, tb, td, tpx, tpy);
+    float hx[NY1], hy[NY1];
 #pragma unroll
-    for (int m = 0; m < ND; ++m) {
-      const int mx = m % N, my = DIM == 2 ? m / N : 0;
-      const float lx = (&C.Lq[0][0])[qx * N + mx], dx_ = (&C.Ldq[0][0])[qx * N + mx];
+    for (int b = 0; b < NY1; ++b) hx[b] = hy[b] = 0.0f;
+#pragma unroll 1
+    for (int qy = 0; qy < NY1; ++qy) {
+      float u, gx, gy, px, py;
+      node(qy, tb, td, tpx, tpy, u, gx, gy, px, py);
+      // f(u) - f(ubar): the cell constant f(ubar) contributes f(ubar) int_K grad phi_a,
+      // which lives on the cell's edges and telescopes between neighbours; cg_node_rhs adds
+      // it as differences f(ubar_R) - f(ubar_L) of neighbouring means
+      float fx, fy;
+      law.flux_dev(u - c[0], fx, fy);
+      const int q = qx + N * qy;
+      const float al = afac >= 0.0f ? sNq[q * NT + threadIdx.x] * afac : 1.0f;
+      const float W = sW[qx] * (DIM == 2 ? sW[qy] : 1.0f) * hdx * hdy;
+      const float Gx = W * (fx - nu * al * (gx - gam * px));
+      const float Gy = W * (fy - nu * al * (gy - gam * py));
       if constexpr (DIM == 2) {
-        const float ly = (&C.Lq[0][0])[qy * N + my], dy_ = (&C.Ldq[0][0])[qy * N + my];
-        r[m] = fmaf(a.two_dx * dx_ * ly, Gx, r[m]);
-        r[m] = fmaf(a.two_dy * lx * dy_, Gy, r[m]);
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+          hx[b] = fmaf((&C.Lq[0][0])[qy * N + b], Gx, hx[b]);
+          hy[b] = fmaf((&C.Ldq[0][0])[qy * N + b], Gy, hy[b]);
+        }
       } else {
-        r[m] = fmaf(a.two_dx * dx_, Gx, r[m]);
+        hx[0] += Gx;
       }
     }
+    // r[a, b] += 2/dx Ldq[qx][a] hx[b] + 2/dy Lq[qx][a] hy[b]
+#pragma unroll
+    for (int b = 0; b < NY1; ++b)
+#pragma unroll
+      for (int aa = 0; aa < N; ++aa) {
+        float v = fmaf(a.two_dx * (&C.Ldq[0][0])[qx * N + aa], hx[b], r[aa + N * b]);
+        if constexpr (DIM == 2) v = fmaf(a.two_dy * (&C.Lq[0][0])[qx * N + aa], hy[b], v);
+        r[aa + N * b] = v;
+      }
   }
 #pragma unroll
   for (int m = 0; m < ND; ++m) a.rloc[cell * ND + m] = r[m];
