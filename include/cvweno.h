@@ -223,10 +223,10 @@ cvweno_status cvweno_positivity(cvweno_mesh m, const float* u, float* out, float
  * it launches; under stream capture the records become event-record nodes, so a graph
  * captured from such a step times each of its replays.  cvweno_kernel_times waits for
  * the last recorded event and writes the durations (ms) of the kernels of the most
- * recent step into ms[capacity] (host), in launch order: DG and Euler one per stage,
- * CG six per stage (cells, node right-hand side, then cell mass and node correction
- * twice); *count receives how many were written.  Timing costs one event record per
- * kernel; turn it off (enable 0) for production runs.  Turning it off keeps the events
+ * recent step into ms[capacity] (host), in launch order: DG and Euler one per stage
+ * (two with the HWENO or positivity limiter), CG four per stage (cells, node right-hand
+ * side, two defect-correction sweeps); *count receives how many were written.  Timing
+ * costs one event record per kernel; turn it off (enable 0) for production runs.  Turning it off keeps the events
  * of the last timed step (and of graphs captured while it was on) readable. */
 cvweno_status cvweno_mesh_set_kernel_timing(cvweno_mesh m, int enable);
 cvweno_status cvweno_kernel_times(cvweno_mesh m, float* ms, int capacity, int* count);

@@ -243,7 +243,7 @@ StageArgs base_args(const cvweno_mesh_s* m) {
   a.rloc = m->d_rloc;
   a.rnode = m->d_r;
   a.du = m->d_du;
-  a.mloc = m->d_mloc;
+  a.du2 = m->d_du2;
   a.ubar = m->d_ubar;
   return a;
 }
@@ -394,7 +394,7 @@ cvweno_status cvweno_mesh_destroy(cvweno_mesh m) {
   cudaFree(m->d_rloc);
   cudaFree(m->d_r);
   cudaFree(m->d_du);
-  cudaFree(m->d_mloc);
+  cudaFree(m->d_du2);
   cudaFree(m->d_ubar);
   cudaFree(m->d_cg_xg);
   cudaFree(m->d_cg_ml);
@@ -475,7 +475,7 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->d_lambda, sizeof(float) * (size_t)m->ncell);
   if (m->kind == CVWENO_CG) {
     if (e == cudaSuccess) e = cudaMalloc(&m->d_rloc, sizeof(float) * (size_t)m->ncell * m->nd);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_mloc, sizeof(float) * (size_t)m->ncell * m->nd);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_du2, sizeof(float) * (size_t)m->nnode);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_ubar, sizeof(float) * (size_t)m->ncell);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_r, sizeof(float) * (size_t)m->nnode);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_du, sizeof(float) * (size_t)m->nnode);

@@ -11,10 +11,10 @@
 //                       int grad phi . f(u) - nu_e sum_q alpha_q w_q grad phi . (grad u - gamma P_h grad u)
 //                       (Sec. 2.2, CG form of eq. stab)
 //   K2 cg_node_rhs      deterministic nodal assembly r_j and du = r_j / ML_j
-//   K3 cg_cell_mass     consistent mass times du, per cell
-//   K4 cg_node_correct  du += ML^{-1}(r - M_C du) (reading A12); the second sweep also
-//                       writes the SSP-RK3 combination (or du itself for a residual)
-// with K3/K4 run twice.  Nodal sums gather the cells around a node in a fixed order.
+//   K3 cg_node_sweep    du <- du + ML^{-1}(r - M_C du) (reading A12), node by node with
+//                       the tensor-product consistent mass; run twice, the second sweep
+//                       writing the SSP-RK3 combination (or du itself for a residual)
+// Nodal sums gather the cells around a node in a fixed order.
 #include "dg_scalar_kernel.cuh"
 
 namespace cvw {
@@ -523,53 +523,50 @@ __global__ void cg_node_rhs(const __grid_constant__ StageArgs a, const __grid_co
   }
 }
 
+// (M_C du) at lattice node (I, J): the consistent mass is the tensor product of the 1D
+// assembled masses, so the product is a sum over the (up to two) cells containing the
+// node in each direction of M1[local][b] times the nodes of that cell, x first, then y.
 template <int DIM, int P>
-__global__ void cg_cell_mass(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C) {
-  constexpr int N = P + 1, ND = DIM == 2 ? N * N : N;
-  const int64_t ncell = (int64_t)a.nx * (DIM == 2 ? a.ny : 1);
-  const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncell; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % a.nx), j = (int)(e / a.nx);
-    float x[ND];
+__device__ __forceinline__ float mass_apply(const CgTables<DIM, P>& C, const float* __restrict__ du, int I, int J,
+                                            int nnx, int nny, float hdx, float hdy) {
+  const int ax = I % P, ay = DIM == 2 ? J % P : 0;
+  const int ncx = ax == 0 ? 2 : 1, ncy = DIM == 2 ? (ay == 0 ? 2 : 1) : 1;
+  float acc = 0.0f;
+  for (int ky = 0; ky < ncy; ++ky) {
+    // y-cell starting at lattice row J0y, node's local index ly in it
+    const int ly = DIM == 2 ? (ay == 0 ? (ky == 0 ? P : 0) : ay) : 0;
+    const int J0y = J - ly;
 #pragma unroll
-    for (int m = 0; m < ND; ++m) {
-      const int aa = m % N, bb = DIM == 2 ? m / N : 0;
-      const int I = (P * i + aa) % a.nnx, J = DIM == 2 ? (P * j + bb) % a.nny : 0;
-      x[m] = a.du[(size_t)J * a.nnx + I];
-    }
-    float y[ND];
+    for (int d = 0; d < (DIM == 2 ? P + 1 : 1); ++d) {
+      const int Jr = DIM == 2 ? ((J0y + d) % nny + nny) % nny : 0;
+      const float* rowp = du + (size_t)Jr * nnx;
+      float w = 0.0f;
+      for (int kx = 0; kx < ncx; ++kx) {
+        const int lx = ax == 0 ? (kx == 0 ? P : 0) : ax;
+        const int I0x = I - lx;
 #pragma unroll
-    for (int m = 0; m < ND; ++m) {
-      const int aa = m % N, bb = DIM == 2 ? m / N : 0;
-      float acc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < ND; ++k) {
-        const int ka = k % N, kb = DIM == 2 ? k / N : 0;
-        acc = fmaf(C.M1[aa][ka] * (DIM == 2 ? C.M1[bb][kb] : 1.0f), x[k], acc);
+        for (int b = 0; b <= P; ++b) w = fmaf(C.M1[lx][b], rowp[((I0x + b) % nnx + nnx) % nnx], w);
       }
-      y[m] = acc * hdx * hdy;
+      acc = DIM == 2 ? fmaf(C.M1[ly][d], w, acc) : w;
     }
-#pragma unroll
-    for (int m = 0; m < ND; ++m) a.mloc[e * ND + m] = y[m];
   }
+  return acc * hdx * hdy;
 }
 
+// One defect-correction sweep du_out = du_in + ML^{-1}(r - M_C du_in) (reading A12), node
+// by node (1D meshes); the final sweep writes the SSP-RK3 combination (or du itself).
 template <int DIM, int P>
-__global__ void cg_node_correct(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C,
-                                int final_sweep) {
-  constexpr int ND = DIM == 2 ? (P + 1) * (P + 1) : P + 1;
+__global__ void cg_node_sweep(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C,
+                              const float* __restrict__ du_in, float* __restrict__ du_out, int final_sweep) {
   const int64_t nn = (int64_t)a.nnx * (DIM == 2 ? a.nny : 1);
   const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
     const int I = (int)(j % a.nnx), J = (int)(j / a.nnx);
-    int cells[4], locs[4];
-    const int n = node_cells<DIM, P>(I, J, a.nx, a.ny, cells, locs);
-    float mc = 0.0f;
-    for (int k = 0; k < n; ++k) mc += a.mloc[(size_t)cells[k] * ND + locs[k]];
+    const float mc = mass_apply<DIM, P>(C, du_in, I, J, a.nnx, DIM == 2 ? a.nny : 1, hdx, hdy);
     const float ml = ml1(C, I % P, hdx) * (DIM == 2 ? ml1(C, J % P, hdy) : 1.0f);
-    const float du = a.du[j] + (a.rnode[j] - mc) / ml;
+    const float du = du_in[j] + (a.rnode[j] - mc) / ml;
     if (!final_sweep) {
-      a.du[j] = du;
+      du_out[j] = du;
     } else if (a.mode & kModeRK) {
       float v = fmaf(a.dt, du, a.u_in[j]);
       if (a.rk_a != 0.0f) v = fmaf(a.rk_b, v - a.u_n[j], a.u_n[j]);  // plain load: u_n may alias u_out
@@ -579,6 +576,72 @@ __global__ void cg_node_correct(const __grid_constant__ StageArgs a, const __gri
       a.u_out[j] = du;
       if (!isfinite(du)) atomicOr(a.status, kStatNonfinite);
     }
+  }
+}
+
+// One defect-correction sweep du_out = du_in + ML^{-1}(r - M_C du_in) (reading A12).  The
+// consistent mass is the tensor product of the 1D assembled masses, so M_C du is applied
+// as two passes over a tile of nodes held in shared memory with a halo of p nodes: along
+// x (each node sums M1[local][b] du over the nodes of the up to two cells containing it),
+// then along y.  The final sweep writes the SSP-RK3 combination (or du for a residual).
+constexpr int kSwX = 32, kSwY = 8;
+
+template <int P>
+__global__ void __launch_bounds__(kSwX* kSwY)
+    cg_node_sweep2d(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<2, P> C,
+                    const float* __restrict__ du_in, float* __restrict__ du_out, int final_sweep) {
+  constexpr int WX = kSwX + 2 * P, WY = kSwY + 2 * P, NT = kSwX * kSwY;
+  __shared__ float win[WY][WX];
+  __shared__ float wx[WY][kSwX];
+  const int nnx = a.nnx, nny = a.nny;
+  const int I0 = blockIdx.x * kSwX, J0 = blockIdx.y * kSwY;
+  for (int f = threadIdx.x; f < WX * WY; f += NT) {
+    const int r = f / WX, c = f - r * WX;
+    const int I = ((I0 - P + c) % nnx + nnx) % nnx, J = ((J0 - P + r) % nny + nny) % nny;
+    win[r][c] = du_in[(size_t)J * nnx + I];
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < WY * kSwX; f += NT) {
+    const int r = f / kSwX, x = f - r * kSwX;
+    const int ax = (I0 + x) % P;
+    float w = 0.0f;
+    const int lx0 = ax == 0 ? P : ax, s0 = P + x - lx0;
+#pragma unroll
+    for (int b = 0; b <= P; ++b) w = fmaf(C.M1[lx0][b], win[r][s0 + b], w);
+    if (ax == 0) {
+#pragma unroll
+      for (int b = 0; b <= P; ++b) w = fmaf(C.M1[0][b], win[r][P + x + b], w);
+    }
+    wx[r][x] = w;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kSwX, ty = threadIdx.x / kSwX;
+  const int I = I0 + tx, J = J0 + ty;
+  if (I >= nnx || J >= nny) return;
+  const int ay = J % P;
+  const int ly0 = ay == 0 ? P : ay, t0 = P + ty - ly0;
+  float mc = 0.0f;
+#pragma unroll
+  for (int d = 0; d <= P; ++d) mc = fmaf(C.M1[ly0][d], wx[t0 + d][tx], mc);
+  if (ay == 0) {
+#pragma unroll
+    for (int d = 0; d <= P; ++d) mc = fmaf(C.M1[0][d], wx[P + ty + d][tx], mc);
+  }
+  const float hdx = 1.0f / a.two_dx, hdy = 1.0f / a.two_dy;
+  mc *= hdx * hdy;
+  const size_t j = (size_t)J * nnx + I;
+  const float ml = ml1(C, I % P, hdx) * ml1(C, ay, hdy);
+  const float du = win[P + ty][P + tx] + (a.rnode[j] - mc) / ml;
+  if (!final_sweep) {
+    du_out[j] = du;
+  } else if (a.mode & kModeRK) {
+    float v = fmaf(a.dt, du, a.u_in[j]);
+    if (a.rk_a != 0.0f) v = fmaf(a.rk_b, v - a.u_n[j], a.u_n[j]);  // plain load: u_n may alias u_out
+    a.u_out[j] = v;
+    if (!isfinite(v)) atomicOr(a.status, kStatNonfinite);
+  } else {
+    a.u_out[j] = du;
+    if (!isfinite(du)) atomicOr(a.status, kStatNonfinite);
   }
 }
 
@@ -600,15 +663,20 @@ cudaError_t launch_cg_t(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t
   k1<<<grid, TX * TY, smem, s>>>(a, T, C);
   if (a.mode & kModeSensorOnly) return cudaGetLastError();
   kernel_mark(m, s);
-  const int64_t nn = m->nnode, nc = m->ncell;
+  const int64_t nn = m->nnode;
   const int bn = (int)((nn + 255) / 256 < 4096 ? (nn + 255) / 256 : 4096);
-  const int bc = (int)((nc + 255) / 256 < 4096 ? (nc + 255) / 256 : 4096);
   cg_node_rhs<DIM, P, SYS><<<bn, 256, 0, s>>>(a, C);
   kernel_mark(m, s);
-  for (int sweep = 0; sweep < 2; ++sweep) {
-    cg_cell_mass<DIM, P><<<bc, 256, 0, s>>>(a, C);
+  if constexpr (DIM == 2) {
+    const dim3 sg((a.nnx + kSwX - 1) / kSwX, (a.nny + kSwY - 1) / kSwY);
+    cg_node_sweep2d<P><<<sg, kSwX * kSwY, 0, s>>>(a, C, a.du, a.du2, 0);
     kernel_mark(m, s);
-    cg_node_correct<DIM, P><<<bn, 256, 0, s>>>(a, C, sweep == 1);
+    cg_node_sweep2d<P><<<sg, kSwX * kSwY, 0, s>>>(a, C, a.du2, nullptr, 1);
+    kernel_mark(m, s);
+  } else {
+    cg_node_sweep<DIM, P><<<bn, 256, 0, s>>>(a, C, a.du, a.du2, 0);
+    kernel_mark(m, s);
+    cg_node_sweep<DIM, P><<<bn, 256, 0, s>>>(a, C, a.du2, nullptr, 1);
     kernel_mark(m, s);
   }
   return cudaGetLastError();

@@ -105,7 +105,7 @@ struct StageArgs {
   float* rloc;  // [ncell][nd] cell-local residuals
   float* rnode; // [nnode] assembled residual
   float* du;    // [nnode] du/dt iterate
-  float* mloc;  // [ncell][nd] cell-local consistent-mass products
+  float* du2;   // [nnode] second defect-correction iterate
   float* ubar;  // [ncell] cell means (Legendre mode 0)
 };
 
@@ -142,7 +142,7 @@ struct cvweno_mesh_s {
   float* d_rloc;
   float* d_r;
   float* d_du;
-  float* d_mloc;
+  float* d_du2;
   float* d_ubar;
   double cg_xg[cvw::kMaxP + 1];  // GLL nodes (host, FP64)
   double cg_wl[cvw::kMaxP + 1];  // GLL weights (host, FP64)

@@ -9,7 +9,7 @@ from paper_2601_16911_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kind,per_stage", [(I.DG, 1), (I.CG, 6)])
+@pytest.mark.parametrize("kind,per_stage", [(I.DG, 1), (I.CG, 4)])
 def test_kernel_times_direct_and_in_graph(kind, per_stage):
     d, ic = I.kpp(0, n=64, degree=2, kind=kind)
     mesh = cv.Mesh(d)
