@@ -89,7 +89,7 @@ constexpr size_t batch_smem(int psel) {
 // kernel to the 255-register ceiling.
 template <int PSEL, int TX, int TY>
 constexpr int batch_min_ctas() {
-  return (PSEL == 0 || PSEL == 4 ? 3 : PSEL == 3 ? 4 : PSEL == 2 ? 5 : 8) * (128 / (TX * TY));
+  return (PSEL == 0 || PSEL == 4 ? 3 : PSEL == 3 ? 4 : PSEL == 2 ? 6 : 8) * (128 / (TX * TY));
 }
 
 template <int PSEL, int SYS, int TX, int TY>
