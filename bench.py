@@ -214,11 +214,15 @@ def fma_per_cell_euler(p: int, troubled_fraction: float) -> float:
 def fma_per_cell_cg_cells(p: int, troubled_fraction: float) -> float:
     """The CG cell kernel: the DG count of stages (a)-(e) without faces' extra terms,
     plus the nodal -> modal map of the tile and halo cells (2n^3 each; 180 halo cells per
-    128-cell tile), the local integrals int phi grad u of the same cells (8n^3 each), and
-    P_h grad u at the cell's Gauss points (4n^3) and nodes (8n^2)."""
+    128-cell tile), the local integrals int phi grad u of the tile's cells (4n^3 each, by
+    tensor factors) and of the 52 halo-ring cells on the node row or column they share
+    with the tile (4n^2 each), and P_h grad u at the cell's Gauss points (4n^3) and nodes
+    (8n^2)."""
     n = p + 1
     halo = 180.0 / 128.0
-    return fma_per_cell(p, troubled_fraction) + halo * (2 * n**3 + 8 * n**3) + 4 * n**3 + 8 * n**2
+    ring = 52.0 / 128.0
+    return (fma_per_cell(p, troubled_fraction) + halo * 2 * n**3 + 4 * n**3 + ring * 4 * n**2 + 4 * n**3
+            + 8 * n**2)
 
 
 def bytes_per_dof_stage() -> float:

@@ -359,9 +359,10 @@ cvweno_status cvweno_mlp_fallbacks(cvweno_mlp n, uint64_t* count, int reset, voi
  * state layout of desc), that allocates nothing -- for callers that cannot allocate
  * device or host memory (a library running inside an arena or memory pool it does not
  * own, or an embedding that forbids cudaMalloc after start-up).  It needs no mesh
- * handle: the tabulations are built on the host stack, and the two RK stage buffers and
- * the status word live in file-scope __device__ storage that the library holds on every
- * GPU that loads it until the process exits (2 x 4,194,304 floats = 32 MiB).
+ * handle: the tabulations are built on the host stack, and the two RK stage buffers, the
+ * status word and the device copy of the tabulations live in file-scope __device__
+ * storage that the library holds on every GPU that loads it until the process exits
+ * (2 x 4,194,304 floats = 32 MiB, plus under 10 KiB).
  * The paper has no counterpart; this is a deployment variant of cvweno_step.
  *   - States larger than 4,194,304 floats (ncells x (p+1)^dim x nvars) return
  *     CVWENO_ERR_ARG; other argument checks and codes are those of cvweno_mesh_create.

@@ -222,6 +222,7 @@ StageArgs base_args(const cvweno_mesh_s* m) {
   a.two_dy = (float)(2.0 / m->dy);
   a.nu_scale = (float)(m->h / (2.0 * m->p));
   a.h_e = (float)m->h;
+  a.tab_img = m->d_tabimg;
   a.mlp = m->surrogate;
   a.mlp_conf_min = m->surrogate_conf_min;
   a.mlp_fallbacks = m->surrogate_fallbacks;
@@ -398,6 +399,7 @@ cvweno_status cvweno_mesh_destroy(cvweno_mesh m) {
   cudaFree(m->d_ubar);
   cudaFree(m->d_cg_xg);
   cudaFree(m->d_cg_ml);
+  cudaFree(m->d_tabimg);
   cudaFreeHost(m->h_status);
   cudaFreeHost(m->h_red);
   for (int i = 0; i < kMaxMarks; ++i)
@@ -473,6 +475,9 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->d_u1, sbytes);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_u2, sbytes);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_lambda, sizeof(float) * (size_t)m->ncell);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_tabimg, sizeof(float) * (size_t)tab_image_floats(m->dim, m->p));
+  if (e == cudaSuccess) e = launch_tab_image(m->dim, m->p, m->tables, m->d_tabimg, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (m->kind == CVWENO_CG) {
     if (e == cudaSuccess) e = cudaMalloc(&m->d_rloc, sizeof(float) * (size_t)m->ncell * m->nd);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_du2, sizeof(float) * (size_t)m->nnode);

@@ -63,7 +63,7 @@ __device__ __forceinline__ void batch_tile(const StageArgs& a, const TT& T, cons
   // a new degree needs its tabulations in shared memory; the previous tile's readers
   // have passed the barrier that ends it, and the tile's first barrier publishes them
   if (cur_p != P) {
-    stage_tables_to_smem<2, P, TX, TY>(t, smem);
+    stage_tables_to_smem<2, P, TX, TY>(a.tab_img, smem);
     cur_p = P;
   }
   scalar_tile<2, P, SYS, TX, TY>(a, t, bt.i0, bt.j0, smem);

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
       cp_async4(snode + f, a.u_in + (size_t)J * nnx + I, 4);
     }
   }
-  stage_tables_to_smem<DIM, P, TX, TY>(T, smem);
+  stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);
   cp_async_wait_all();
   __syncthreads();
   // ---- every halo cell: nodal -> Legendre modes c = (V x V) u_loc -------------------------
@@ -120,67 +120,113 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   __syncthreads();
   // ---- (a)+(b) vertex candidates (shared with DG) ---------------------------------------
   tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
-  // ---- P_h local integrals b_a = int phi_a grad u for every halo cell ------------------------
-  for (int h = threadIdx.x; h < NH; h += NT) {
-    float c[ND];
-#pragma unroll
-    for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + h];
-    float bx[ND], by[ND];
-#pragma unroll
-    for (int m = 0; m < ND; ++m) bx[m] = by[m] = 0.0f;
-#pragma unroll 1
-    for (int qx = 0; qx < N; ++qx) {
-      float tb[NY1], td[NY1];
-#pragma unroll
-      for (int my = 0; my < NY1; ++my) {
-        float s0 = 0.0f, sd = 0.0f;
-#pragma unroll
-        for (int mx = 0; mx < N; ++mx) {
-          s0 = fmaf(sB[qx * N + mx], c[mx + N * my], s0);
-          sd = fmaf(sBd[qx * N + mx], c[mx + N * my], sd);
-        }
-        tb[my] = s0;
-        td[my] = sd;
-      }
-      float hx_[NY1], hy_[NY1];
-#pragma unroll
-      for (int b = 0; b < NY1; ++b) hx_[b] = hy_[b] = 0.0f;
-#pragma unroll
-      for (int qy = 0; qy < NY1; ++qy) {
-        float gx = td[0], gy = 0.0f;
-        if constexpr (DIM == 2) {
-          gx = 0.0f;
-#pragma unroll
-          for (int my = 0; my < N; ++my) {
-            gx = fmaf(T.B[qy][my], td[my], gx);
-            gy = fmaf(T.Bd[qy][my], tb[my], gy);
-          }
-        }
-        const float W = sW[qx] * (DIM == 2 ? T.w[qy] : 1.0f) * hdx * hdy;
-        gx *= a.two_dx * W;
-        gy *= a.two_dy * W;
-#pragma unroll
-        for (int b = 0; b < NY1; ++b) {
-          const float lb = DIM == 2 ? C.Lq[qy][b] : 1.0f;
-          hx_[b] = fmaf(lb, gx, hx_[b]);
-          hy_[b] = fmaf(lb, gy, hy_[b]);
-        }
-      }
-      // accumulate with the run-time row qx
+  // ---- P_h local integrals b_a = int phi_a grad u (reading A13) ------------------------------
+  // For u = sum_m c_m P_mx P_my on the cell, with dx dy / 4 = hdx hdy and the factor 2/dx
+  // of d/dx cancelling hdx (Em, Dm: integrals of l_a against P_m and P_m'):
+  //   bx[a,b] = hdy sum_{mx,my} Dm[a][mx] Em[b][my] c[mx,my]
+  //   by[a,b] = hdx sum_{mx,my} Em[a][mx] Dm[b][my] c[mx,my]
+  // A tile cell takes every entry; a halo cell only those of its nodes on the tile's
+  // boundary, the ones that the tile's nodes gather (one row or column of nodes).
+  if constexpr (DIM == 1) {
+    for (int h = threadIdx.x; h < NH; h += NT) {
 #pragma unroll
       for (int aa = 0; aa < N; ++aa) {
-        const float la = (&C.Lq[0][0])[qx * N + aa];
+        float acc = 0.0f;
 #pragma unroll
-        for (int b = 0; b < NY1; ++b) {
-          bx[aa + N * b] = fmaf(la, hx_[b], bx[aa + N * b]);
-          by[aa + N * b] = fmaf(la, hy_[b], by[aa + N * b]);
-        }
+        for (int m = 0; m < N; ++m) acc = fmaf(C.Dm[aa][m], sc[m * NH + h], acc);
+        sbx[aa * NH + h] = acc;
+        sby[aa * NH + h] = 0.0f;
       }
     }
+  } else {
+    constexpr int HY = L::HY;
+    {
+      const int h = (threadIdx.x / TX + 1) * HX + threadIdx.x % TX + 1;
+      float c[ND];
 #pragma unroll
-    for (int m = 0; m < ND; ++m) {
-      sbx[m * NH + h] = bx[m];
-      sby[m * NH + h] = by[m];
+      for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + h];
+      float tE[N][N], tD[N][N];  // [b][mx]: the y-contractions
+#pragma unroll
+      for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int mx = 0; mx < N; ++mx) {
+          float e = 0.0f, d = 0.0f;
+#pragma unroll
+          for (int my = 0; my < N; ++my) {
+            e = fmaf(C.Em[b][my], c[mx + N * my], e);
+            d = fmaf(C.Dm[b][my], c[mx + N * my], d);
+          }
+          tE[b][mx] = e;
+          tD[b][mx] = d;
+        }
+#pragma unroll
+      for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int aa = 0; aa < N; ++aa) {
+          float bx = 0.0f, by = 0.0f;
+#pragma unroll
+          for (int mx = 0; mx < N; ++mx) {
+            bx = fmaf(C.Dm[aa][mx], tE[b][mx], bx);
+            by = fmaf(C.Em[aa][mx], tD[b][mx], by);
+          }
+          sbx[(aa + N * b) * NH + h] = hdy * bx;
+          sby[(aa + N * b) * NH + h] = hdx * by;
+        }
+    }
+    // halo ring: the bottom and top rows (corners included) need the node row b = l that
+    // faces the tile (l = P below it, 0 above), the left and right columns the node
+    // column a = l (P left of it, 0 right)
+    constexpr int NR = 2 * HX + 2 * TY;
+    for (int r = threadIdx.x; r < NR; r += NT) {
+      const bool row = r < 2 * HX;
+      int hx, hy, l;
+      if (row) {
+        const bool top = r >= HX;
+        hx = top ? r - HX : r;
+        hy = top ? HY - 1 : 0;
+        l = top ? 0 : P;
+      } else {
+        const int rr = r - 2 * HX;
+        const bool right = rr >= TY;
+        hx = right ? HX - 1 : 0;
+        hy = 1 + (right ? rr - TY : rr);
+        l = right ? 0 : P;
+      }
+      const int h = hy * HX + hx;
+      float c[ND];
+#pragma unroll
+      for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + h];
+      // s1: the contraction along the fixed direction with Em (row) or Dm (column) of
+      // node l; s2 with the other table
+      float s1[N], s2[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        float e = 0.0f, d = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const float cv = row ? c[k + N * j] : c[j + N * k];  // row: k = mx, j = my
+          const float t1 = row ? (l ? C.Em[P][j] : C.Em[0][j]) : (l ? C.Dm[P][j] : C.Dm[0][j]);
+          const float t2 = row ? (l ? C.Dm[P][j] : C.Dm[0][j]) : (l ? C.Em[P][j] : C.Em[0][j]);
+          e = fmaf(t1, cv, e);
+          d = fmaf(t2, cv, d);
+        }
+        s1[k] = e;
+        s2[k] = d;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float bx = 0.0f, by = 0.0f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          // row: bx[i,l] = sum_mx Dm[i][mx] s1[mx], by[i,l] = sum_mx Em[i][mx] s2[mx]
+          // column: bx[l,i] = sum_my Em[i][my] s1[my], by[l,i] = sum_my Dm[i][my] s2[my]
+          bx = fmaf(row ? C.Dm[i][k] : C.Em[i][k], s1[k], bx);
+          by = fmaf(row ? C.Em[i][k] : C.Dm[i][k], s2[k], by);
+        }
+        const int lm = row ? i + N * l : l + N * i;
+        sbx[lm * NH + h] = hdy * bx;
+        sby[lm * NH + h] = hdx * by;
+      }
     }
   }
   __syncthreads();
@@ -294,9 +340,10 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
           sx += sbx[lm * NH + hh];
           sy += sby[lm * NH + hh];
         }
-      const float ml = ml1(C, aa == P ? 0 : aa, hdx) * (DIM == 2 ? ml1(C, bb == P ? 0 : bb, hdy) : 1.0f);
-      phx[aa + N * bb] = sx / ml;
-      phy[aa + N * bb] = sy / ml;
+      // 1 / ML of the node: the inverse lumped masses of its two 1D indices
+      const float iml = C.iml[aa == P ? 0 : aa] * a.two_dx * (DIM == 2 ? C.iml[bb == P ? 0 : bb] * a.two_dy : 1.0f);
+      phx[aa + N * bb] = sx * iml;
+      phy[aa + N * bb] = sy * iml;
     }
 
   // (d) SC weights (A24) and (e) local residual over the volume Gauss nodes, by sum

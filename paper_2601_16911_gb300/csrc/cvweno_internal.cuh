@@ -16,7 +16,8 @@ enum : int { kStatNonfinite = 1, kStatPositivity = 2 };
 
 // Reference-cell tabulations of one (dim, p) pair, FP64 on the host rounded once to
 // FP32, passed to the kernels by value (__grid_constant__), so that every warp reads
-// them through the constant bank with uniform addresses.
+// them through the constant bank with uniform addresses (the entries read with per-lane
+// indices come from TabImage instead).
 //   E[k][m]     = P_m^(k)(+1); the value at -1 is (-1)^(m+k) E[k][m]
 //   B[q][m]     = P_m(xi_q), Bd[q][m] = P_m'(xi_q) at the n Gauss-Legendre nodes xi_q
 //   Bk[k][q][m] = P_m^(k)(xi_q) (pointwise semi-norm at quadrature nodes, stage d)
@@ -45,11 +46,47 @@ struct DgTables {
   float A[NC][NS][NS];
 };
 
+// Device image of the tabulations that the stage kernels index with a different value in
+// every lane (A padded to NSP columns, B, Bd, Bk, w), in the order they take in shared
+// memory: a tile stages it with 16-byte copies from global memory, where reading the
+// by-value tables with per-lane indices would serialise in the constant bank.  Built on
+// the device from DgTables by launch_tab_image (once per mesh).
+template <int DIM, int P>
+struct TabImage {
+  using Tb = DgTables<DIM, P>;
+  static constexpr int N = P + 1, NS = Tb::NS, NC = Tb::NC;
+  static constexpr int NSP = (NS + 3) / 4 * 4;
+  static constexpr int A = 0;                  // [NC][NS][NSP], columns >= NS zero
+  static constexpr int B = A + NC * NS * NSP;  // [N][N]
+  static constexpr int BD = B + N * N;         // [N][N]
+  static constexpr int BK = BD + N * N;        // [N][N][N]
+  static constexpr int W = BK + N * N * N;     // [N]
+  static constexpr int FLOATS = (W + N + 3) / 4 * 4;  // whole 16-byte chunks
+};
+constexpr int kMaxTabImage = TabImage<2, kMaxP>::FLOATS;
+inline int tab_image_floats(int dim, int p) {
+  switch (dim * 10 + p) {
+    case 11: return TabImage<1, 1>::FLOATS;
+    case 12: return TabImage<1, 2>::FLOATS;
+    case 13: return TabImage<1, 3>::FLOATS;
+    case 14: return TabImage<1, 4>::FLOATS;
+    case 21: return TabImage<2, 1>::FLOATS;
+    case 22: return TabImage<2, 2>::FLOATS;
+    case 23: return TabImage<2, 3>::FLOATS;
+    case 24: return TabImage<2, 4>::FLOATS;
+    default: return 0;
+  }
+}
+
 // CG tabulations (Gauss-Lobatto-Legendre nodal basis l_a on [-1,1]):
 //   V[m][a]   Legendre mode m of l_a: (2m+1)/2 int P_m l_a      (nodal -> modal)
 //   Lq[q][a]  l_a(xi_q) and Ldq[q][a] = l_a'(xi_q) at the Gauss nodes
 //   M1[a][b]  int l_a l_b (1D reference mass), wl[a] = int l_a (GLL weight)
 //   xg[a]     GLL nodes
+//   Em[a][m]  int l_a P_m and Dm[a][m] = int l_a P_m' (local integrals of a Legendre
+//             expansion against the nodal basis)
+//   iml[a]    1 / (m_a wl[a]), m_a = 2 for the vertex node a = 0 (shared by two cells
+//             along the line), else 1: the inverse 1D lumped mass of local node a
 template <int DIM, int P>
 struct CgTables {
   static constexpr int N = P + 1;
@@ -57,7 +94,10 @@ struct CgTables {
   float Lq[N][N];
   float Ldq[N][N];
   float M1[N][N];
+  float Em[N][N];
+  float Dm[N][N];
   float wl[N];
+  float iml[N];
   float xg[N];
 };
 
@@ -98,6 +138,7 @@ struct StageArgs {
   float* feat_out;
   float* norm_out;     // kModeFeatures: ||u^e||_e per cell (may be null)
   float h_e;           // cell diameter
+  const float* tab_img;  // TabImage of the mesh's tabulations (device)
   float adv_vx, adv_vy;
   float gas_gamma;
   // CG only: nodal lattice and the per-stage work arrays
@@ -133,6 +174,7 @@ struct cvweno_mesh_s {
   // reference tabulations, one per (dim, p) -- only the matching one is filled
   void* tables;            // host copy of DgTables<dim, p>
   size_t tables_bytes;
+  float* d_tabimg;         // TabImage<dim, p> (device)
   // CG: nodal lattice, tabulations and stage work arrays
   int kind;
   int nnx, nny;
@@ -178,6 +220,9 @@ cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_
 cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 // dg_euler.cu: the positivity limiter on a.u_in -> a.u_out (may alias), theta per cell
 cudaError_t launch_positivity(const cvweno_mesh_s* m, const StageArgs& a, float* theta, cudaStream_t s);
+// dg_scalar_2d.cu: writes TabImage<dim, p> of the host tables t (DgTables<dim, p>) to
+// dst (device, tab_image_floats(dim, p) floats), stream-ordered on s
+cudaError_t launch_tab_image(int dim, int p, const void* t, float* dst, cudaStream_t s);
 // cg_scalar.cu
 cudaError_t launch_stage_cg(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 // api.cu: the stage arguments common to every launch on mesh m (no state pointers, no RK)

@@ -27,4 +27,27 @@ cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_
   }
 }
 
+namespace {
+template <int DIM, int P>
+cudaError_t tab_image(const void* t, float* dst, cudaStream_t s) {
+  tab_image_kernel<DIM, P><<<1, 256, 0, s>>>(*static_cast<const DgTables<DIM, P>*>(t), dst);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_tab_image(int dim, int p, const void* t, float* dst, cudaStream_t s) {
+  if (!t || !dst) return cudaErrorInvalidValue;
+  switch (dim * 10 + p) {
+    case 11: return tab_image<1, 1>(t, dst, s);
+    case 12: return tab_image<1, 2>(t, dst, s);
+    case 13: return tab_image<1, 3>(t, dst, s);
+    case 14: return tab_image<1, 4>(t, dst, s);
+    case 21: return tab_image<2, 1>(t, dst, s);
+    case 22: return tab_image<2, 2>(t, dst, s);
+    case 23: return tab_image<2, 3>(t, dst, s);
+    case 24: return tab_image<2, 4>(t, dst, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 }  // namespace cvw

@@ -204,18 +204,21 @@ template <int DIM, int P, int TX, int TY>
 struct TileLayout {
   using Tb = DgTables<DIM, P>;
   static constexpr int N = P + 1, ND = Tb::ND, NS = Tb::NS, NC = Tb::NC;
-  static constexpr int NSP = (NS + 3) / 4 * 4;
+  using Img = TabImage<DIM, P>;
+  static constexpr int NSP = Img::NSP;
   static constexpr int NT = TX * TY;
   static constexpr int HX = TX + 2, HY = DIM == 2 ? TY + 2 : 1, NH = HX * HY;
   static constexpr int VXT = TX + 1, VYT = DIM == 2 ? TY + 1 : 1, NVT = VXT * VYT;
   static constexpr int OFF_SC = 0;                                // [ND][NH]
   static constexpr int OFF_ST = OFF_SC + ND * NH;                 // [ND][NVT]
-  static constexpr int OFF_A = (OFF_ST + ND * NVT + 3) / 4 * 4;   // [NC][NS][NSP]
-  static constexpr int OFF_B = OFF_A + NC * NS * NSP;             // [N][N]  B[q][m]
-  static constexpr int OFF_BD = OFF_B + N * N;                    // [N][N]  Bd[q][m]
-  static constexpr int OFF_BK = OFF_BD + N * N;                   // [N][N][N] Bk[k][q][m]
-  static constexpr int OFF_W = OFF_BK + N * N * N;                // [N]
-  static constexpr int OFF_NQ = OFF_W + N;                        // [ND][NT] pointwise indicators
+  // the staged TabImage (16-byte aligned): A [NC][NS][NSP], B[q][m], Bd[q][m],
+  // Bk[k][q][m], w[q]
+  static constexpr int OFF_A = (OFF_ST + ND * NVT + 3) / 4 * 4;
+  static constexpr int OFF_B = OFF_A + Img::B;
+  static constexpr int OFF_BD = OFF_A + Img::BD;
+  static constexpr int OFF_BK = OFF_A + Img::BK;
+  static constexpr int OFF_W = OFF_A + Img::W;
+  static constexpr int OFF_NQ = OFF_A + Img::FLOATS;              // [ND][NT] pointwise indicators
   static constexpr int OFF_UN = OFF_NQ + ND * NT;                 // [ND][NT] u_n of the tile's cells
   static constexpr int FLOATS = OFF_UN + ND * NT;
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
@@ -303,22 +306,41 @@ __device__ __forceinline__ float cell_norm0(const DgTables<DIM, P>& T, const flo
   return sqrtf(n2);
 }
 
-// Copies the tabulations read with run-time indices into shared memory.
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+
+// Starts the copy of the tabulation image img (device, TabImage<DIM, P>) into shared
+// memory; it lands with the tile's first cp.async wait.
 template <int DIM, int P, int TX, int TY>
-__device__ __forceinline__ void stage_tables_to_smem(const DgTables<DIM, P>& T, float* smem) {
+__device__ __forceinline__ void stage_tables_to_smem(const float* img, float* smem) {
   using L = TileLayout<DIM, P, TX, TY>;
-  constexpr int N = L::N, NS = L::NS, NC = L::NC, NSP = L::NSP, NT = L::NT;
-  float* sA = smem + L::OFF_A;
-  for (int f = threadIdx.x; f < NC * NS * NSP; f += NT) {
-    int l = f / (NS * NSP), rem = f - l * (NS * NSP), i = rem / NSP, j = rem - i * NSP;
-    sA[f] = j < NS ? T.A[l][i][j] : 0.0f;
+  for (int f = threadIdx.x; f < TabImage<DIM, P>::FLOATS / 4; f += L::NT) cp_async16(smem + L::OFF_A + 4 * f, img + 4 * f);
+}
+
+// Writes TabImage<DIM, P> of T to img (one block; run once per mesh, off the stage path).
+template <int DIM, int P>
+__global__ void tab_image_kernel(const __grid_constant__ DgTables<DIM, P> T, float* __restrict__ img) {
+  using I = TabImage<DIM, P>;
+  constexpr int N = I::N, NS = I::NS, NSP = I::NSP;
+  for (int f = threadIdx.x; f < I::FLOATS; f += blockDim.x) {
+    float v = 0.0f;
+    if (f < I::B) {
+      const int l = f / (NS * NSP), rem = f - l * (NS * NSP), i = rem / NSP, j = rem - i * NSP;
+      v = j < NS ? T.A[l][i][j] : 0.0f;
+    } else if (f < I::BD) {
+      v = (&T.B[0][0])[f - I::B];
+    } else if (f < I::BK) {
+      v = (&T.Bd[0][0])[f - I::BD];
+    } else if (f < I::W) {
+      v = (&T.Bk[0][0][0])[f - I::BK];
+    } else if (f < I::W + N) {
+      v = T.w[f - I::W];
+    }
+    img[f] = v;
   }
-  for (int f = threadIdx.x; f < N * N; f += NT) {
-    smem[L::OFF_B + f] = (&T.B[0][0])[f];
-    smem[L::OFF_BD + f] = (&T.Bd[0][0])[f];
-  }
-  for (int f = threadIdx.x; f < N * N * N; f += NT) smem[L::OFF_BK + f] = (&T.Bk[0][0][0])[f];
-  if (threadIdx.x < N) smem[L::OFF_W + threadIdx.x] = T.w[threadIdx.x];
 }
 
 // Stages (a)+(b) for the tile's vertices, from the halo coefficients sc (mode-major):
@@ -445,9 +467,10 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
 // One tile of one stage: the whole path (a)-(e) for the cells [i0, i0+TX) x [j0, j0+TY)
 // (SURR: the instantiation that also runs the surrogate sensor and the features mode; the
 // plain instantiation carries none of that code, so its registers are unaffected)
-// of the mesh described by a.  The tabulations must already be staged in smem
-// (stage_tables_to_smem) and visible to the CTA; the function contains its own barriers
-// and is called by every thread of the CTA.
+// of the mesh described by a.  Every thread must have started the staging of the
+// tabulations (stage_tables_to_smem) before the call: the tile's first cp.async wait and
+// barrier complete it.  The function contains its own barriers and is called by every
+// thread of the CTA.
 template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false>
 __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<DIM, P>& T, int i0, int j0,
                                             float* smem) {
@@ -911,7 +934,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 template <int DIM, int P, int SYS, int TX, int TY, bool SURR>
 __device__ __forceinline__ void stage_body(const StageArgs& a, const DgTables<DIM, P>& T) {
   extern __shared__ __align__(16) float smem[];
-  stage_tables_to_smem<DIM, P, TX, TY>(T, smem);  // made visible by the tile's first barrier
+  stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);  // lands with the tile's first wait
   if constexpr (SURR && DIM == 2) {
     if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY>(a.mlp, smem);
   }

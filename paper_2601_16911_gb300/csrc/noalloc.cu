@@ -25,10 +25,12 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float g_stage_scratch[2 * kStaticStateFloats];
 static __device__ __align__(256) int g_static_status;
+static __device__ __align__(256) float g_static_tab_image[cvw::kMaxTabImage];
 
 struct DeviceSlots {
   float* scratch;
   int* status;
+  float* tab_image;
 };
 DeviceSlots g_slots[kMaxDevices];
 bool g_ready[kMaxDevices];
@@ -47,6 +49,8 @@ cudaError_t static_slots(DeviceSlots* out) {
     e = cudaGetSymbolAddress((void**)&s.scratch, g_stage_scratch);
     if (e != cudaSuccess) return e;
     e = cudaGetSymbolAddress((void**)&s.status, g_static_status);
+    if (e != cudaSuccess) return e;
+    e = cudaGetSymbolAddress((void**)&s.tab_image, g_static_tab_image);
     if (e != cudaSuccess) return e;
     g_slots[dev] = s;
     g_ready[dev] = true;
@@ -305,6 +309,7 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   // the status word must start at zero for this step; the stage buffers are fully
   // written before they are read
   if (cudaMemsetAsync(slots.status, 0, sizeof(int), s) != cudaSuccess) return CVWENO_ERR_CUDA;
+  if (launch_tab_image(m.dim, m.p, m.tables, slots.tab_image, s) != cudaSuccess) return CVWENO_ERR_CUDA;
 
   StageArgs a;
   memset(&a, 0, sizeof(a));
@@ -318,6 +323,7 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   a.two_dy = (float)(2.0 / m.dy);
   a.nu_scale = (float)(m.h / (2.0 * m.p));
   a.h_e = (float)m.h;
+  a.tab_img = slots.tab_image;
   a.eps = (float)p.eps;
   a.r = (int)p.r;
   a.q = (float)p.q;

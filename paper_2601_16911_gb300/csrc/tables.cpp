@@ -284,8 +284,23 @@ cvweno_status fill_cg(cvweno_mesh m) {
       wl += qw[q] * va;
     }
     t->wl[a] = (float)wl;
+    t->iml[a] = (float)(1.0 / ((a == 0 ? 2.0 : 1.0) * wl));
     m->cg_wl[a] = wl;
   }
+  // Em[a][m] = int l_a P_m, Dm[a][m] = int l_a P_m' (exact: degree <= 2p < 2 NG)
+  for (int a = 0; a < N; ++a)
+    for (int mm = 0; mm < N; ++mm) {
+      double e = 0.0, dd = 0.0, tab[2 * N];
+      for (int q = 0; q < NG; ++q) {
+        double va, da;
+        lagrange_eval(P, xg, a, qx[q], &va, &da);
+        legendre_derivs(qx[q], P, 1, tab);
+        e += qw[q] * va * tab[mm];
+        dd += qw[q] * va * tab[N + mm];
+      }
+      t->Em[a][mm] = (float)e;
+      t->Dm[a][mm] = (float)dd;
+    }
   // V[m][a] = (2m+1)/2 int P_m l_a and M1[a][b] = int l_a l_b, in FP64 then rounded once
   for (int mm = 0; mm < N; ++mm)
     for (int a = 0; a < N; ++a) {
