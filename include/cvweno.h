@@ -224,8 +224,9 @@ cvweno_status cvweno_positivity(cvweno_mesh m, const float* u, float* out, float
  * captured from such a step times each of its replays.  cvweno_kernel_times waits for
  * the last recorded event and writes the durations (ms) of the kernels of the most
  * recent step into ms[capacity] (host), in launch order: DG and Euler one per stage
- * (two with the HWENO or positivity limiter), CG four per stage (cells, node right-hand
- * side, two defect-correction sweeps); *count receives how many were written.  Timing
+ * (two with the HWENO or positivity limiter), CG two per stage in 2D (cells, then the
+ * node phase: assembly and both defect-correction sweeps) and four in 1D (cells, node
+ * right-hand side, two sweeps); *count receives how many were written.  Timing
  * costs one event record per kernel; turn it off (enable 0) for production runs.  Turning it off keeps the events
  * of the last timed step (and of graphs captured while it was on) readable. */
 cvweno_status cvweno_mesh_set_kernel_timing(cvweno_mesh m, int enable);

@@ -245,7 +245,6 @@ StageArgs base_args(const cvweno_mesh_s* m) {
   a.rnode = m->d_r;
   a.du = m->d_du;
   a.du2 = m->d_du2;
-  a.ubar = m->d_ubar;
   return a;
 }
 
@@ -396,7 +395,6 @@ cvweno_status cvweno_mesh_destroy(cvweno_mesh m) {
   cudaFree(m->d_r);
   cudaFree(m->d_du);
   cudaFree(m->d_du2);
-  cudaFree(m->d_ubar);
   cudaFree(m->d_cg_xg);
   cudaFree(m->d_cg_ml);
   cudaFree(m->d_tabimg);
@@ -480,10 +478,11 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (m->kind == CVWENO_CG) {
     if (e == cudaSuccess) e = cudaMalloc(&m->d_rloc, sizeof(float) * (size_t)m->ncell * m->nd);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_du2, sizeof(float) * (size_t)m->nnode);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_ubar, sizeof(float) * (size_t)m->ncell);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_r, sizeof(float) * (size_t)m->nnode);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_du, sizeof(float) * (size_t)m->nnode);
+    if (m->dim == 1) {  // 2D meshes keep the node phase in one kernel's shared memory
+      if (e == cudaSuccess) e = cudaMalloc(&m->d_du2, sizeof(float) * (size_t)m->nnode);
+      if (e == cudaSuccess) e = cudaMalloc(&m->d_r, sizeof(float) * (size_t)m->nnode);
+      if (e == cudaSuccess) e = cudaMalloc(&m->d_du, sizeof(float) * (size_t)m->nnode);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&m->d_cg_xg, sizeof(float) * (kMaxP + 1));
     if (e == cudaSuccess) e = cudaMalloc(&m->d_cg_ml, sizeof(double) * 2 * (kMaxP + 1));
     if (e == cudaSuccess) {

@@ -10,10 +10,13 @@
 //                       and the cell-local residual
 //                       int grad phi . f(u) - nu_e sum_q alpha_q w_q grad phi . (grad u - gamma P_h grad u)
 //                       (Sec. 2.2, CG form of eq. stab)
-//   K2 cg_node_rhs      deterministic nodal assembly r_j and du = r_j / ML_j
-//   K3 cg_node_sweep    du <- du + ML^{-1}(r - M_C du) (reading A12), node by node with
-//                       the tensor-product consistent mass; run twice, the second sweep
-//                       writing the SSP-RK3 combination (or du itself for a residual)
+//   K2 cg_node_stage2d  (2D) per tile of lattice nodes: the deterministic nodal assembly
+//                       r_j, du = r_j / ML_j, and the two defect-correction sweeps
+//                       du <- du + ML^{-1}(r - M_C du) (reading A12) with the
+//                       tensor-product consistent mass, the second writing the SSP-RK3
+//                       combination (or du itself for a residual); r and the first
+//                       iterate are formed on a halo of 2p nodes, so one launch suffices
+//   1D: cg_node_rhs (assembly, du = r / ML) and two cg_node_sweep launches
 // Nodal sums gather the cells around a node in a fixed order.
 #include "dg_scalar_kernel.cuh"
 
@@ -465,8 +468,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
       float u, gx, gy, px, py;
       node(qy, tb, td, tpx, tpy, u, gx, gy, px, py);
       // f(u) - f(ubar): the cell constant f(ubar) contributes f(ubar) int_K grad phi_a,
-      // which lives on the cell's edges and telescopes between neighbours; cg_node_rhs adds
-      // it as differences f(ubar_R) - f(ubar_L) of neighbouring means
+      // which lives on the cell's edges and telescopes between neighbours (added below)
       float fx, fy;
       law.flux_dev(u - c[0], fx, fy);
       const int q = qx + N * qy;
@@ -494,9 +496,25 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
         r[aa + N * b] = v;
       }
   }
+  // The constant part of the flux: int_K d_x phi_ab f(ubar_e) = (delta_{a,p} - delta_{a,0})
+  // wl_b (dy/2) f_x(ubar_e) (likewise in y).  At the nodes of an edge between a left cell L
+  // and a right cell R the two cells' terms sum to (f_x(ubar_L) - f_x(ubar_R)) wl_b dy/2;
+  // each cell adds that sum for its left and bottom edges (its right and top edges are
+  // its neighbours' left and bottom ones), the difference formed by the deviation formula
+  // of its own law from the halo means.
+  {
+    float fx, fy;
+    law.flux_dev(sc[hc - 1] - c[0], fx, fy);  // f(ubar_left) - f(ubar_e)
+#pragma unroll
+    for (int b = 0; b < NY1; ++b) r[N * b] = fmaf(fx, DIM == 2 ? C.wl[b] * hdy : 1.0f, r[N * b]);
+    if constexpr (DIM == 2) {
+      law.flux_dev(sc[hc - HX] - c[0], fx, fy);  // f(ubar_below) - f(ubar_e)
+#pragma unroll
+      for (int aa = 0; aa < N; ++aa) r[aa] = fmaf(fy, C.wl[aa] * hdx, r[aa]);
+    }
+  }
 #pragma unroll
   for (int m = 0; m < ND; ++m) a.rloc[cell * ND + m] = r[m];
-  a.ubar[cell] = c[0];
 }
 
 // cells around lattice node (I, J) in a fixed order, with the node's local index in each
@@ -505,9 +523,9 @@ __device__ __forceinline__ int node_cells(int I, int J, int nx, int ny, int* cel
   constexpr int N = P + 1;
   const int i = I / P, aa = I % P, j = DIM == 2 ? J / P : 0, bb = DIM == 2 ? J % P : 0;
   int cx[2], lx[2], ncx = 1, cy[2], ly[2], ncy = 1;
-  if (aa == 0) { cx[0] = (i - 1 + nx) % nx; lx[0] = P; cx[1] = i; lx[1] = 0; ncx = 2; }
+  if (aa == 0) { cx[0] = i == 0 ? nx - 1 : i - 1; lx[0] = P; cx[1] = i; lx[1] = 0; ncx = 2; }
   else { cx[0] = i; lx[0] = aa; }
-  if (DIM == 2 && bb == 0) { cy[0] = (j - 1 + ny) % ny; ly[0] = P; cy[1] = j; ly[1] = 0; ncy = 2; }
+  if (DIM == 2 && bb == 0) { cy[0] = j == 0 ? ny - 1 : j - 1; ly[0] = P; cy[1] = j; ly[1] = 0; ncy = 2; }
   else { cy[0] = j; ly[0] = bb; }
   int n = 0;
   for (int y = 0; y < ncy; ++y)
@@ -519,52 +537,30 @@ __device__ __forceinline__ int node_cells(int I, int J, int nx, int ny, int* cel
   return n;
 }
 
-// Nodal assembly.  Besides the cell-local residuals, the constant part of the flux:
-// int_K d_x phi_ab f(ubar_e) = (delta_{a,p} - delta_{a,0}) wl_b (dy/2) f_x(ubar_e) (and
-// likewise in y), which at a node shared by a left cell L and a right cell R sums to
-// -(f_x(ubar_R) - f_x(ubar_L)) wl_b dy/2; the difference of the two means' fluxes is
-// formed accurately by the deviation formula of the left cell's law.
-template <int DIM, int P, int SYS>
-__global__ void cg_node_rhs(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C) {
-  using Law = ScalarLaw<SYS, DIM>;
+// Nodal assembly r_j at lattice node (I, J), 0 <= I < nnx, 0 <= J < nny: the sum of the
+// cell-local residuals (which carry the telescoped flux of the cell means) over the
+// cells containing the node, in node_cells' order.
+template <int DIM, int P>
+__device__ __forceinline__ float node_residual(const StageArgs& a, int I, int J) {
   constexpr int ND = DIM == 2 ? (P + 1) * (P + 1) : P + 1;
+  int cells[4], locs[4];
+  const int n = node_cells<DIM, P>(I, J, a.nx, DIM == 2 ? a.ny : 1, cells, locs);
+  float r = 0.0f;
+#pragma unroll
+  for (int k = 0; k < (DIM == 2 ? 4 : 2); ++k)
+    if (k < n) r += a.rloc[(size_t)cells[k] * ND + locs[k]];
+  return r;
+}
+
+// 1D nodal assembly: r_j and du = r_j / ML_j.
+template <int DIM, int P>
+__global__ void cg_node_rhs(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<DIM, P> C) {
   const int64_t nn = (int64_t)a.nnx * (DIM == 2 ? a.nny : 1);
   const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
-  const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
     const int I = (int)(j % a.nnx), J = (int)(j / a.nnx);
-    int cells[4], locs[4];
-    const int n = node_cells<DIM, P>(I, J, nx, ny, cells, locs);
-    float r = 0.0f;
-    for (int k = 0; k < n; ++k) r += a.rloc[(size_t)cells[k] * ND + locs[k]];
-    const int i = I / P, ai = I % P, jj = J / P, bj = J % P;
-    if (ai == 0) {  // vertical cell edge: x-flux differences across it, one per cell row
-      const int iL = (i - 1 + nx) % nx;
-      const int nrow = (DIM == 2 && bj == 0) ? 2 : 1;
-      for (int k = 0; k < nrow; ++k) {
-        const int row = DIM == 2 ? ((bj == 0 && k == 0) ? (jj - 1 + ny) % ny : jj) : 0;
-        const int lb = DIM == 2 ? ((bj == 0) ? (k == 0 ? P : 0) : bj) : 0;
-        const float uL = a.ubar[iL + (size_t)nx * row], uR = a.ubar[i + (size_t)nx * row];
-        const Law law(a, uL);
-        float dfx, dfy;
-        law.flux_dev(uR - uL, dfx, dfy);
-        r -= dfx * (DIM == 2 ? C.wl[lb] * hdy : 1.0f);
-      }
-    }
-    if (DIM == 2 && bj == 0) {  // horizontal cell edge: y-flux differences, one per cell column
-      const int jB = (jj - 1 + ny) % ny;
-      const int ncol = ai == 0 ? 2 : 1;
-      for (int k = 0; k < ncol; ++k) {
-        const int col = (ai == 0 && k == 0) ? (i - 1 + nx) % nx : i;
-        const int la = (ai == 0) ? (k == 0 ? P : 0) : ai;
-        const float uB = a.ubar[col + (size_t)nx * jB], uT = a.ubar[col + (size_t)nx * jj];
-        const Law law(a, uB);
-        float dfx, dfy;
-        law.flux_dev(uT - uB, dfx, dfy);
-        r -= dfy * C.wl[la] * hdx;
-      }
-    }
-    const float ml = ml1(C, ai, hdx) * (DIM == 2 ? ml1(C, bj, hdy) : 1.0f);
+    const float r = node_residual<DIM, P>(a, I, J);
+    const float ml = ml1(C, I % P, hdx) * (DIM == 2 ? ml1(C, J % P, hdy) : 1.0f);
     a.rnode[j] = r;
     a.du[j] = r / ml;
   }
@@ -626,64 +622,119 @@ __global__ void cg_node_sweep(const __grid_constant__ StageArgs a, const __grid_
   }
 }
 
-// One defect-correction sweep du_out = du_in + ML^{-1}(r - M_C du_in) (reading A12).  The
-// consistent mass is the tensor product of the 1D assembled masses, so M_C du is applied
-// as two passes over a tile of nodes held in shared memory with a halo of p nodes: along
+// The node phase of one 2D stage, per tile of kNdX x kNdY lattice nodes: the nodal
+// assembly r and du0 = r / ML on the tile and a halo of 2p nodes, the first
+// defect-correction sweep du1 = du0 + ML^{-1}(r - M_C du0) (reading A12) on the tile and a
+// halo of p nodes, and the second at the tile's nodes, which writes the SSP-RK3
+// combination (or du itself for a residual).  The consistent mass is the tensor product
+// of the 1D assembled masses, so M_C du is applied as two passes over the window: along
 // x (each node sums M1[local][b] du over the nodes of the up to two cells containing it),
-// then along y.  The final sweep writes the SSP-RK3 combination (or du for a residual).
-constexpr int kSwX = 32, kSwY = 8;
+// then along y.  The halo values are recomputed by every tile that needs them, in the same
+// arithmetic, so neighbouring tiles agree bitwise.
+constexpr int kNdX = 32, kNdY = 8;
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+  if ((unsigned)i < (unsigned)n) return i;
+  i %= n;
+  return i < 0 ? i + n : i;
+}
 
 template <int P>
-__global__ void __launch_bounds__(kSwX* kSwY)
-    cg_node_sweep2d(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<2, P> C,
-                    const float* __restrict__ du_in, float* __restrict__ du_out, int final_sweep) {
-  constexpr int WX = kSwX + 2 * P, WY = kSwY + 2 * P, NT = kSwX * kSwY;
-  __shared__ float win[WY][WX];
-  __shared__ float wx[WY][kSwX];
+__global__ void __launch_bounds__(kNdX* kNdY)
+    cg_node_stage2d(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<2, P> C) {
+  constexpr int N = P + 1, NT = kNdX * kNdY;
+  constexpr int RX = kNdX + 4 * P, RY = kNdY + 4 * P;  // r and du0 window (halo 2p)
+  constexpr int DX = kNdX + 2 * P, DY = kNdY + 2 * P;  // du1 window (halo p)
+  __shared__ float sr[RY][RX];
+  __shared__ float sd0[RY][RX];
+  __shared__ float sxp[RY * DX];  // x-pass of M_C du0 [RY][DX], then of M_C du1 [DY][kNdX]
+  __shared__ float sd1[DY][DX];
+  __shared__ float sM1[N][N], siml[P];
   const int nnx = a.nnx, nny = a.nny;
-  const int I0 = blockIdx.x * kSwX, J0 = blockIdx.y * kSwY;
-  for (int f = threadIdx.x; f < WX * WY; f += NT) {
-    const int r = f / WX, c = f - r * WX;
-    const int I = ((I0 - P + c) % nnx + nnx) % nnx, J = ((J0 - P + r) % nny + nny) % nny;
-    win[r][c] = du_in[(size_t)J * nnx + I];
+  const int I0 = blockIdx.x * kNdX, J0 = blockIdx.y * kNdY;
+  const float hh = (1.0f / a.two_dx) * (1.0f / a.two_dy), k2 = a.two_dx * a.two_dy;
+  if (threadIdx.x < N * N) sM1[threadIdx.x / N][threadIdx.x % N] = (&C.M1[0][0])[threadIdx.x];
+  if (threadIdx.x < P) siml[threadIdx.x] = C.iml[threadIdx.x];
+  // this thread's output node and its RK inputs, loaded first so that their latency
+  // overlaps the window (u_n may alias u_out: only this thread reads or writes node j)
+  const int tx = threadIdx.x % kNdX, ty = threadIdx.x / kNdX;
+  const int I = I0 + tx, J = J0 + ty;
+  const bool own = I < nnx && J < nny;
+  const size_t j = own ? (size_t)J * nnx + I : 0;
+  const bool rk = (a.mode & kModeRK) != 0, with_un = rk && a.rk_a != 0.0f;
+  float uin = 0.0f, un = 0.0f;
+  if (own && rk) uin = a.u_in[j];
+  if (own && with_un) un = a.u_n[j];
+  // ---- r and du0 on the window --------------------------------------------------------------
+  for (int f = threadIdx.x; f < RX * RY; f += NT) {
+    const int ry = f / RX, rx = f - ry * RX;
+    sr[ry][rx] = node_residual<2, P>(a, wrap_index(I0 - 2 * P + rx, nnx), wrap_index(J0 - 2 * P + ry, nny));
   }
   __syncthreads();
-  for (int f = threadIdx.x; f < WY * kSwX; f += NT) {
-    const int r = f / kSwX, x = f - r * kSwX;
-    const int ax = (I0 + x) % P;
+  // 1 / ML of the node with 1D local indices (ax, ay), ax, ay in [0, p)
+  auto inv_ml = [&](int ax, int ay) { return siml[ax] * siml[ay] * k2; };
+  for (int f = threadIdx.x; f < RX * RY; f += NT) {
+    const int ry = f / RX, rx = f - ry * RX;
+    // window column rx is lattice column I0 - 2p + rx, whose local index is (I0 + rx) mod p
+    sd0[ry][rx] = sr[ry][rx] * inv_ml((I0 + rx) % P, (J0 + ry) % P);
+  }
+  __syncthreads();
+  // ---- first sweep: x-pass over the rows of the window, columns of the du1 window ----------
+  for (int f = threadIdx.x; f < RY * DX; f += NT) {
+    const int ry = f / DX, cx = f - ry * DX, rx = cx + P;
+    const int ax = (I0 + cx) % P, lx0 = ax == 0 ? P : ax;
     float w = 0.0f;
-    const int lx0 = ax == 0 ? P : ax, s0 = P + x - lx0;
 #pragma unroll
-    for (int b = 0; b <= P; ++b) w = fmaf(C.M1[lx0][b], win[r][s0 + b], w);
+    for (int b = 0; b <= P; ++b) w = fmaf(sM1[lx0][b], sd0[ry][rx - lx0 + b], w);
     if (ax == 0) {
 #pragma unroll
-      for (int b = 0; b <= P; ++b) w = fmaf(C.M1[0][b], win[r][P + x + b], w);
+      for (int b = 0; b <= P; ++b) w = fmaf(sM1[0][b], sd0[ry][rx + b], w);
     }
-    wx[r][x] = w;
+    sxp[ry * DX + cx] = w;
   }
   __syncthreads();
-  const int tx = threadIdx.x % kSwX, ty = threadIdx.x / kSwX;
-  const int I = I0 + tx, J = J0 + ty;
-  if (I >= nnx || J >= nny) return;
-  const int ay = J % P;
-  const int ly0 = ay == 0 ? P : ay, t0 = P + ty - ly0;
+  // ---- first sweep: y-pass and du1 -----------------------------------------------------------
+  for (int f = threadIdx.x; f < DY * DX; f += NT) {
+    const int dy = f / DX, cx = f - dy * DX, ry = dy + P, rx = cx + P;
+    const int ay = (J0 + dy) % P, ly0 = ay == 0 ? P : ay;
+    float mc = 0.0f;
+#pragma unroll
+    for (int d = 0; d <= P; ++d) mc = fmaf(sM1[ly0][d], sxp[(ry - ly0 + d) * DX + cx], mc);
+    if (ay == 0) {
+#pragma unroll
+      for (int d = 0; d <= P; ++d) mc = fmaf(sM1[0][d], sxp[(ry + d) * DX + cx], mc);
+    }
+    sd1[dy][cx] = sd0[ry][rx] + (sr[ry][rx] - mc * hh) * inv_ml((I0 + cx) % P, ay);
+  }
+  __syncthreads();
+  // ---- second sweep: x-pass over the du1 window's rows, the tile's columns ------------------
+  for (int f = threadIdx.x; f < DY * kNdX; f += NT) {
+    const int dy = f / kNdX, ox = f - dy * kNdX, cx = ox + P;
+    const int ax = (I0 + ox) % P, lx0 = ax == 0 ? P : ax;
+    float w = 0.0f;
+#pragma unroll
+    for (int b = 0; b <= P; ++b) w = fmaf(sM1[lx0][b], sd1[dy][cx - lx0 + b], w);
+    if (ax == 0) {
+#pragma unroll
+      for (int b = 0; b <= P; ++b) w = fmaf(sM1[0][b], sd1[dy][cx + b], w);
+    }
+    sxp[dy * kNdX + ox] = w;
+  }
+  __syncthreads();
+  if (!own) return;
+  // ---- second sweep: y-pass at this thread's node, and the stage output ----------------------
+  const int ay = J % P, ly0 = ay == 0 ? P : ay, dy = ty + P;
   float mc = 0.0f;
 #pragma unroll
-  for (int d = 0; d <= P; ++d) mc = fmaf(C.M1[ly0][d], wx[t0 + d][tx], mc);
+  for (int d = 0; d <= P; ++d) mc = fmaf(sM1[ly0][d], sxp[(dy - ly0 + d) * kNdX + tx], mc);
   if (ay == 0) {
 #pragma unroll
-    for (int d = 0; d <= P; ++d) mc = fmaf(C.M1[0][d], wx[P + ty + d][tx], mc);
+    for (int d = 0; d <= P; ++d) mc = fmaf(sM1[0][d], sxp[(dy + d) * kNdX + tx], mc);
   }
-  const float hdx = 1.0f / a.two_dx, hdy = 1.0f / a.two_dy;
-  mc *= hdx * hdy;
-  const size_t j = (size_t)J * nnx + I;
-  const float ml = ml1(C, I % P, hdx) * ml1(C, ay, hdy);
-  const float du = win[P + ty][P + tx] + (a.rnode[j] - mc) / ml;
-  if (!final_sweep) {
-    du_out[j] = du;
-  } else if (a.mode & kModeRK) {
-    float v = fmaf(a.dt, du, a.u_in[j]);
-    if (a.rk_a != 0.0f) v = fmaf(a.rk_b, v - a.u_n[j], a.u_n[j]);  // plain load: u_n may alias u_out
+  const float du = sd1[dy][tx + P] + (sr[ty + 2 * P][tx + 2 * P] - mc * hh) * inv_ml(I % P, ay);
+  if (rk) {
+    float v = fmaf(a.dt, du, uin);
+    if (with_un) v = fmaf(a.rk_b, v - un, un);
     a.u_out[j] = v;
     if (!isfinite(v)) atomicOr(a.status, kStatNonfinite);
   } else {
@@ -710,17 +761,15 @@ cudaError_t launch_cg_t(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t
   k1<<<grid, TX * TY, smem, s>>>(a, T, C);
   if (a.mode & kModeSensorOnly) return cudaGetLastError();
   kernel_mark(m, s);
-  const int64_t nn = m->nnode;
-  const int bn = (int)((nn + 255) / 256 < 4096 ? (nn + 255) / 256 : 4096);
-  cg_node_rhs<DIM, P, SYS><<<bn, 256, 0, s>>>(a, C);
-  kernel_mark(m, s);
   if constexpr (DIM == 2) {
-    const dim3 sg((a.nnx + kSwX - 1) / kSwX, (a.nny + kSwY - 1) / kSwY);
-    cg_node_sweep2d<P><<<sg, kSwX * kSwY, 0, s>>>(a, C, a.du, a.du2, 0);
-    kernel_mark(m, s);
-    cg_node_sweep2d<P><<<sg, kSwX * kSwY, 0, s>>>(a, C, a.du2, nullptr, 1);
+    const dim3 ng((a.nnx + kNdX - 1) / kNdX, (a.nny + kNdY - 1) / kNdY);
+    cg_node_stage2d<P><<<ng, kNdX * kNdY, 0, s>>>(a, C);
     kernel_mark(m, s);
   } else {
+    const int64_t nn = m->nnode;
+    const int bn = (int)((nn + 255) / 256 < 4096 ? (nn + 255) / 256 : 4096);
+    cg_node_rhs<DIM, P><<<bn, 256, 0, s>>>(a, C);
+    kernel_mark(m, s);
     cg_node_sweep<DIM, P><<<bn, 256, 0, s>>>(a, C, a.du, a.du2, 0);
     kernel_mark(m, s);
     cg_node_sweep<DIM, P><<<bn, 256, 0, s>>>(a, C, a.du2, nullptr, 1);

@@ -144,10 +144,9 @@ struct StageArgs {
   // CG only: nodal lattice and the per-stage work arrays
   int nnx, nny;
   float* rloc;  // [ncell][nd] cell-local residuals
-  float* rnode; // [nnode] assembled residual
-  float* du;    // [nnode] du/dt iterate
-  float* du2;   // [nnode] second defect-correction iterate
-  float* ubar;  // [ncell] cell means (Legendre mode 0)
+  float* rnode; // [nnode] assembled residual (1D)
+  float* du;    // [nnode] du/dt iterate (1D)
+  float* du2;   // [nnode] second defect-correction iterate (1D)
 };
 
 enum : int {
@@ -185,7 +184,6 @@ struct cvweno_mesh_s {
   float* d_r;
   float* d_du;
   float* d_du2;
-  float* d_ubar;
   double cg_xg[cvw::kMaxP + 1];  // GLL nodes (host, FP64)
   double cg_wl[cvw::kMaxP + 1];  // GLL weights (host, FP64)
   float* d_cg_xg;           // GLL nodes (device)

@@ -9,9 +9,13 @@ from paper_2601_16911_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kind,per_stage", [(I.DG, 1), (I.CG, 4)])
-def test_kernel_times_direct_and_in_graph(kind, per_stage):
-    d, ic = I.kpp(0, n=64, degree=2, kind=kind)
+@pytest.mark.parametrize("kind,dim,per_stage", [(I.DG, 2, 1), (I.CG, 2, 2), (I.CG, 1, 4)])
+def test_kernel_times_direct_and_in_graph(kind, dim, per_stage):
+    if dim == 2:
+        d, ic = I.kpp(0, n=64, degree=2, kind=kind)
+    else:
+        d, ic = I.burgers1d_step(0, nx=64, degree=2)
+        d = dict(d, kind=kind)
     mesh = cv.Mesh(d)
     u = mesh.project(*ic)
     assert mesh.kernel_times() == []
