@@ -517,39 +517,33 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   for (int m = 0; m < ND; ++m) a.rloc[cell * ND + m] = r[m];
 }
 
-// cells around lattice node (I, J) in a fixed order, with the node's local index in each
-template <int DIM, int P>
-__device__ __forceinline__ int node_cells(int I, int J, int nx, int ny, int* cells, int* locs) {
-  constexpr int N = P + 1;
-  const int i = I / P, aa = I % P, j = DIM == 2 ? J / P : 0, bb = DIM == 2 ? J % P : 0;
-  int cx[2], lx[2], ncx = 1, cy[2], ly[2], ncy = 1;
-  if (aa == 0) { cx[0] = i == 0 ? nx - 1 : i - 1; lx[0] = P; cx[1] = i; lx[1] = 0; ncx = 2; }
-  else { cx[0] = i; lx[0] = aa; }
-  if (DIM == 2 && bb == 0) { cy[0] = j == 0 ? ny - 1 : j - 1; ly[0] = P; cy[1] = j; ly[1] = 0; ncy = 2; }
-  else { cy[0] = j; ly[0] = bb; }
-  int n = 0;
-  for (int y = 0; y < ncy; ++y)
-    for (int x = 0; x < ncx; ++x) {
-      cells[n] = cx[x] + nx * cy[y];
-      locs[n] = lx[x] + (DIM == 2 ? N * ly[y] : 0);
-      ++n;
-    }
-  return n;
-}
-
 // Nodal assembly r_j at lattice node (I, J), 0 <= I < nnx, 0 <= J < nny: the sum of the
 // cell-local residuals (which carry the telescoped flux of the cell means) over the
-// cells containing the node, in node_cells' order.
+// cells containing the node, in a fixed order: the cell below-left of the node first,
+// then the one to its right, then the row above.  A node with local index a = 0 in x
+// lies in cell i - 1 (as its local p) and cell i (as its local 0); likewise in y.
 template <int DIM, int P>
 __device__ __forceinline__ float node_residual(const StageArgs& a, int I, int J) {
-  constexpr int ND = DIM == 2 ? (P + 1) * (P + 1) : P + 1;
-  int cells[4], locs[4];
-  const int n = node_cells<DIM, P>(I, J, a.nx, DIM == 2 ? a.ny : 1, cells, locs);
-  float r = 0.0f;
-#pragma unroll
-  for (int k = 0; k < (DIM == 2 ? 4 : 2); ++k)
-    if (k < n) r += a.rloc[(size_t)cells[k] * ND + locs[k]];
-  return r;
+  constexpr int N = P + 1, ND = DIM == 2 ? N * N : N;
+  const int nx = a.nx;
+  const int i = I / P, aa = I - i * P;
+  const int cx0 = aa == 0 ? (i == 0 ? nx - 1 : i - 1) : i, lx0 = aa == 0 ? P : aa;
+  if constexpr (DIM == 1) {
+    float r = a.rloc[(size_t)cx0 * ND + lx0];
+    if (aa == 0) r += a.rloc[(size_t)i * ND];
+    return r;
+  } else {
+    const int j = J / P, bb = J - j * P;
+    const int cy0 = bb == 0 ? (j == 0 ? a.ny - 1 : j - 1) : j, ly0 = bb == 0 ? P : bb;
+    const size_t row0 = (size_t)cy0 * nx, row1 = (size_t)j * nx;
+    float r = a.rloc[(row0 + cx0) * ND + lx0 + N * ly0];
+    if (aa == 0) r += a.rloc[(row0 + i) * ND + N * ly0];
+    if (bb == 0) {
+      r += a.rloc[(row1 + cx0) * ND + lx0];
+      if (aa == 0) r += a.rloc[(row1 + i) * ND];
+    }
+    return r;
+  }
 }
 
 // 1D nodal assembly: r_j and du = r_j / ML_j.
@@ -631,7 +625,7 @@ __global__ void cg_node_sweep(const __grid_constant__ StageArgs a, const __grid_
 // x (each node sums M1[local][b] du over the nodes of the up to two cells containing it),
 // then along y.  The halo values are recomputed by every tile that needs them, in the same
 // arithmetic, so neighbouring tiles agree bitwise.
-constexpr int kNdX = 32, kNdY = 8;
+constexpr int kNdX = 32, kNdY = 16;
 
 __device__ __forceinline__ int wrap_index(int i, int n) {
   if ((unsigned)i < (unsigned)n) return i;
@@ -640,7 +634,7 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(kNdX* kNdY)
+__global__ void __launch_bounds__(kNdX* kNdY, 4)
     cg_node_stage2d(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<2, P> C) {
   constexpr int N = P + 1, NT = kNdX * kNdY;
   constexpr int RX = kNdX + 4 * P, RY = kNdY + 4 * P;  // r and du0 window (halo 2p)
@@ -649,12 +643,11 @@ __global__ void __launch_bounds__(kNdX* kNdY)
   __shared__ float sd0[RY][RX];
   __shared__ float sxp[RY * DX];  // x-pass of M_C du0 [RY][DX], then of M_C du1 [DY][kNdX]
   __shared__ float sd1[DY][DX];
-  __shared__ float sM1[N][N], siml[P];
+  __shared__ float sM1[N][N];
   const int nnx = a.nnx, nny = a.nny;
   const int I0 = blockIdx.x * kNdX, J0 = blockIdx.y * kNdY;
   const float hh = (1.0f / a.two_dx) * (1.0f / a.two_dy), k2 = a.two_dx * a.two_dy;
   if (threadIdx.x < N * N) sM1[threadIdx.x / N][threadIdx.x % N] = (&C.M1[0][0])[threadIdx.x];
-  if (threadIdx.x < P) siml[threadIdx.x] = C.iml[threadIdx.x];
   // this thread's output node and its RK inputs, loaded first so that their latency
   // overlaps the window (u_n may alias u_out: only this thread reads or writes node j)
   const int tx = threadIdx.x % kNdX, ty = threadIdx.x / kNdX;
@@ -665,18 +658,35 @@ __global__ void __launch_bounds__(kNdX* kNdY)
   float uin = 0.0f, un = 0.0f;
   if (own && rk) uin = a.u_in[j];
   if (own && with_un) un = a.u_n[j];
-  // ---- r and du0 on the window --------------------------------------------------------------
-  for (int f = threadIdx.x; f < RX * RY; f += NT) {
-    const int ry = f / RX, rx = f - ry * RX;
-    sr[ry][rx] = node_residual<2, P>(a, wrap_index(I0 - 2 * P + rx, nnx), wrap_index(J0 - 2 * P + ry, nny));
-  }
-  __syncthreads();
   // 1 / ML of the node with 1D local indices (ax, ay), ax, ay in [0, p)
-  auto inv_ml = [&](int ax, int ay) { return siml[ax] * siml[ay] * k2; };
-  for (int f = threadIdx.x; f < RX * RY; f += NT) {
-    const int ry = f / RX, rx = f - ry * RX;
-    // window column rx is lattice column I0 - 2p + rx, whose local index is (I0 + rx) mod p
-    sd0[ry][rx] = sr[ry][rx] * inv_ml((I0 + rx) % P, (J0 + ry) % P);
+  auto iml = [&](int l) {
+    float v = C.iml[0];
+#pragma unroll
+    for (int k = 1; k < P; ++k) v = l == k ? C.iml[k] : v;
+    return v;
+  };
+  auto inv_ml = [&](int ax, int ay) { return iml(ax) * iml(ay) * k2; };
+  // ---- r and du0 on the window: every gather of the thread in flight before the first use -----
+  constexpr int NW = (RX * RY + NT - 1) / NT;
+  float rv[NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const int f = threadIdx.x + k * NT;
+    rv[k] = 0.0f;
+    if (f < RX * RY) {
+      const int ry = f / RX, rx = f - ry * RX;
+      rv[k] = node_residual<2, P>(a, wrap_index(I0 - 2 * P + rx, nnx), wrap_index(J0 - 2 * P + ry, nny));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const int f = threadIdx.x + k * NT;
+    if (f < RX * RY) {
+      const int ry = f / RX, rx = f - ry * RX;
+      sr[ry][rx] = rv[k];
+      // window column rx is lattice column I0 - 2p + rx, whose local index is (I0 + rx) mod p
+      sd0[ry][rx] = rv[k] * inv_ml((I0 + rx) % P, (J0 + ry) % P);
+    }
   }
   __syncthreads();
   // ---- first sweep: x-pass over the rows of the window, columns of the du1 window ----------
