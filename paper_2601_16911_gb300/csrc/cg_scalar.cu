@@ -23,6 +23,13 @@
 namespace cvw {
 namespace {
 
+// i mod n for any int i (n > 0), without a division when i is already in range
+__device__ __forceinline__ int wrap_index(int i, int n) {
+  if ((unsigned)i < (unsigned)n) return i;
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
 template <int DIM, int P, int TX, int TY>
 struct CgLayout {
   using L = TileLayout<DIM, P, TX, TY>;
@@ -75,8 +82,8 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
     const int I0 = P * (i0 - 1), J0 = DIM == 2 ? P * (j0 - 1) : 0;
     for (int f = threadIdx.x; f < NNX * NNY; f += NT) {
       const int ix = f % NNX, iy = f / NNX;
-      const int I = ((I0 + ix) % nnx + nnx) % nnx;
-      const int J = DIM == 2 ? ((J0 + iy) % nny + nny) % nny : 0;
+      const int I = wrap_index(I0 + ix, nnx);
+      const int J = DIM == 2 ? wrap_index(J0 + iy, nny) : 0;
       cp_async4(snode + f, a.u_in + (size_t)J * nnx + I, 4);
     }
   }
@@ -627,11 +634,6 @@ __global__ void cg_node_sweep(const __grid_constant__ StageArgs a, const __grid_
 // arithmetic, so neighbouring tiles agree bitwise.
 constexpr int kNdX = 32, kNdY = 16;
 
-__device__ __forceinline__ int wrap_index(int i, int n) {
-  if ((unsigned)i < (unsigned)n) return i;
-  i %= n;
-  return i < 0 ? i + n : i;
-}
 
 template <int P>
 __global__ void __launch_bounds__(kNdX* kNdY, 4)

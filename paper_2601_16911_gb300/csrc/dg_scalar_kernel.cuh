@@ -219,7 +219,7 @@ struct TileLayout {
   static constexpr int OFF_BK = OFF_A + Img::BK;
   static constexpr int OFF_W = OFF_A + Img::W;
   static constexpr int OFF_NQ = OFF_A + Img::FLOATS;              // [ND][NT] pointwise indicators
-  static constexpr int OFF_UN = OFF_NQ + ND * NT;                 // [ND][NT] u_n of the tile's cells
+  static constexpr int OFF_UN = OFF_NQ + ND * NT;                 // u_n of the tile's cells, [ND][NT] or [NT][ND]
   static constexpr int FLOATS = OFF_UN + ND * NT;
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
   // with the surrogate sensor: packed weights, then one 32 x 16 bf16 input block per warp
@@ -507,18 +507,29 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     }
     cp_async4(sc + mm * NH + r * HX + cc, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + mm : a.u_in, ok ? 4 : 0);
   }
-  const bool pre_un = (a.mode & kModeRK) && a.rk_a != 0.0f;
-  if (pre_un) {
-    float* sUn = smem + L::OFF_UN;
-    for (int f = threadIdx.x; f < NT * ND; f += NT) {
-      const int cl = f / ND, mm = f - cl * ND;
-      const int gi = i0 + cl % TX, gj = DIM == 2 ? j0 + cl / TX : 0;
-      const bool ok = gi < nx && gj < ny;
-      cp_async4(sUn + mm * NT + cl, ok ? a.u_n + ((size_t)gj * nx + gi) * ND + mm : a.u_n, ok ? 4 : 0);
-    }
-  }
   cp_async_wait_all();
   __syncthreads();
+
+  // u_n of the thread's own cell (RK stages 2 and 3), read only by the output: copied after
+  // the halo burst so that it overlaps the stages below, and awaited before the output.
+  // Only this thread reads u_n or writes u_out for its cell, so u_n may alias u_out.
+  // Cell-major 16-byte copies where the cell is whole 16-byte chunks, else mode-major.
+  const bool pre_un = (a.mode & kModeRK) && a.rk_a != 0.0f;
+  const bool un16 = ND % 4 == 0 && (reinterpret_cast<uintptr_t>(a.u_n) & 15) == 0;
+  {
+    const int ogi = i0 + threadIdx.x % TX, ogj = DIM == 2 ? j0 + threadIdx.x / TX : 0;
+    if (pre_un && ogi < nx && ogj < ny) {
+      const float* src = a.u_n + ((size_t)ogj * nx + ogi) * ND;
+      float* sUn = smem + L::OFF_UN;
+      if (un16) {
+#pragma unroll
+        for (int k = 0; k < ND / 4; ++k) cp_async16(sUn + threadIdx.x * ND + 4 * k, src + 4 * k);
+      } else {
+#pragma unroll 1
+        for (int m = 0; m < ND; ++m) cp_async4(sUn + m * NT + threadIdx.x, src + m, 4);
+      }
+    }
+  }
 
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
   tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
@@ -910,7 +921,8 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   // M^{-1} and output
   bool bad = false;
   float* out = a.u_out + cell * ND;
-  const float* sUn = smem + L::OFF_UN;  // u_n of this cell, copied before any write
+  const float* sUn = smem + L::OFF_UN;  // u_n of this cell
+  if (pre_un) cp_async_wait_all();
 #pragma unroll
   for (int m = 0; m < ND; ++m) {
     const int mx = m % N, my = DIM == 2 ? m / N : 0;
@@ -920,7 +932,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     if (a.mode & kModeRK) {
       float v = fmaf(a.dt, d, c[m]);
       if (pre_un) {
-        const float un = sUn[m * NT + threadIdx.x];
+        const float un = un16 ? sUn[threadIdx.x * ND + m] : sUn[m * NT + threadIdx.x];
         v = fmaf(a.rk_b, v - un, un);
       }
       out[m] = v;
