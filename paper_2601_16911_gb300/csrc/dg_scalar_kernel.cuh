@@ -306,10 +306,15 @@ __device__ __forceinline__ float cell_norm0(const DgTables<DIM, P>& T, const flo
   return sqrtf(n2);
 }
 
-// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned).
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned); the
+// zero-filling form copies src_bytes (0 or 16) and fills the rest with zeros.
 __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async16z(float* dst, const float* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
 }
 
 // Starts the copy of the tabulation image img (device, TabImage<DIM, P>) into shared
@@ -490,25 +495,59 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 
   const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
 
-  // ---- load tile + halo (and u_n of the tile's cells for the RK combination) ------------
-  // asynchronous copies: every load of the thread is in flight before the first wait
-  for (int f = threadIdx.x; f < NH * ND; f += NT) {
-    int r = f / (HX * ND);
-    int rem = f - r * (HX * ND);
-    int cc = rem / ND;
-    int mm = rem - cc * ND;
-    int gi = i0 - 1 + cc, gj = DIM == 2 ? j0 - 1 + r : 0;
-    bool ok = true;
-    if (gi < 0 || gi >= nx) {
-      if (a.perx) gi = (gi + nx) % nx; else ok = false;
+  // ---- load tile + halo ---------------------------------------------------------------------
+  // Asynchronous copies, every one of the thread's in flight before the first wait.  Where a
+  // cell is whole 16-byte chunks, 16-byte copies land cell-major in a staging area (over the
+  // indicator and u_n regions, unused until later) and are transposed to the mode-major
+  // layout sc[m][h]; otherwise 4-byte copies write sc directly.
+  static_assert(NH * ND <= 2 * ND * NT, "halo staging must fit the indicator and u_n regions");
+  const bool in16 = ND % 4 == 0 && (reinterpret_cast<uintptr_t>(a.u_in) & 15) == 0;
+  float* stg = smem + L::OFF_NQ;
+  constexpr int NQ4 = ND / 4;
+  if (in16) {
+    for (int f = threadIdx.x; f < NH * NQ4; f += NT) {
+      const int h = f / NQ4, q = f - h * NQ4;
+      const int r = DIM == 2 ? h / HX : 0, cc = h - r * HX;
+      int gi = i0 - 1 + cc, gj = DIM == 2 ? j0 - 1 + r : 0;
+      bool ok = true;
+      if (gi < 0 || gi >= nx) {
+        if (a.perx) gi = (gi + nx) % nx; else ok = false;
+      }
+      if (DIM == 2 && (gj < 0 || gj >= ny)) {
+        if (a.pery) gj = (gj + ny) % ny; else ok = false;
+      }
+      cp_async16z(stg + 4 * f, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + 4 * q : a.u_in, ok ? 16 : 0);
     }
-    if (DIM == 2 && (gj < 0 || gj >= ny)) {
-      if (a.pery) gj = (gj + ny) % ny; else ok = false;
+  } else {
+    for (int f = threadIdx.x; f < NH * ND; f += NT) {
+      int r = f / (HX * ND);
+      int rem = f - r * (HX * ND);
+      int cc = rem / ND;
+      int mm = rem - cc * ND;
+      int gi = i0 - 1 + cc, gj = DIM == 2 ? j0 - 1 + r : 0;
+      bool ok = true;
+      if (gi < 0 || gi >= nx) {
+        if (a.perx) gi = (gi + nx) % nx; else ok = false;
+      }
+      if (DIM == 2 && (gj < 0 || gj >= ny)) {
+        if (a.pery) gj = (gj + ny) % ny; else ok = false;
+      }
+      cp_async4(sc + mm * NH + r * HX + cc, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + mm : a.u_in, ok ? 4 : 0);
     }
-    cp_async4(sc + mm * NH + r * HX + cc, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + mm : a.u_in, ok ? 4 : 0);
   }
   cp_async_wait_all();
   __syncthreads();
+  if (in16) {
+    for (int f = threadIdx.x; f < NH * NQ4; f += NT) {
+      const int h = f / NQ4, q = f - h * NQ4;
+      const float4 v = *reinterpret_cast<const float4*>(stg + 4 * f);
+      sc[(4 * q + 0) * NH + h] = v.x;
+      sc[(4 * q + 1) * NH + h] = v.y;
+      sc[(4 * q + 2) * NH + h] = v.z;
+      sc[(4 * q + 3) * NH + h] = v.w;
+    }
+    __syncthreads();
+  }
 
   // u_n of the thread's own cell (RK stages 2 and 3), read only by the output: copied after
   // the halo burst so that it overlaps the stages below, and awaited before the output.
