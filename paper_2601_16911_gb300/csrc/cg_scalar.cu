@@ -35,10 +35,15 @@ struct CgLayout {
   using L = TileLayout<DIM, P, TX, TY>;
   static constexpr int N = P + 1, ND = L::ND, NH = L::NH;
   static constexpr int NNX = P * (TX + 2) + 1, NNY = DIM == 2 ? P * (TY + 2) + 1 : 1;
-  static constexpr int OFF_NODE = L::FLOATS;              // [NNY][NNX] nodal values
-  static constexpr int OFF_BX = OFF_NODE + NNX * NNY;     // [ND][NH] int phi_a d_x u
+  // nodal rows at a 16-byte stride with room for a per-row phase of up to 3 floats
+  static constexpr int NNXP = (NNX + 3 + 3) / 4 * 4;
+  // The nodal tile is dead once the halo cells are converted to modes, and the local
+  // integrals are written after that barrier: both start at the u_n region of the DG
+  // layout, which the CG kernel does not use (its RK combination runs on the nodes).
+  static constexpr int OFF_NODE = L::OFF_UN;              // [NNY][NNXP] nodal values
+  static constexpr int OFF_BX = L::OFF_UN;                // [ND][NH] int phi_a d_x u
   static constexpr int OFF_BY = OFF_BX + ND * NH;         // [ND][NH] int phi_a d_y u
-  static constexpr int FLOATS = OFF_BY + ND * NH;
+  static constexpr int FLOATS = L::OFF_UN + (2 * ND * NH > NNXP * NNY ? 2 * ND * NH : NNXP * NNY);
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
 };
 
@@ -57,7 +62,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   using G = CgLayout<DIM, P, TX, TY>;
   using Law = ScalarLaw<SYS, DIM>;
   constexpr int N = L::N, ND = L::ND, NT = L::NT, HX = L::HX, NH = L::NH;
-  constexpr int NNX = G::NNX, NNY = G::NNY;
+  constexpr int NNX = G::NNX, NNY = G::NNY, NNXP = G::NNXP;
   constexpr int NY1 = DIM == 2 ? N : 1;
   extern __shared__ __align__(16) float smem[];
   float* sc = smem + L::OFF_SC;
@@ -78,13 +83,35 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
 
   // ---- nodal values of the tile and its halo (periodic lattice) -------------------------
+  // Node (ix, iy) lands at snode[iy][sph[iy] + ix].  Where the tile's rows do not wrap in x
+  // and the state is 16-byte aligned, each row is copied as the 16-byte chunks that cover
+  // it: the first chunk starts up to 3 floats early (sph, the row's phase), the last is
+  // zero-filled past the row's last node, so no read leaves the row's own span or the
+  // floats just before it.  Otherwise 4-byte copies, phase 0.
+  __shared__ int sph[NNY];
   {
     const int I0 = P * (i0 - 1), J0 = DIM == 2 ? P * (j0 - 1) : 0;
-    for (int f = threadIdx.x; f < NNX * NNY; f += NT) {
-      const int ix = f % NNX, iy = f / NNX;
-      const int I = wrap_index(I0 + ix, nnx);
-      const int J = DIM == 2 ? wrap_index(J0 + iy, nny) : 0;
-      cp_async4(snode + f, a.u_in + (size_t)J * nnx + I, 4);
+    const bool rows16 = I0 >= 0 && I0 + NNX <= nnx && (reinterpret_cast<uintptr_t>(a.u_in) & 15) == 0;
+    if (rows16) {
+      constexpr int NCH = NNXP / 4;  // chunks per row
+      for (int f = threadIdx.x; f < NNY * NCH; f += NT) {
+        const int iy = f / NCH, k = f - iy * NCH;
+        const int J = DIM == 2 ? wrap_index(J0 + iy, nny) : 0;
+        const int64_t g0 = (int64_t)J * nnx + I0;  // the row's first node
+        const int ph = (int)(g0 & 3);
+        const int64_t c0 = g0 - ph + 4 * k;
+        const int64_t left = g0 + NNX - c0;  // wanted floats from the chunk's start on
+        if (left > 0) cp_async16z(snode + iy * NNXP + 4 * k, a.u_in + c0, left >= 4 ? 16 : (int)left * 4);
+        if (k == 0) sph[iy] = ph;
+      }
+    } else {
+      for (int f = threadIdx.x; f < NNX * NNY; f += NT) {
+        const int ix = f % NNX, iy = f / NNX;
+        const int I = wrap_index(I0 + ix, nnx);
+        const int J = DIM == 2 ? wrap_index(J0 + iy, nny) : 0;
+        cp_async4(snode + iy * NNXP + ix, a.u_in + (size_t)J * nnx + I, 4);
+      }
+      for (int iy = threadIdx.x; iy < NNY; iy += NT) sph[iy] = 0;
     }
   }
   stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);
@@ -100,7 +127,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
 #pragma unroll
     for (int b = 0; b < NY1; ++b)
 #pragma unroll
-      for (int aa = 0; aa < N; ++aa) ul[aa + N * b] = snode[(P * hx + aa) + NNX * (P * hy + b)];
+      for (int aa = 0; aa < N; ++aa) ul[aa + N * b] = snode[sph[P * hy + b] + (P * hx + aa) + NNXP * (P * hy + b)];
     const float uref = ul[0];
 #pragma unroll
     for (int m = 0; m < ND; ++m) ul[m] -= uref;
@@ -646,6 +673,12 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
   __shared__ float sxp[RY * DX];  // x-pass of M_C du0 [RY][DX], then of M_C du1 [DY][kNdX]
   __shared__ float sd1[DY][DX];
   __shared__ float sM1[N][N];
+  // per window column rx (lattice column I0 - 2p + rx) and row ry: the offsets of the
+  // local residual entries the node gathers (B: the second cell, -1 if none), the node's
+  // 1D local index and its inverse 1D lumped mass
+  __shared__ long long srowA[RY], srowB[RY];
+  __shared__ int scolA[RX], scolB[RX], slx[RX], sly[RY];
+  __shared__ float simlx[RX], simly[RY];
   const int nnx = a.nnx, nny = a.nny;
   const int I0 = blockIdx.x * kNdX, J0 = blockIdx.y * kNdY;
   const float hh = (1.0f / a.two_dx) * (1.0f / a.two_dy), k2 = a.two_dx * a.two_dy;
@@ -660,14 +693,32 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
   float uin = 0.0f, un = 0.0f;
   if (own && rk) uin = a.u_in[j];
   if (own && with_un) un = a.u_n[j];
-  // 1 / ML of the node with 1D local indices (ax, ay), ax, ay in [0, p)
+  // 1 / (m_l wl[l]) of 1D local index l in [0, p)
   auto iml = [&](int l) {
     float v = C.iml[0];
 #pragma unroll
     for (int k = 1; k < P; ++k) v = l == k ? C.iml[k] : v;
     return v;
   };
-  auto inv_ml = [&](int ax, int ay) { return iml(ax) * iml(ay) * k2; };
+  // A node with 1D local index 0 lies in two cells (the one before it as its local p),
+  // any other in one; the nodal sum takes the cells below-left first (node_residual's order).
+  if (threadIdx.x < RX) {
+    const int rx = threadIdx.x, Iw = wrap_index(I0 - 2 * P + rx, nnx), i = Iw / P, aa = Iw - i * P;
+    const int cx0 = aa == 0 ? (i == 0 ? a.nx - 1 : i - 1) : i;
+    scolA[rx] = cx0 * (N * N) + (aa == 0 ? P : aa);
+    scolB[rx] = aa == 0 ? i * (N * N) : -1;
+    slx[rx] = aa;
+    simlx[rx] = iml(aa);
+  } else if (threadIdx.x < RX + RY) {
+    const int ry = threadIdx.x - RX, Jw = wrap_index(J0 - 2 * P + ry, nny), jc = Jw / P, bb = Jw - jc * P;
+    const int cy0 = bb == 0 ? (jc == 0 ? a.ny - 1 : jc - 1) : jc;
+    const long long rowlen = (long long)a.nx * (N * N);
+    srowA[ry] = cy0 * rowlen + N * (bb == 0 ? P : bb);
+    srowB[ry] = bb == 0 ? jc * rowlen : -1;
+    sly[ry] = bb;
+    simly[ry] = iml(bb);
+  }
+  __syncthreads();
   // ---- r and du0 on the window: every gather of the thread in flight before the first use -----
   constexpr int NW = (RX * RY + NT - 1) / NT;
   float rv[NW];
@@ -677,7 +728,15 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
     rv[k] = 0.0f;
     if (f < RX * RY) {
       const int ry = f / RX, rx = f - ry * RX;
-      rv[k] = node_residual<2, P>(a, wrap_index(I0 - 2 * P + rx, nnx), wrap_index(J0 - 2 * P + ry, nny));
+      const long long rA = srowA[ry], rB = srowB[ry];
+      const int cA = scolA[rx], cB = scolB[rx];
+      float r = a.rloc[rA + cA];
+      if (cB >= 0) r += a.rloc[rA + cB];
+      if (rB >= 0) {
+        r += a.rloc[rB + cA];
+        if (cB >= 0) r += a.rloc[rB + cB];
+      }
+      rv[k] = r;
     }
   }
 #pragma unroll
@@ -686,15 +745,14 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
     if (f < RX * RY) {
       const int ry = f / RX, rx = f - ry * RX;
       sr[ry][rx] = rv[k];
-      // window column rx is lattice column I0 - 2p + rx, whose local index is (I0 + rx) mod p
-      sd0[ry][rx] = rv[k] * inv_ml((I0 + rx) % P, (J0 + ry) % P);
+      sd0[ry][rx] = rv[k] * (simlx[rx] * simly[ry] * k2);
     }
   }
   __syncthreads();
   // ---- first sweep: x-pass over the rows of the window, columns of the du1 window ----------
   for (int f = threadIdx.x; f < RY * DX; f += NT) {
     const int ry = f / DX, cx = f - ry * DX, rx = cx + P;
-    const int ax = (I0 + cx) % P, lx0 = ax == 0 ? P : ax;
+    const int ax = slx[rx], lx0 = ax == 0 ? P : ax;
     float w = 0.0f;
 #pragma unroll
     for (int b = 0; b <= P; ++b) w = fmaf(sM1[lx0][b], sd0[ry][rx - lx0 + b], w);
@@ -708,7 +766,7 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
   // ---- first sweep: y-pass and du1 -----------------------------------------------------------
   for (int f = threadIdx.x; f < DY * DX; f += NT) {
     const int dy = f / DX, cx = f - dy * DX, ry = dy + P, rx = cx + P;
-    const int ay = (J0 + dy) % P, ly0 = ay == 0 ? P : ay;
+    const int ay = sly[ry], ly0 = ay == 0 ? P : ay;
     float mc = 0.0f;
 #pragma unroll
     for (int d = 0; d <= P; ++d) mc = fmaf(sM1[ly0][d], sxp[(ry - ly0 + d) * DX + cx], mc);
@@ -716,13 +774,13 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
 #pragma unroll
       for (int d = 0; d <= P; ++d) mc = fmaf(sM1[0][d], sxp[(ry + d) * DX + cx], mc);
     }
-    sd1[dy][cx] = sd0[ry][rx] + (sr[ry][rx] - mc * hh) * inv_ml((I0 + cx) % P, ay);
+    sd1[dy][cx] = sd0[ry][rx] + (sr[ry][rx] - mc * hh) * (simlx[rx] * simly[ry] * k2);
   }
   __syncthreads();
   // ---- second sweep: x-pass over the du1 window's rows, the tile's columns ------------------
   for (int f = threadIdx.x; f < DY * kNdX; f += NT) {
     const int dy = f / kNdX, ox = f - dy * kNdX, cx = ox + P;
-    const int ax = (I0 + ox) % P, lx0 = ax == 0 ? P : ax;
+    const int ax = slx[ox + 2 * P], lx0 = ax == 0 ? P : ax;
     float w = 0.0f;
 #pragma unroll
     for (int b = 0; b <= P; ++b) w = fmaf(sM1[lx0][b], sd1[dy][cx - lx0 + b], w);
@@ -735,7 +793,7 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
   __syncthreads();
   if (!own) return;
   // ---- second sweep: y-pass at this thread's node, and the stage output ----------------------
-  const int ay = J % P, ly0 = ay == 0 ? P : ay, dy = ty + P;
+  const int ay = sly[ty + 2 * P], ly0 = ay == 0 ? P : ay, dy = ty + P;
   float mc = 0.0f;
 #pragma unroll
   for (int d = 0; d <= P; ++d) mc = fmaf(sM1[ly0][d], sxp[(dy - ly0 + d) * kNdX + tx], mc);
@@ -743,7 +801,7 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
 #pragma unroll
     for (int d = 0; d <= P; ++d) mc = fmaf(sM1[0][d], sxp[(dy + d) * kNdX + tx], mc);
   }
-  const float du = sd1[dy][tx + P] + (sr[ty + 2 * P][tx + 2 * P] - mc * hh) * inv_ml(I % P, ay);
+  const float du = sd1[dy][tx + P] + (sr[ty + 2 * P][tx + 2 * P] - mc * hh) * (simlx[tx + 2 * P] * simly[ty + 2 * P] * k2);
   if (rk) {
     float v = fmaf(a.dt, du, uin);
     if (with_un) v = fmaf(a.rk_b, v - un, un);
