@@ -317,6 +317,64 @@ __device__ __forceinline__ void cp_async16z(float* dst, const float* src, int sr
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
 }
 
+// Starts the copy of R rows of W consecutive columns of a row-major global array (nrow
+// rows of ncol columns, each column E floats) into shared memory: row r, column c lands at
+// dst[r * RS + ph[r] + c * E + e].  Global row r0 + r and column c0 + c wrap (periodic) or,
+// outside the array, read as zeros.  The row's in-range columns are one run in global
+// memory; ph[r] is its offset within a 16-byte chunk, so the run's whole chunks are copied
+// 16 bytes at a time (src 16-byte aligned required) and only its head and tail (under 4
+// floats each, 6 at most when the run has no whole chunk) and the wrapped or absent
+// columns float by float.  One warp per row (rows of many chunks).  Requires
+// RS >= W * E + 3; the copies land with the thread's next cp.async wait, the zeros and
+// ph[] with the next barrier.
+template <int E, int W, int R, int RS, int NT>
+__device__ __forceinline__ void stage_rows16(float* dst, int* ph, const float* src, int ncol, int nrow, int c0,
+                                             int r0, bool perc, bool perr) {
+  static_assert(RS >= W * E + 3 && RS % 4 == 0, "staging row too short");
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int c_lo = max(0, -c0), c_hi = min(W - 1, ncol - 1 - c0);  // in-range columns
+  const int cr = max(c_hi + 1, c_lo), nout = (c_lo + W - cr) * E;  // columns [0, c_lo), [cr, W)
+#pragma unroll 1
+  for (int r = warp; r < R; r += NW) {
+    int gr = r0 + r;
+    bool row_ok = true;
+    if (gr < 0 || gr >= nrow) {
+      if (perr) gr = ((gr % nrow) + nrow) % nrow; else row_ok = false;
+    }
+    float* d = dst + r * RS;
+    if (!row_ok) {
+      for (int e = lane; e < W * E; e += 32) d[e] = 0.0f;
+      if (lane == 0) ph[r] = 0;
+      continue;
+    }
+    const int64_t gbase = ((int64_t)gr * ncol + c0) * E;  // global float of column 0
+    const int p = (int)(gbase & 3);
+    if (lane == 0) ph[r] = p;
+    d += p;
+    // body: the whole 16-byte chunks of the in-range run [g0, g1)
+    const int64_t g0 = gbase + (int64_t)c_lo * E, g1 = c_hi < c_lo ? g0 : gbase + (int64_t)(c_hi + 1) * E;
+    const int64_t b0 = (g0 + 3) & ~(int64_t)3, b1 = g1 & ~(int64_t)3;
+    const bool body = b0 < b1;
+    if (body)
+      for (int64_t x = b0 + 4 * lane; x < b1; x += 128) cp_async16(d + (x - gbase), src + x);
+    // head and tail of the run (or the whole run when it has no whole chunk)
+    const int nh = body ? (int)(b0 - g0) : (int)(g1 - g0), nt = body ? (int)(g1 - b1) : 0;
+    if (lane < nh) cp_async4(d + (g0 + lane - gbase), src + g0 + lane, 4);
+    else if (lane < nh + nt) cp_async4(d + (b1 + lane - nh - gbase), src + b1 + lane - nh, 4);
+    for (int j = lane; j < nout; j += 32) {
+      const int cj = j / E, e = j - cj * E;
+      const int c = cj < c_lo ? cj : cr + (cj - c_lo);
+      if (perc) {
+        const int gc = ((c0 + c) % ncol + ncol) % ncol;
+        cp_async4(d + c * E + e, src + ((int64_t)gr * ncol + gc) * E + e, 4);
+      } else {
+        d[c * E + e] = 0.0f;
+      }
+    }
+  }
+}
+
 // Starts the copy of the tabulation image img (device, TabImage<DIM, P>) into shared
 // memory; it lands with the tile's first cp.async wait.
 template <int DIM, int P, int TX, int TY>
@@ -496,15 +554,25 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   const int nx = a.nx, ny = DIM == 2 ? a.ny : 1;
 
   // ---- load tile + halo ---------------------------------------------------------------------
-  // Asynchronous copies, every one of the thread's in flight before the first wait.  Where a
-  // cell is whole 16-byte chunks, 16-byte copies land cell-major in a staging area (over the
-  // indicator and u_n regions, unused until later) and are transposed to the mode-major
-  // layout sc[m][h]; otherwise 4-byte copies write sc directly.
+  // Asynchronous copies, every one of the thread's in flight before the first wait, landing
+  // in a staging area (over the indicator and u_n regions, unused until later) and then
+  // transposed to the mode-major layout sc[m][h]:
+  //  - a cell of whole 16-byte chunks (Q1, Q3): 16-byte copies per cell, cell-major;
+  //  - otherwise each halo row by stage_rows16, at the row's phase sph[r];
+  //  - a state that is not 16-byte aligned: 4-byte copies straight into sc.
   static_assert(NH * ND <= 2 * ND * NT, "halo staging must fit the indicator and u_n regions");
-  const bool in16 = ND % 4 == 0 && (reinterpret_cast<uintptr_t>(a.u_in) & 15) == 0;
+  constexpr int HY = L::HY, RSP = (HX * ND + 6) / 4 * 4;  // staging row stride (floats)
+  static_assert(ND % 4 == 0 || HY * RSP <= 2 * ND * NT, "halo row staging must fit the indicator and u_n regions");
+  __shared__ int sph[HY];
+  const bool aligned = (reinterpret_cast<uintptr_t>(a.u_in) & 15) == 0;
+  const bool in16 = ND % 4 == 0 && aligned;
+  const bool rows16 = ND % 4 != 0 && aligned;
   float* stg = smem + L::OFF_NQ;
   constexpr int NQ4 = ND / 4;
-  if (in16) {
+  if (rows16) {
+    stage_rows16<ND, HX, HY, RSP, NT>(stg, sph, a.u_in, nx, DIM == 2 ? ny : 1, i0 - 1, DIM == 2 ? j0 - 1 : 0, a.perx,
+                                      DIM == 2 && a.pery);
+  } else if (in16) {
     for (int f = threadIdx.x; f < NH * NQ4; f += NT) {
       const int h = f / NQ4, q = f - h * NQ4;
       const int r = DIM == 2 ? h / HX : 0, cc = h - r * HX;
@@ -545,6 +613,14 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
       sc[(4 * q + 1) * NH + h] = v.y;
       sc[(4 * q + 2) * NH + h] = v.z;
       sc[(4 * q + 3) * NH + h] = v.w;
+    }
+    __syncthreads();
+  } else if (rows16) {
+    for (int h = threadIdx.x; h < NH; h += NT) {
+      const int r = DIM == 2 ? h / HX : 0, cc = h - r * HX;
+      const float* src = stg + r * RSP + sph[r] + cc * ND;
+#pragma unroll
+      for (int m = 0; m < ND; ++m) sc[m * NH + h] = src[m];
     }
     __syncthreads();
   }
