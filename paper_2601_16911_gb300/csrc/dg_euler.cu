@@ -137,7 +137,11 @@ struct EulerLayout {
   static constexpr int OFF_SC = 0;                    // [NV][ND][NH] tile + halo, mode-major
   static constexpr int OFF_ST = OFF_SC + NV * ND * NH; // [ND][NVT] density vertex candidates
   static constexpr int OFF_NQ = OFF_ST + ND * NVT;     // [ND][NT] pointwise density indicator
-  static constexpr int FLOATS = OFF_NQ + ND * NT;
+  // halo staging of two variables, cell-major (cells of whole 16-byte chunks only), over
+  // the vertex and indicator regions, which are written after the load
+  static constexpr int OFF_STG = OFF_ST;
+  static constexpr int STG = ND % 4 == 0 ? 2 * NH * ND : 0;
+  static constexpr int FLOATS = OFF_NQ + ND * NT > OFF_STG + STG ? OFF_NQ + ND * NT : OFF_STG + STG;
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
 };
 
@@ -176,6 +180,43 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
   const float g = a.gas_gamma;
 
   // ---- load tile + halo of all variables (asynchronous copies) ---------------------------
+  // Cells of whole 16-byte chunks (Q1, Q3) in a 16-byte-aligned state: 16-byte copies,
+  // two variables at a time, land cell-major in the staging area and are transposed to
+  // the mode-major layout; otherwise 4-byte copies straight into sc.
+  static_assert(L::OFF_STG % 4 == 0, "staging must be 16-byte aligned");
+  if (ND % 4 == 0 && (reinterpret_cast<uintptr_t>(a.u_in) & 15) == 0) {
+    constexpr int NQ4 = ND / 4, NCH = NH * NQ4;
+    float* stg = smem + L::OFF_STG;
+#pragma unroll 1
+    for (int half = 0; half < NV / 2; ++half) {
+      for (int f = threadIdx.x; f < 2 * NCH; f += NT) {
+        const int vv = f / NCH, rem = f - vv * NCH, h = rem / NQ4, q = rem - h * NQ4;
+        const int v = 2 * half + vv, r = h / HX, cc = h - r * HX;
+        int gi = i0 - 1 + cc, gj = j0 - 1 + r;
+        bool ok = true;
+        if (gi < 0 || gi >= nx) {
+          if (a.perx) gi = (gi + nx) % nx; else ok = false;
+        }
+        if (gj < 0 || gj >= ny) {
+          if (a.pery) gj = (gj + ny) % ny; else ok = false;
+        }
+        cp_async16z(stg + 4 * f, ok ? a.u_in + ((size_t)v * ncell + (size_t)gj * nx + gi) * ND + 4 * q : a.u_in,
+                    ok ? 16 : 0);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int f = threadIdx.x; f < 2 * NCH; f += NT) {
+        const int vv = f / NCH, rem = f - vv * NCH, h = rem / NQ4, q = rem - h * NQ4;
+        const float4 x = *reinterpret_cast<const float4*>(stg + 4 * f);
+        float* d = sc + ((2 * half + vv) * ND + 4 * q) * NH + h;
+        d[0] = x.x;
+        d[NH] = x.y;
+        d[2 * NH] = x.z;
+        d[3 * NH] = x.w;
+      }
+      __syncthreads();
+    }
+  } else {
   for (int f = threadIdx.x; f < NV * NH * ND; f += NT) {
     int v = f / (NH * ND);
     int rem0 = f - v * (NH * ND);
@@ -196,6 +237,7 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
   }
   cp_async_wait_all();
   __syncthreads();
+  }
 
   // ---- (a)+(b): density vertex candidates ---------------------------------------------------
   const int act_x = min(TX, nx - i0), act_y = min(TY, ny - j0);
