@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
 
   // ---- nodal values of the tile and its halo (periodic lattice) -------------------------
+  stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);
+  pdl_wait();  // everything below reads or writes what earlier kernels write
   // Node (ix, iy) lands at snode[iy][sph[iy] + ix].  Where the tile's rows do not wrap in x
   // and the state is 16-byte aligned, each row is copied as the 16-byte chunks that cover
   // it: the first chunk starts up to 3 floats early (sph, the row's phase), the last is
@@ -114,7 +116,6 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
       for (int iy = threadIdx.x; iy < NNY; iy += NT) sph[iy] = 0;
     }
   }
-  stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);
   cp_async_wait_all();
   __syncthreads();
   // ---- every halo cell: nodal -> Legendre modes c = (V x V) u_loc -------------------------
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
     }
   }
   __syncthreads();
+  pdl_launch_dependents();
 
   // ---- one thread per own cell ------------------------------------------------------------------
   const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
@@ -683,16 +685,15 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
   const int I0 = blockIdx.x * kNdX, J0 = blockIdx.y * kNdY;
   const float hh = (1.0f / a.two_dx) * (1.0f / a.two_dy), k2 = a.two_dx * a.two_dy;
   if (threadIdx.x < N * N) sM1[threadIdx.x / N][threadIdx.x % N] = (&C.M1[0][0])[threadIdx.x];
-  // this thread's output node and its RK inputs, loaded first so that their latency
-  // overlaps the window (u_n may alias u_out: only this thread reads or writes node j)
+  // this thread's output node; its RK inputs are loaded right after pdl_wait, so that their
+  // latency overlaps the window (u_n may alias u_out: only this thread reads or writes
+  // node j)
   const int tx = threadIdx.x % kNdX, ty = threadIdx.x / kNdX;
   const int I = I0 + tx, J = J0 + ty;
   const bool own = I < nnx && J < nny;
   const size_t j = own ? (size_t)J * nnx + I : 0;
   const bool rk = (a.mode & kModeRK) != 0, with_un = rk && a.rk_a != 0.0f;
   float uin = 0.0f, un = 0.0f;
-  if (own && rk) uin = a.u_in[j];
-  if (own && with_un) un = a.u_n[j];
   // 1 / (m_l wl[l]) of 1D local index l in [0, p)
   auto iml = [&](int l) {
     float v = C.iml[0];
@@ -718,6 +719,9 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
     sly[ry] = bb;
     simly[ry] = iml(bb);
   }
+  pdl_wait();  // everything below reads or writes what earlier kernels write
+  if (own && rk) uin = a.u_in[j];
+  if (own && with_un) un = a.u_n[j];
   __syncthreads();
   // ---- r and du0 on the window: every gather of the thread in flight before the first use -----
   constexpr int NW = (RX * RY + NT - 1) / NT;
@@ -791,6 +795,7 @@ __global__ void __launch_bounds__(kNdX* kNdY, 4)
     sxp[dy * kNdX + ox] = w;
   }
   __syncthreads();
+  pdl_launch_dependents();
   if (!own) return;
   // ---- second sweep: y-pass at this thread's node, and the stage output ----------------------
   const int ay = sly[ty + 2 * P], ly0 = ay == 0 ? P : ay, dy = ty + P;
@@ -828,12 +833,14 @@ cudaError_t launch_cg_t(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   dim3 grid((a.nx + TX - 1) / TX, DIM == 2 ? (a.ny + TY - 1) / TY : 1);
-  k1<<<grid, TX * TY, smem, s>>>(a, T, C);
+  cudaError_t e = launch_pdl(k1, grid, dim3(TX * TY), smem, s, a, T, C);
+  if (e != cudaSuccess) return e;
   if (a.mode & kModeSensorOnly) return cudaGetLastError();
   kernel_mark(m, s);
   if constexpr (DIM == 2) {
     const dim3 ng((a.nnx + kNdX - 1) / kNdX, (a.nny + kNdY - 1) / kNdY);
-    cg_node_stage2d<P><<<ng, kNdX * kNdY, 0, s>>>(a, C);
+    e = launch_pdl(cg_node_stage2d<P>, ng, dim3(kNdX * kNdY), 0, s, a, C);
+    if (e != cudaSuccess) return e;
     kernel_mark(m, s);
   } else {
     const int64_t nn = m->nnode;

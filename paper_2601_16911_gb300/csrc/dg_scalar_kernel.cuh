@@ -28,6 +28,8 @@
 // short loops over modes are unrolled into registers.  All arithmetic is FP32.
 #pragma once
 
+#include <utility>
+
 #include "cvweno_internal.cuh"
 #include "mlp_mma.cuh"
 
@@ -304,6 +306,35 @@ __device__ __forceinline__ float cell_norm0(const DgTables<DIM, P>& T, const flo
     n2 = fmaf(acc, acc, n2);
   }
   return sqrtf(n2);
+}
+
+// Programmatic dependent launch.  A stage kernel launched with programmatic stream
+// serialisation may start while the previous kernel on its stream finishes: before
+// pdl_wait() it touches only data that no kernel of the current step writes (the
+// tabulation image, shared memory); pdl_wait() returns once the previous kernel has
+// completed and its writes are visible.  pdl_launch_dependents() lets the next kernel
+// start once every CTA of this one has passed it.  Both are no-ops without the launch
+// attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// Host: launches kern with programmatic stream serialisation, so that it may start while
+// the previous kernel on stream s finishes (the kernel must call pdl_wait() before it
+// touches anything that kernel writes).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned); the
@@ -649,6 +680,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
   tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
   __syncthreads();
+  pdl_launch_dependents();
 
   // ---- one thread per cell from here on (no further barriers in this tile) -----------------
   const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
@@ -1062,6 +1094,7 @@ template <int DIM, int P, int SYS, int TX, int TY, bool SURR>
 __device__ __forceinline__ void stage_body(const StageArgs& a, const DgTables<DIM, P>& T) {
   extern __shared__ __align__(16) float smem[];
   stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);  // lands with the tile's first wait
+  pdl_wait();  // everything below reads or writes what earlier kernels write
   if constexpr (SURR && DIM == 2) {
     if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY>(a.mlp, smem);
   }
