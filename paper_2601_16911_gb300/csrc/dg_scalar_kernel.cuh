@@ -222,7 +222,16 @@ struct TileLayout {
   static constexpr int OFF_W = OFF_A + Img::W;
   static constexpr int OFF_NQ = OFF_A + Img::FLOATS;              // [ND][NT] pointwise indicators
   static constexpr int OFF_UN = OFF_NQ + ND * NT;                 // u_n of the tile's cells, [ND][NT] or [NT][ND]
-  static constexpr int FLOATS = OFF_UN + ND * NT;
+  // face fluxes of the tile, projected on the tangential modes: x-faces ((TX+1) per tile
+  // row), then y-faces (TX per row, TY+1 rows)
+  // (degree 3 only, from measurements: below, the face work per cell is too small to pay
+  // for the face phase's own law evaluations and its uneven rounds before the barrier; at
+  // p = 4 the batch kernel, at its register cap, lost time)
+  static constexpr bool SHARED_FACES = P == 3;
+  static constexpr int NFP = DIM == 2 ? N : 1;
+  static constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0, NFACE = NFX + NFY;
+  static constexpr int OFF_F = OFF_UN + ND * NT;                  // [NFACE][NFP]
+  static constexpr int FLOATS = OFF_F + (SHARED_FACES ? NFACE * NFP : 0);
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
   // with the surrogate sensor: packed weights, then one 32 x 16 bf16 input block per warp
   static constexpr int OFF_MLP = (FLOATS + 3) / 4 * 4;
@@ -558,6 +567,99 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
   return 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
 }
 
+// Stage (e), faces: every face of the tile once (the cell-wise loop saw each interior face
+// from both sides).  The LLF flux at the face's Gauss nodes minus f(ubar_l) . n, ubar_l the
+// mean of the left/lower cell (of the right/upper one where the left/lower cell is absent
+// at a transmissive boundary, whose ghost is the present cell's trace), projected onto the
+// tangential Legendre modes: sF[face][j] = sum_q w_q P_j(xi_q) F_q.  The right/upper cell
+// adds the difference of the two means' fluxes (mode 0 only).
+template <int DIM, int P, int SYS, int TX, int TY>
+__device__ __forceinline__ void tile_face_phase(const StageArgs& a, const float* sc, const float* sB, const float* sW,
+                                                float* sF, int i0, int j0, int nx, int ny) {
+  using L = TileLayout<DIM, P, TX, TY>;
+  using Law = ScalarLaw<SYS, DIM>;
+  constexpr int N = L::N, NH = L::NH, HX = L::HX, NT = L::NT, NFX = L::NFX, NFACE = L::NFACE, NFP = L::NFP;
+#pragma unroll 1
+  for (int f = threadIdx.x; f < NFACE; f += NT) {
+    int dirn, hl, hr;
+    bool hasl, hasr;
+    if (f < NFX) {
+      const int row = f / (TX + 1), col = f - row * (TX + 1);
+      hl = (DIM == 2 ? (row + 1) * HX : 0) + col;
+      hr = hl + 1;
+      dirn = 0;
+      const int gl = i0 - 1 + col;
+      hasl = a.perx || gl >= 0;
+      hasr = a.perx || gl + 1 < nx;
+    } else {
+      const int g = f - NFX, row = g / TX, col = g - row * TX;
+      hl = row * HX + col + 1;
+      hr = hl + HX;
+      dirn = 1;
+      const int gl = j0 - 1 + row;
+      hasl = a.pery || gl >= 0;
+      hasr = a.pery || gl + 1 < ny;
+    }
+    // traces along the face, relative to each cell's own mean: the left/lower cell meets
+    // the face with its right/upper side (+1), the right/upper cell with its left/lower
+    // side ((-1)^i along the normal)
+    float tl[NFP], tr[NFP];
+#pragma unroll
+    for (int j = 0; j < NFP; ++j) {
+      float sl = 0.0f, sr = 0.0f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int m = DIM == 1 ? i : (dirn == 0 ? i + N * j : j + N * i);
+        if (m == 0) continue;
+        const float vr = sc[m * NH + hr];
+        sl += sc[m * NH + hl];
+        sr += (i & 1) ? -vr : vr;
+      }
+      tl[j] = sl;
+      tr[j] = sr;
+    }
+    float ul = sc[hl], ur = sc[hr];
+    if (!hasl) {
+#pragma unroll
+      for (int j = 0; j < NFP; ++j) tl[j] = tr[j];
+      ul = ur;
+    }
+    if (!hasr) {
+#pragma unroll
+      for (int j = 0; j < NFP; ++j) tr[j] = tl[j];
+      ur = ul;
+    }
+    const Law law(a, ul);
+    const float dm = ur - ul;
+    float h[NFP];
+#pragma unroll
+    for (int j = 0; j < NFP; ++j) h[j] = 0.0f;
+#pragma unroll 1
+    for (int q = 0; q < NFP; ++q) {
+      float vl = tl[0], vr = tr[0];
+      if constexpr (DIM == 2) {
+        vl = vr = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const float bq = sB[q * N + j];
+          vl = fmaf(bq, tl[j], vl);
+          vr = fmaf(bq, tr[j], vr);
+        }
+      }
+      const float F = llf_dev(law, a, ul, vl, dm + vr, dirn);
+      if constexpr (DIM == 2) {
+        const float wq = sW[q] * F;
+#pragma unroll
+        for (int j = 0; j < N; ++j) h[j] = fmaf(wq, sB[q * N + j], h[j]);
+      } else {
+        h[0] = F;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NFP; ++j) sF[f * NFP + j] = h[j];
+  }
+}
+
 // One tile of one stage: the whole path (a)-(e) for the cells [i0, i0+TX) x [j0, j0+TY)
 // (SURR: the instantiation that also runs the surrogate sensor and the features mode; the
 // plain instantiation carries none of that code, so its registers are unaffected)
@@ -679,6 +781,10 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
   tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
+  if constexpr (L::SHARED_FACES) {
+    if (!(a.mode & (kModeSensorOnly | kModeLimit | kModeFeatures)))
+      tile_face_phase<DIM, P, SYS, TX, TY>(a, sc, sB, sW, smem + L::OFF_F, i0, j0, nx, ny);
+  }
   __syncthreads();
   pdl_launch_dependents();
 
@@ -923,86 +1029,125 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 #pragma unroll
   for (int m = 0; m < ND; ++m) r[m] = 0.0f;
   const float mu = (1.0f - gam) * nu;
-  // faces: neighbour traces relative to this cell's mean (ghost = own trace on a
-  // transmissive side)
-  if constexpr (DIM == 1) {
-    const bool hasR = a.perx || gi + 1 < nx, hasL = a.perx || gi > 0;
-    float nbR = trR[0], nbL = trL[0];
-    if (hasR) {
-      float s = 0.0f;
-#pragma unroll
-      for (int m = 1; m < N; ++m) s += (m & 1) ? -sc[m * NH + hc + 1] : sc[m * NH + hc + 1];
-      nbR = (sc[hc + 1] - ubar) + s;
+  if constexpr (L::SHARED_FACES) {
+    // faces, from the tile's face phase: a lower face (left/bottom) was projected relative to
+    // the neighbour's mean, so this cell adds f(ubar_nb) - f(ubar) (mode 0: the integral of
+    // P_j over the face is 2 delta_j0) where that neighbour is present
+    const float* sF = smem + L::OFF_F;
+    if constexpr (DIM == 1) {
+      const bool hasL = a.perx || gi > 0;
+      const float FR = sF[tx + 1];
+      const float FL = sF[tx] + (hasL ? law.flux_dev_dir(sc[hc - 1] - ubar, 0) : 0.0f);
+  #pragma unroll
+      for (int m = 0; m < N; ++m) r[m] = -a.two_dx * (FR - ((m & 1) ? -FL : FL));
+    } else {
+  #pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int dirn = f >> 1;          // 0: x-face, 1: y-face
+        const bool upper = (f & 1) == 0;  // right / top
+        const int fi = dirn == 0 ? ty * (TX + 1) + tx + (upper ? 1 : 0) : L::NFX + (ty + (upper ? 1 : 0)) * TX + tx;
+        float h[N];
+  #pragma unroll
+        for (int j = 0; j < N; ++j) h[j] = sF[fi * N + j];
+        if (!upper && (dirn == 0 ? (a.perx || gi > 0) : (a.pery || gj > 0)))
+          h[0] = fmaf(2.0f, law.flux_dev_dir(sc[hc + (dirn == 0 ? -1 : -HX)] - ubar, dirn), h[0]);
+        // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
+        const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
+  #pragma unroll
+        for (int my = 0; my < N; ++my)
+  #pragma unroll
+          for (int mx = 0; mx < N; ++mx) {
+            const int nrm = dirn == 0 ? mx : my;  // mode index along the normal
+            const float hv = dirn == 0 ? h[my] : h[mx];
+            if (upper)
+              r[mx + N * my] = fmaf(-s2d, hv, r[mx + N * my]);
+            else
+              r[mx + N * my] = fmaf(s2d, (nrm & 1) ? -hv : hv, r[mx + N * my]);
+          }
+      }
     }
-    if (hasL) {
-      float s = 0.0f;
-#pragma unroll
-      for (int m = 1; m < N; ++m) s += sc[m * NH + hc - 1];
-      nbL = (sc[hc - 1] - ubar) + s;
-    }
-    const float FR = llf_dev(law, a, ubar, trR[0], nbR, 0);
-    const float FL = llf_dev(law, a, ubar, nbL, trL[0], 0);
-#pragma unroll
-    for (int m = 0; m < N; ++m) r[m] = -a.two_dx * (FR - ((m & 1) ? -FL : FL));
   } else {
-    // face f: 0 right (+x), 1 left, 2 top (+y), 3 bottom.  The neighbour's trace along
-    // the shared face relative to ubar, a rolled loop over the face nodes, and the
-    // projection onto the tangential modes h[j] = sum_q w_q P_j(xi_q) F_q.
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const int dirn = f >> 1;          // 0: x-face, 1: y-face
-      const bool upper = (f & 1) == 0;  // right / top
-      const int off = dirn == 0 ? (upper ? 1 : -1) : (upper ? HX : -HX);
-      const bool has = dirn == 0 ? (a.perx || (upper ? gi + 1 < nx : gi > 0))
-                                 : (a.pery || (upper ? gj + 1 < ny : gj > 0));
-      const float* own = dirn == 0 ? (upper ? trR : trL) : (upper ? trT : trB);
-      float nb[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
+    // faces: neighbour traces relative to this cell's mean (ghost = own trace on a
+    // transmissive side)
+    if constexpr (DIM == 1) {
+      const bool hasR = a.perx || gi + 1 < nx, hasL = a.perx || gi > 0;
+      float nbR = trR[0], nbL = trL[0];
+      if (hasR) {
         float s = 0.0f;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const int m = dirn == 0 ? i + N * j : j + N * i;
-          if (m == 0) continue;
-          const float v = sc[m * NH + hc + off];
-          // the neighbour meets this face with its opposite side: sign (-1)^i on a
-          // right/top face (its left/bottom side), +1 on a left/bottom face
-          s += (upper && (i & 1)) ? -v : v;
-        }
-        nb[j] = s;
+  #pragma unroll
+        for (int m = 1; m < N; ++m) s += (m & 1) ? -sc[m * NH + hc + 1] : sc[m * NH + hc + 1];
+        nbR = (sc[hc + 1] - ubar) + s;
       }
-      const float dmean = has ? sc[hc + off] - ubar : 0.0f;
-      float h[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) h[j] = 0.0f;
-#pragma unroll 1
-      for (int q = 0; q < N; ++q) {
-        float vo = 0.0f, vn = 0.0f;
-#pragma unroll
+      if (hasL) {
+        float s = 0.0f;
+  #pragma unroll
+        for (int m = 1; m < N; ++m) s += sc[m * NH + hc - 1];
+        nbL = (sc[hc - 1] - ubar) + s;
+      }
+      const float FR = llf_dev(law, a, ubar, trR[0], nbR, 0);
+      const float FL = llf_dev(law, a, ubar, nbL, trL[0], 0);
+  #pragma unroll
+      for (int m = 0; m < N; ++m) r[m] = -a.two_dx * (FR - ((m & 1) ? -FL : FL));
+    } else {
+      // face f: 0 right (+x), 1 left, 2 top (+y), 3 bottom.  The neighbour's trace along
+      // the shared face relative to ubar, a rolled loop over the face nodes, and the
+      // projection onto the tangential modes h[j] = sum_q w_q P_j(xi_q) F_q.
+  #pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int dirn = f >> 1;          // 0: x-face, 1: y-face
+        const bool upper = (f & 1) == 0;  // right / top
+        const int off = dirn == 0 ? (upper ? 1 : -1) : (upper ? HX : -HX);
+        const bool has = dirn == 0 ? (a.perx || (upper ? gi + 1 < nx : gi > 0))
+                                   : (a.pery || (upper ? gj + 1 < ny : gj > 0));
+        const float* own = dirn == 0 ? (upper ? trR : trL) : (upper ? trT : trB);
+        float nb[N];
+  #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const float bq = sB[q * N + j];
-          vo = fmaf(bq, own[j], vo);
-          vn = fmaf(bq, nb[j], vn);
+          float s = 0.0f;
+  #pragma unroll
+          for (int i = 0; i < N; ++i) {
+            const int m = dirn == 0 ? i + N * j : j + N * i;
+            if (m == 0) continue;
+            const float v = sc[m * NH + hc + off];
+            // the neighbour meets this face with its opposite side: sign (-1)^i on a
+            // right/top face (its left/bottom side), +1 on a left/bottom face
+            s += (upper && (i & 1)) ? -v : v;
+          }
+          nb[j] = s;
         }
-        vn = has ? dmean + vn : vo;
-        const float F = upper ? llf_dev(law, a, ubar, vo, vn, dirn) : llf_dev(law, a, ubar, vn, vo, dirn);
-        const float wq = sW[q] * F;
-#pragma unroll
-        for (int j = 0; j < N; ++j) h[j] = fmaf(wq, sB[q * N + j], h[j]);
+        const float dmean = has ? sc[hc + off] - ubar : 0.0f;
+        float h[N];
+  #pragma unroll
+        for (int j = 0; j < N; ++j) h[j] = 0.0f;
+  #pragma unroll 1
+        for (int q = 0; q < N; ++q) {
+          float vo = 0.0f, vn = 0.0f;
+  #pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const float bq = sB[q * N + j];
+            vo = fmaf(bq, own[j], vo);
+            vn = fmaf(bq, nb[j], vn);
+          }
+          vn = has ? dmean + vn : vo;
+          const float F = upper ? llf_dev(law, a, ubar, vo, vn, dirn) : llf_dev(law, a, ubar, vn, vo, dirn);
+          const float wq = sW[q] * F;
+  #pragma unroll
+          for (int j = 0; j < N; ++j) h[j] = fmaf(wq, sB[q * N + j], h[j]);
+        }
+        // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
+        const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
+  #pragma unroll
+        for (int my = 0; my < N; ++my)
+  #pragma unroll
+          for (int mx = 0; mx < N; ++mx) {
+            const int nrm = dirn == 0 ? mx : my;  // mode index along the normal
+            const float hv = dirn == 0 ? h[my] : h[mx];
+            if (upper)
+              r[mx + N * my] = fmaf(-s2d, hv, r[mx + N * my]);
+            else
+              r[mx + N * my] = fmaf(s2d, (nrm & 1) ? -hv : hv, r[mx + N * my]);
+          }
       }
-      // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
-      const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
-#pragma unroll
-      for (int my = 0; my < N; ++my)
-#pragma unroll
-        for (int mx = 0; mx < N; ++mx) {
-          const int nrm = dirn == 0 ? mx : my;  // mode index along the normal
-          const float hv = dirn == 0 ? h[my] : h[mx];
-          if (upper)
-            r[mx + N * my] = fmaf(-s2d, hv, r[mx + N * my]);
-          else
-            r[mx + N * my] = fmaf(s2d, (nrm & 1) ? -hv : hv, r[mx + N * my]);
-        }
     }
   }
   // volume: flux deviation and alpha-weighted viscous term, projected by sum factorisation
