@@ -549,8 +549,14 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
       for (int aa = 0; aa < N; ++aa) r[aa] = fmaf(fy, C.wl[aa] * hdx, r[aa]);
     }
   }
+  if constexpr (ND % 4 == 0) {  // rloc is mesh-owned (aligned): 16-byte stores
 #pragma unroll
-  for (int m = 0; m < ND; ++m) a.rloc[cell * ND + m] = r[m];
+    for (int q = 0; q < ND / 4; ++q)
+      reinterpret_cast<float4*>(a.rloc + cell * ND)[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < ND; ++m) a.rloc[cell * ND + m] = r[m];
+  }
 }
 
 // Nodal assembly r_j at lattice node (I, J), 0 <= I < nnx, 0 <= J < nny: the sum of the

@@ -1210,7 +1210,8 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
         r[mx + N * my] = v;
       }
   }
-  // M^{-1} and output
+  // M^{-1} and output (into r); 16-byte stores where the cell is whole 16-byte chunks and
+  // the output is 16-byte aligned
   bool bad = false;
   float* out = a.u_out + cell * ND;
   const float* sUn = smem + L::OFF_UN;  // u_n of this cell
@@ -1227,10 +1228,17 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
         const float un = un16 ? sUn[threadIdx.x * ND + m] : sUn[m * NT + threadIdx.x];
         v = fmaf(a.rk_b, v - un, un);
       }
-      out[m] = v;
-    } else {
-      out[m] = d;
+      d = v;
     }
+    r[m] = d;
+  }
+  if (ND % 4 == 0 && (reinterpret_cast<uintptr_t>(a.u_out) & 15) == 0) {
+#pragma unroll
+    for (int q = 0; q < ND / 4; ++q)
+      reinterpret_cast<float4*>(out)[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < ND; ++m) out[m] = r[m];
   }
   if (bad) atomicOr(a.status, kStatNonfinite);
 }
