@@ -579,8 +579,10 @@ __device__ __forceinline__ void tile_face_phase(const StageArgs& a, const float*
   using L = TileLayout<DIM, P, TX, TY>;
   using Law = ScalarLaw<SYS, DIM>;
   constexpr int N = L::N, NH = L::NH, HX = L::HX, NT = L::NT, NFX = L::NFX, NFACE = L::NFACE, NFP = L::NFP;
+  // faces from the block's last thread backwards: the vertex phase's extra round falls on
+  // the first warp, the face phase's on the last
 #pragma unroll 1
-  for (int f = threadIdx.x; f < NFACE; f += NT) {
+  for (int f = NT - 1 - threadIdx.x; f < NFACE; f += NT) {
     int dirn, hl, hr;
     bool hasl, hasr;
     if (f < NFX) {
