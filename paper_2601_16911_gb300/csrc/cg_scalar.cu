@@ -215,7 +215,9 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
     // faces the tile (l = P below it, 0 above), the left and right columns the node
     // column a = l (P left of it, 0 right)
     constexpr int NR = 2 * HX + 2 * TY;
-    for (int r = threadIdx.x; r < NR; r += NT) {
+    // from the block's last thread backwards: the vertex phase's extra round falls on the
+    // first warp, the ring on the last ones
+    for (int r = NT - 1 - threadIdx.x; r < NR; r += NT) {
       const bool row = r < 2 * HX;
       int hx, hy, l;
       if (row) {
