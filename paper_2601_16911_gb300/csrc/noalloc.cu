@@ -306,10 +306,12 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   float* u1 = slots.scratch;
   float* u2 = slots.scratch + kStaticStateFloats;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the tabulation image first: the stage kernels read it before their dependent-launch
+  // wait, so a stream operation that is not one of them (the status reset) separates them
+  if (launch_tab_image(m.dim, m.p, m.tables, slots.tab_image, s) != cudaSuccess) return CVWENO_ERR_CUDA;
   // the status word must start at zero for this step; the stage buffers are fully
   // written before they are read
   if (cudaMemsetAsync(slots.status, 0, sizeof(int), s) != cudaSuccess) return CVWENO_ERR_CUDA;
-  if (launch_tab_image(m.dim, m.p, m.tables, slots.tab_image, s) != cudaSuccess) return CVWENO_ERR_CUDA;
 
   StageArgs a;
   memset(&a, 0, sizeof(a));
