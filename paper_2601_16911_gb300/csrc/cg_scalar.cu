@@ -669,11 +669,11 @@ __global__ void cg_node_sweep(const __grid_constant__ StageArgs a, const __grid_
 // x (each node sums M1[local][b] du over the nodes of the up to two cells containing it),
 // then along y.  The halo values are recomputed by every tile that needs them, in the same
 // arithmetic, so neighbouring tiles agree bitwise.
-constexpr int kNdX = 32, kNdY = 16;
+constexpr int kNdX = 32, kNdY = 32;
 
 
 template <int P>
-__global__ void __launch_bounds__(kNdX* kNdY, 4)
+__global__ void __launch_bounds__(kNdX* kNdY, 2)
     cg_node_stage2d(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<2, P> C) {
   constexpr int N = P + 1, NT = kNdX * kNdY;
   constexpr int RX = kNdX + 4 * P, RY = kNdY + 4 * P;  // r and du0 window (halo 2p)
