@@ -25,7 +25,12 @@
  *     mode, 1D: k = kx).  The library never frees caller memory.
  *   - Host pointers are marked "host".  Streams are cudaStream_t passed as void*;
  *     NULL means the legacy default stream.  Work is stream-ordered; an entry point
- *     only synchronises where it says so.
+ *     only synchronises where it says so.  The scalar stage kernels are launched with
+ *     programmatic dependent launch: one may start while the previous kernel on the
+ *     stream (the caller's included) finishes, but it reads or writes no memory that
+ *     kernel can touch until that kernel has completed.  A caller kernel launched with
+ *     the same attribute right after them must wait likewise before reading their
+ *     output.
  *   - Errors are returned as cvweno_status; nothing is thrown across the ABI.
  *     Kernels report non-finite values and non-positive density/pressure through a
  *     device status word that cvweno_status_check() (and every synchronising
