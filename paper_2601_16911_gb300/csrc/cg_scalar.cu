@@ -761,46 +761,92 @@ __global__ void __launch_bounds__(kNdX* kNdY, 2)
     }
   }
   __syncthreads();
-  // ---- first sweep: x-pass over the rows of the window, columns of the du1 window ----------
-  for (int f = threadIdx.x; f < RY * DX; f += NT) {
-    const int ry = f / DX, cx = f - ry * DX, rx = cx + P;
-    const int ax = slx[rx], lx0 = ax == 0 ? P : ax;
+  // The passes work cell by cell: a cell's p+1 nodes along the pass direction (and the p
+  // nodes of the cell before it, for the node shared by both) are read once, and its p
+  // outputs follow with compile-time local indices: output a of the cell sums
+  // M1[a][b] over the cell's nodes, plus M1[p][b] over the previous cell's for a = 0.
+  // Segment s of a line starts at the cell whose local node 0 sits at source index
+  // z = out0 - a0 + s p (a0: the local index of the line's first output); the products
+  // are taken in the same order as node by node, so the results are the same bits.
+  auto cell_pass = [&](const float (&v)[2 * P + 1], int a) {
     float w = 0.0f;
+    if (a == 0) {
 #pragma unroll
-    for (int b = 0; b <= P; ++b) w = fmaf(sM1[lx0][b], sd0[ry][rx - lx0 + b], w);
-    if (ax == 0) {
+      for (int b = 0; b <= P; ++b) w = fmaf(C.M1[P][b], v[b], w);
 #pragma unroll
-      for (int b = 0; b <= P; ++b) w = fmaf(sM1[0][b], sd0[ry][rx + b], w);
+      for (int b = 0; b <= P; ++b) w = fmaf(C.M1[0][b], v[P + b], w);
+    } else {
+#pragma unroll
+      for (int aa = 1; aa < P; ++aa)
+        if (aa == a) {
+#pragma unroll
+          for (int b = 0; b <= P; ++b) w = fmaf(C.M1[aa][b], v[P + b], w);
+        }
     }
-    sxp[ry * DX + cx] = w;
+    return w;
+  };
+  // ---- first sweep: x-pass over the rows of the window, columns of the du1 window ----------
+  {
+    constexpr int NSEG = (DX + P - 1) / P + 1;
+    const int a0 = slx[P];
+    for (int f = threadIdx.x; f < RY * NSEG; f += NT) {
+      const int ry = f / NSEG, sg = f - ry * NSEG, z = P - a0 + sg * P;  // r-window column of node 0
+      float v[2 * P + 1];
+#pragma unroll
+      for (int j = 0; j <= 2 * P; ++j) {
+        const int col = z - P + j;
+        v[j] = col >= 0 && col < RX ? sd0[ry][col] : 0.0f;
+      }
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        const int cx = z - P + a;  // du1-window column
+        if (cx >= 0 && cx < DX) sxp[ry * DX + cx] = cell_pass(v, a);
+      }
+    }
   }
   __syncthreads();
   // ---- first sweep: y-pass and du1 -----------------------------------------------------------
-  for (int f = threadIdx.x; f < DY * DX; f += NT) {
-    const int dy = f / DX, cx = f - dy * DX, ry = dy + P, rx = cx + P;
-    const int ay = sly[ry], ly0 = ay == 0 ? P : ay;
-    float mc = 0.0f;
+  {
+    constexpr int NSEG = (DY + P - 1) / P + 1;
+    const int b0 = sly[P];
+    for (int f = threadIdx.x; f < DX * NSEG; f += NT) {
+      const int cx = f / NSEG, sg = f - cx * NSEG, z = P - b0 + sg * P;  // r-window row of node 0
+      const int rx = cx + P;
+      float v[2 * P + 1];
 #pragma unroll
-    for (int d = 0; d <= P; ++d) mc = fmaf(sM1[ly0][d], sxp[(ry - ly0 + d) * DX + cx], mc);
-    if (ay == 0) {
+      for (int j = 0; j <= 2 * P; ++j) {
+        const int row = z - P + j;
+        v[j] = row >= 0 && row < RY ? sxp[row * DX + cx] : 0.0f;
+      }
 #pragma unroll
-      for (int d = 0; d <= P; ++d) mc = fmaf(sM1[0][d], sxp[(ry + d) * DX + cx], mc);
+      for (int a = 0; a < P; ++a) {
+        const int dy = z - P + a, ry = dy + P;
+        if (dy >= 0 && dy < DY) {
+          const float mc = cell_pass(v, a);
+          sd1[dy][cx] = sd0[ry][rx] + (sr[ry][rx] - mc * hh) * (simlx[rx] * simly[ry] * k2);
+        }
+      }
     }
-    sd1[dy][cx] = sd0[ry][rx] + (sr[ry][rx] - mc * hh) * (simlx[rx] * simly[ry] * k2);
   }
   __syncthreads();
   // ---- second sweep: x-pass over the du1 window's rows, the tile's columns ------------------
-  for (int f = threadIdx.x; f < DY * kNdX; f += NT) {
-    const int dy = f / kNdX, ox = f - dy * kNdX, cx = ox + P;
-    const int ax = slx[ox + 2 * P], lx0 = ax == 0 ? P : ax;
-    float w = 0.0f;
+  {
+    constexpr int NSEG = (kNdX + P - 1) / P + 1;
+    const int a0 = slx[2 * P];
+    for (int f = threadIdx.x; f < DY * NSEG; f += NT) {
+      const int dy = f / NSEG, sg = f - dy * NSEG, z = P - a0 + sg * P;  // du1-window column of node 0
+      float v[2 * P + 1];
 #pragma unroll
-    for (int b = 0; b <= P; ++b) w = fmaf(sM1[lx0][b], sd1[dy][cx - lx0 + b], w);
-    if (ax == 0) {
+      for (int j = 0; j <= 2 * P; ++j) {
+        const int col = z - P + j;
+        v[j] = col >= 0 && col < DX ? sd1[dy][col] : 0.0f;
+      }
 #pragma unroll
-      for (int b = 0; b <= P; ++b) w = fmaf(sM1[0][b], sd1[dy][cx + b], w);
+      for (int a = 0; a < P; ++a) {
+        const int ox = z - P + a;
+        if (ox >= 0 && ox < kNdX) sxp[dy * kNdX + ox] = cell_pass(v, a);
+      }
     }
-    sxp[dy * kNdX + ox] = w;
   }
   __syncthreads();
   pdl_launch_dependents();
