@@ -669,12 +669,16 @@ __global__ void cg_node_sweep(const __grid_constant__ StageArgs a, const __grid_
 // x (each node sums M1[local][b] du over the nodes of the up to two cells containing it),
 // then along y.  The halo values are recomputed by every tile that needs them, in the same
 // arithmetic, so neighbouring tiles agree bitwise.
-constexpr int kNdX = 32, kNdY = 32;
+// 32x32 tiles of 1024 threads from p = 3 on, 32x16 of 512 threads below (measured)
+constexpr int kNdX = 32;
+template <int P>
+__host__ __device__ constexpr int node_tile_y() { return P >= 3 ? 32 : 16; }
 
 
 template <int P>
-__global__ void __launch_bounds__(kNdX* kNdY, 2)
+__global__ void __launch_bounds__(kNdX* node_tile_y<P>(), 2048 / (kNdX * node_tile_y<P>()))
     cg_node_stage2d(const __grid_constant__ StageArgs a, const __grid_constant__ CgTables<2, P> C) {
+  constexpr int kNdY = node_tile_y<P>();
   constexpr int N = P + 1, NT = kNdX * kNdY;
   constexpr int RX = kNdX + 4 * P, RY = kNdY + 4 * P;  // r and du0 window (halo 2p)
   constexpr int DX = kNdX + 2 * P, DY = kNdY + 2 * P;  // du1 window (halo p)
@@ -892,6 +896,7 @@ cudaError_t launch_cg_t(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t
   if (a.mode & kModeSensorOnly) return cudaGetLastError();
   kernel_mark(m, s);
   if constexpr (DIM == 2) {
+    constexpr int kNdY = node_tile_y<P>();
     const dim3 ng((a.nnx + kNdX - 1) / kNdX, (a.nny + kNdY - 1) / kNdY);
     e = launch_pdl(cg_node_stage2d<P>, ng, dim3(kNdX * kNdY), 0, s, a, C);
     if (e != cudaSuccess) return e;
