@@ -41,7 +41,10 @@ __device__ __forceinline__ float ipowf(float x, int r) {
   return y;
 }
 
-__device__ __forceinline__ float powq(float x, float q) { return q == 1.0f ? x : powf(x, q); }
+// The general power is out of line: it is cold at the paper's q = 1, and inlined at every
+// call site it crowds the instruction cache of the stage kernels.
+static __device__ __noinline__ float powf_cold(float x, float q) { return powf(x, q); }
+__device__ __forceinline__ float powq(float x, float q) { return q == 1.0f ? x : powf_cold(x, q); }
 
 // ---- scalar fluxes, evaluated as deviations from the cell mean -------------------------
 // A law object is built per cell from its mean ubar.  flux_dev returns
