@@ -1265,10 +1265,11 @@ __global__ void __launch_bounds__(TX* TY)
   stage_body<DIM, P, SYS, TX, TY, false>(a, T);
 }
 
-// The surrogate instantiation is held to the register budget of 4 resident CTAs (3 at
-// p = 4), which the network's fragments would otherwise exceed.
+// The surrogate instantiation is held to the register budget of 5 resident CTAs below
+// p = 3 (its shared memory allows 5), 4 at p = 3 and 3 at p = 4, which the network's
+// fragments would otherwise exceed.
 template <int DIM, int P, int SYS, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, (P >= 4 ? 3 : 4) * (128 / (TX * TY)))
+__global__ void __launch_bounds__(TX* TY, (P >= 4 ? 3 : P == 3 ? 4 : 5) * (128 / (TX * TY)))
     dg_scalar_stage_surrogate(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
   stage_body<DIM, P, SYS, TX, TY, true>(a, T);
 }
