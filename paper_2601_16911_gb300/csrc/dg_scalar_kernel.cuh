@@ -227,10 +227,11 @@ struct TileLayout {
   static constexpr int OFF_UN = OFF_NQ + ND * NT;                 // u_n of the tile's cells, [ND][NT] or [NT][ND]
   // face fluxes of the tile, projected on the tangential modes: x-faces ((TX+1) per tile
   // row), then y-faces (TX per row, TY+1 rows)
-  // (degree 3 only, from measurements: below, the face work per cell is too small to pay
-  // for the face phase's own law evaluations and its uneven rounds before the barrier; at
-  // p = 4 the batch kernel, at its register cap, lost time)
-  static constexpr bool SHARED_FACES = P == 3;
+  // (degrees 2 and 3, from measurements: at p = 1 the face work per cell is too small to
+  // pay for the face phase's own law evaluations and its uneven rounds before the
+  // barrier; at p = 4 the batch kernel, at its register cap, lost time; the surrogate
+  // instantiation at p = 2, held to 96 registers, keeps the cell-wise faces)
+  static constexpr bool SHARED_FACES = P == 2 || P == 3;
   static constexpr int NFP = DIM == 2 ? N : 1;
   static constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0, NFACE = NFX + NFY;
   static constexpr int OFF_F = OFF_UN + ND * NT;                  // [NFACE][NFP]
@@ -786,7 +787,8 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
   tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
-  if constexpr (L::SHARED_FACES) {
+  constexpr bool kSharedFaces = L::SHARED_FACES && !(SURR && P == 2);
+  if constexpr (kSharedFaces) {
     if (!(a.mode & (kModeSensorOnly | kModeLimit | kModeFeatures)))
       tile_face_phase<DIM, P, SYS, TX, TY>(a, sc, sB, sW, smem + L::OFF_F, i0, j0, nx, ny);
   }
@@ -1034,7 +1036,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
 #pragma unroll
   for (int m = 0; m < ND; ++m) r[m] = 0.0f;
   const float mu = (1.0f - gam) * nu;
-  if constexpr (L::SHARED_FACES) {
+  if constexpr (kSharedFaces) {
     // faces, from the tile's face phase: a lower face (left/bottom) was projected relative to
     // the neighbour's mean, so this cell adds f(ubar_nb) - f(ubar) (mode 0: the integral of
     // P_j over the face is 2 delta_j0) where that neighbour is present
