@@ -197,9 +197,17 @@ def measured_peaks():
 # Algorithmic work per cell and stage, sum-factorised FMA counts of the method's steps for
 # 2D scalar DG Q_p with n = p+1 (stage d only in troubled cells):
 #   (a) 8n^3 + 4n^2, (b) 4n^2, (c) 8n^3 + 6n^4, (d) 2n^5, (e) 14n^3 + 20n^2.
+def fma_face_terms(p: int) -> float:
+    """The face part of stage (e): trace, flux and lift on the cell's four sides, each
+    side once (the shared-face phase evaluates each face once, both sides' traces)."""
+    n = p + 1
+    return 20 * n**2
+
+
 def fma_per_cell(p: int, troubled_fraction: float) -> float:
     n = p + 1
-    return (8 * n**3 + 4 * n**2) + 4 * n**2 + (8 * n**3 + 6 * n**4) + troubled_fraction * 2 * n**5 + (14 * n**3 + 20 * n**2)
+    return ((8 * n**3 + 4 * n**2) + 4 * n**2 + (8 * n**3 + 6 * n**4) + troubled_fraction * 2 * n**5
+            + 14 * n**3 + fma_face_terms(p))
 
 
 def fma_per_cell_euler(p: int, troubled_fraction: float) -> float:
@@ -212,8 +220,8 @@ def fma_per_cell_euler(p: int, troubled_fraction: float) -> float:
 
 
 def fma_per_cell_cg_cells(p: int, troubled_fraction: float) -> float:
-    """The CG cell kernel: the DG count of stages (a)-(e) without faces' extra terms,
-    plus the nodal -> modal map of the tile and halo cells (2n^3 each; 180 halo cells per
+    """The CG cell kernel: the DG count of stages (a)-(e) less the face part of (e) (a
+    continuous solution has no face fluxes), plus the nodal -> modal map of the tile and halo cells (2n^3 each; 180 halo cells per
     128-cell tile), the local integrals int phi grad u of the tile's cells (4n^3 each, by
     tensor factors) and of the 52 halo-ring cells on the node row or column they share
     with the tile (4n^2 each), and P_h grad u at the cell's Gauss points (4n^3) and nodes
@@ -221,7 +229,7 @@ def fma_per_cell_cg_cells(p: int, troubled_fraction: float) -> float:
     n = p + 1
     halo = 180.0 / 128.0
     ring = 52.0 / 128.0
-    return (fma_per_cell(p, troubled_fraction) + halo * 2 * n**3 + 4 * n**3 + ring * 4 * n**2 + 4 * n**3
+    return (fma_per_cell(p, troubled_fraction) - fma_face_terms(p) + halo * 2 * n**3 + 4 * n**3 + ring * 4 * n**2 + 4 * n**3
             + 8 * n**2)
 
 
