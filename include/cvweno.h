@@ -188,7 +188,10 @@ cvweno_status cvweno_residual(cvweno_mesh m, const float* u, float* dudt, void* 
  * dt_used (host, may be NULL) receives the step size. */
 cvweno_status cvweno_step(cvweno_mesh m, float* u, double dt, double cfl, double* dt_used, void* stream);
 
-/* nsteps SSP-RK3 steps of fixed size dt > 0, enqueued without synchronisation. */
+/* nsteps SSP-RK3 steps of fixed size dt > 0, enqueued without synchronisation.  A 1D
+ * scalar DG mesh of at most 128 cells without a limiter (one tile) runs all the steps of
+ * the call in one kernel launch (cvweno_step: its one step), unless kernel timing is on;
+ * the results are bitwise those of one launch per stage. */
 cvweno_status cvweno_advance(cvweno_mesh m, float* u, double dt, int nsteps, void* stream);
 
 /* FP64 totals sum_e int_{K_e} u_h of every conserved variable into totals[nvars]
@@ -229,7 +232,8 @@ cvweno_status cvweno_positivity(cvweno_mesh m, const float* u, float* out, float
  * captured from such a step times each of its replays.  cvweno_kernel_times waits for
  * the last recorded event and writes the durations (ms) of the kernels of the most
  * recent step into ms[capacity] (host), in launch order: DG and Euler one per stage
- * (two with the HWENO or positivity limiter), CG two per stage in 2D (cells, then the
+ * (two with the HWENO or positivity limiter; with timing on, a one-tile 1D mesh also
+ * launches stage by stage), CG two per stage in 2D (cells, then the
  * node phase: assembly and both defect-correction sweeps) and four in 1D (cells, node
  * right-hand side, two sweeps); *count receives how many were written.  Timing
  * costs one event record per kernel; turn it off (enable 0) for production runs.  Turning it off keeps the events

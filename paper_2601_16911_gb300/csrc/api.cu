@@ -300,7 +300,35 @@ cvweno_status positivity_stage(cvweno_mesh m, float* x, cudaStream_t s) {
   return cuda_status(e);
 }
 
+// A 1D scalar DG mesh of one tile without a limiter runs its steps in one launch, unless
+// kernel timing asks for the stages one by one.
+bool steps_in_one_launch(cvweno_mesh m) {
+  return m->dim == 1 && m->kind != CVWENO_CG && m->desc.system != CVWENO_EULER && !m->desc.params.positivity &&
+         !m->desc.params.hweno_limiter && !m->timing && m->nx <= kTile1D;
+}
+
+cvweno_status enqueue_steps_one_launch(cvweno_mesh m, float* u, float dt, int nsteps, cudaStream_t s) {
+  StepArgs sa;
+  const float* in[3] = {u, m->d_u1, m->d_u2};
+  float* out[3] = {m->d_u1, m->d_u2, u};
+  const float ra[3] = {0.0f, 0.75f, 1.0f / 3.0f}, rb[3] = {1.0f, 0.25f, 2.0f / 3.0f};
+  for (int k = 0; k < 3; ++k) {
+    StageArgs& a = sa.st[k];
+    a = base_args(m);
+    a.u_in = in[k];
+    a.u_n = u;
+    a.u_out = out[k];
+    a.rk_a = ra[k];
+    a.rk_b = rb[k];
+    a.dt = dt;
+    a.mode = kModeRK;
+  }
+  sa.nsteps = nsteps;
+  return cuda_status(launch_steps_1d_tile(m, sa, s));
+}
+
 cvweno_status enqueue_step(cvweno_mesh m, float* u, float dt, cudaStream_t s) {
+  if (steps_in_one_launch(m)) return enqueue_steps_one_launch(m, u, dt, 1, s);
   if (m->desc.params.positivity) {
     // every stage result is limited in place (reading P3): the limiter is cell-local
     if (m->timing) {
@@ -684,6 +712,7 @@ cvweno_status cvweno_step(cvweno_mesh m, float* u, double dt, double cfl, double
 
 cvweno_status cvweno_advance(cvweno_mesh m, float* u, double dt, int nsteps, void* stream) {
   if (!m || !u || !(dt > 0.0) || nsteps < 0) return CVWENO_ERR_ARG;
+  if (nsteps > 0 && steps_in_one_launch(m)) return enqueue_steps_one_launch(m, u, (float)dt, nsteps, S(stream));
   for (int i = 0; i < nsteps; ++i) {
     cvweno_status st = enqueue_step(m, u, (float)dt, S(stream));
     if (st != CVWENO_OK) return st;

@@ -149,6 +149,16 @@ struct StageArgs {
   float* du2;   // [nnode] second defect-correction iterate (1D)
 };
 
+// The three SSP-RK3 stages of a step, each a full StageArgs (kModeRK), repeated nsteps
+// times by the one-launch step kernel of a 1D mesh that is a single tile.
+struct StepArgs {
+  StageArgs st[3];
+  int nsteps;
+};
+
+// Cells of a 1D tile: a 1D DG mesh of at most this many cells is one CTA.
+constexpr int kTile1D = 128;
+
 enum : int {
   kModeResidual = 1,   // write dudt to u_out
   kModeRK = 2,         // write u_n + rk_b (u_in + dt L - u_n) (or u_in + dt L) to u_out
@@ -216,6 +226,9 @@ void legendre_values(double x, int mmax, double* out);  // P_0..P_mmax at x
 // dg_scalar.cu / dg_euler.cu
 cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_euler(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);
+// dg_scalar_1d.cu: nsteps whole SSP-RK3 steps of a 1D scalar DG mesh of at most kTile1D
+// cells in one launch (cudaErrorNotSupported for any other mesh)
+cudaError_t launch_steps_1d_tile(const cvweno_mesh_s* m, const StepArgs& a, cudaStream_t s);
 // dg_euler.cu: the positivity limiter on a.u_in -> a.u_out (may alias), theta per cell
 cudaError_t launch_positivity(const cvweno_mesh_s* m, const StageArgs& a, float* theta, cudaStream_t s);
 // dg_scalar_2d.cu: writes TabImage<dim, p> of the host tables t (DgTables<dim, p>) to

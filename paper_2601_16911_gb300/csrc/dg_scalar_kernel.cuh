@@ -420,11 +420,11 @@ __device__ __forceinline__ void stage_rows16(float* dst, int* ph, const float* s
 }
 
 // Starts the copy of the tabulation image img (device, TabImage<DIM, P>) into shared
-// memory; it lands with the tile's first cp.async wait.
-template <int DIM, int P, int TX, int TY>
+// memory; it lands with the tile's first cp.async wait.  NB: threads of the block.
+template <int DIM, int P, int TX, int TY, int NB = TX * TY>
 __device__ __forceinline__ void stage_tables_to_smem(const float* img, float* smem) {
   using L = TileLayout<DIM, P, TX, TY>;
-  for (int f = threadIdx.x; f < TabImage<DIM, P>::FLOATS / 4; f += L::NT) cp_async16(smem + L::OFF_A + 4 * f, img + 4 * f);
+  for (int f = threadIdx.x; f < TabImage<DIM, P>::FLOATS / 4; f += NB) cp_async16(smem + L::OFF_A + 4 * f, img + 4 * f);
 }
 
 // Writes TabImage<DIM, P> of T to img (one block; run once per mesh, off the stage path).
@@ -452,13 +452,14 @@ __global__ void tab_image_kernel(const __grid_constant__ DgTables<DIM, P> T, flo
 
 // Stages (a)+(b) for the tile's vertices, from the halo coefficients sc (mode-major):
 // vertex candidates t* into st, and (optionally) the physical vertex data to tstar_out.
-template <int DIM, int P, int TX, int TY>
+// NB threads of the block share the vertices.
+template <int DIM, int P, int TX, int TY, int NB = TX * TY>
 __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTables<DIM, P>& T, const float* sc,
                                                   float* st, int i0, int j0, int nx, int ny) {
   using L = TileLayout<DIM, P, TX, TY>;
-  constexpr int ND = L::ND, NC = L::NC, NT = L::NT, HX = L::HX, NH = L::NH, VXT = L::VXT, NVT = L::NVT;
+  constexpr int ND = L::ND, NC = L::NC, HX = L::HX, NH = L::NH, VXT = L::VXT, NVT = L::NVT;
   const int act_x = min(TX, nx - i0), act_y = DIM == 2 ? min(TY, ny - j0) : 1;
-  for (int v = threadIdx.x; v < NVT; v += NT) {
+  for (int v = threadIdx.x; v < NVT; v += NB) {
     int va = v % VXT, vb = DIM == 2 ? v / VXT : 0;
     if (va > act_x || (DIM == 2 && vb > act_y)) continue;
     float acc[ND];
@@ -471,7 +472,7 @@ __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTa
     const float* base = sc + (DIM == 2 ? vb * HX : 0) + va;
     // slots SW, SE, NW, NE: the cell right of / above the vertex touches it with its
     // left / lower corner (sign -1), the cell left of / below with its right / upper one
-#pragma unroll 1
+#pragma unroll (DIM == 1 ? NC : 1)
     for (int s = 0; s < NC; ++s) {
       const int ex = s & 1, ey = (s >> 1) & 1;
       if (!((ex ? has_e : has_w) && (ey ? has_n : has_s))) continue;
@@ -527,7 +528,7 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
 #pragma unroll
   for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
   float osum = om0;
-#pragma unroll 1
+#pragma unroll (DIM == 1 ? NC : 1)
   for (int l = 0; l < NC; ++l) {
     const int vi = (tx + (l & 1)) + (DIM == 2 ? (ty + ((l >> 1) & 1)) * VXT : 0);
     float tl[NSP];
@@ -577,16 +578,16 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
 // at a transmissive boundary, whose ghost is the present cell's trace), projected onto the
 // tangential Legendre modes: sF[face][j] = sum_q w_q P_j(xi_q) F_q.  The right/upper cell
 // adds the difference of the two means' fluxes (mode 0 only).
-template <int DIM, int P, int SYS, int TX, int TY>
+template <int DIM, int P, int SYS, int TX, int TY, int NB = TX * TY>
 __device__ __forceinline__ void tile_face_phase(const StageArgs& a, const float* sc, const float* sB, const float* sW,
                                                 float* sF, int i0, int j0, int nx, int ny) {
   using L = TileLayout<DIM, P, TX, TY>;
   using Law = ScalarLaw<SYS, DIM>;
-  constexpr int N = L::N, NH = L::NH, HX = L::HX, NT = L::NT, NFX = L::NFX, NFACE = L::NFACE, NFP = L::NFP;
+  constexpr int N = L::N, NH = L::NH, HX = L::HX, NFX = L::NFX, NFACE = L::NFACE, NFP = L::NFP;
   // faces from the block's last thread backwards: the vertex phase's extra round falls on
   // the first warp, the face phase's on the last
 #pragma unroll 1
-  for (int f = NT - 1 - threadIdx.x; f < NFACE; f += NT) {
+  for (int f = NB - 1 - threadIdx.x; f < NFACE; f += NB) {
     int dirn, hl, hr;
     bool hasl, hasr;
     if (f < NFX) {
@@ -672,8 +673,10 @@ __device__ __forceinline__ void tile_face_phase(const StageArgs& a, const float*
 // of the mesh described by a.  Every thread must have started the staging of the
 // tabulations (stage_tables_to_smem) before the call: the tile's first cp.async wait and
 // barrier complete it.  The function contains its own barriers and is called by every
-// thread of the CTA.
-template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false>
+// thread of the CTA.  A block of NB > TX * TY threads shares the loads, the vertices and
+// the faces among all of them; its threads beyond the cells leave before the per-cell
+// stages.
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false, int NB = TX * TY>
 __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<DIM, P>& T, int i0, int j0,
                                             float* smem) {
   using L = TileLayout<DIM, P, TX, TY>;
@@ -707,12 +710,12 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   const bool in16 = ND % 4 == 0 && aligned;
   const bool rows16 = ND % 4 != 0 && aligned;
   float* stg = smem + L::OFF_NQ;
-  constexpr int NQ4 = ND / 4;
+  constexpr int NQ4 = ND / 4 > 0 ? ND / 4 : 1;  // used only where ND % 4 == 0
   if (rows16) {
-    stage_rows16<ND, HX, HY, RSP, NT>(stg, sph, a.u_in, nx, DIM == 2 ? ny : 1, i0 - 1, DIM == 2 ? j0 - 1 : 0, a.perx,
+    stage_rows16<ND, HX, HY, RSP, NB>(stg, sph, a.u_in, nx, DIM == 2 ? ny : 1, i0 - 1, DIM == 2 ? j0 - 1 : 0, a.perx,
                                       DIM == 2 && a.pery);
   } else if (in16) {
-    for (int f = threadIdx.x; f < NH * NQ4; f += NT) {
+    for (int f = threadIdx.x; f < NH * NQ4; f += NB) {
       const int h = f / NQ4, q = f - h * NQ4;
       const int r = DIM == 2 ? h / HX : 0, cc = h - r * HX;
       int gi = i0 - 1 + cc, gj = DIM == 2 ? j0 - 1 + r : 0;
@@ -726,7 +729,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
       cp_async16z(stg + 4 * f, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + 4 * q : a.u_in, ok ? 16 : 0);
     }
   } else {
-    for (int f = threadIdx.x; f < NH * ND; f += NT) {
+    for (int f = threadIdx.x; f < NH * ND; f += NB) {
       int r = f / (HX * ND);
       int rem = f - r * (HX * ND);
       int cc = rem / ND;
@@ -745,7 +748,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   cp_async_wait_all();
   __syncthreads();
   if (in16) {
-    for (int f = threadIdx.x; f < NH * NQ4; f += NT) {
+    for (int f = threadIdx.x; f < NH * NQ4; f += NB) {
       const int h = f / NQ4, q = f - h * NQ4;
       const float4 v = *reinterpret_cast<const float4*>(stg + 4 * f);
       sc[(4 * q + 0) * NH + h] = v.x;
@@ -755,7 +758,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     }
     __syncthreads();
   } else if (rows16) {
-    for (int h = threadIdx.x; h < NH; h += NT) {
+    for (int h = threadIdx.x; h < NH; h += NB) {
       const int r = DIM == 2 ? h / HX : 0, cc = h - r * HX;
       const float* src = stg + r * RSP + sph[r] + cc * ND;
 #pragma unroll
@@ -772,7 +775,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   const bool un16 = ND % 4 == 0 && (reinterpret_cast<uintptr_t>(a.u_n) & 15) == 0;
   {
     const int ogi = i0 + threadIdx.x % TX, ogj = DIM == 2 ? j0 + threadIdx.x / TX : 0;
-    if (pre_un && ogi < nx && ogj < ny) {
+    if (pre_un && threadIdx.x < NT && ogi < nx && ogj < ny) {
       const float* src = a.u_n + ((size_t)ogj * nx + ogi) * ND;
       float* sUn = smem + L::OFF_UN;
       if (un16) {
@@ -786,16 +789,17 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   }
 
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
-  tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
+  tile_vertex_phase<DIM, P, TX, TY, NB>(a, T, sc, st, i0, j0, nx, ny);
   constexpr bool kSharedFaces = L::SHARED_FACES && !(SURR && P == 2);
   if constexpr (kSharedFaces) {
     if (!(a.mode & (kModeSensorOnly | kModeLimit | kModeFeatures)))
-      tile_face_phase<DIM, P, SYS, TX, TY>(a, sc, sB, sW, smem + L::OFF_F, i0, j0, nx, ny);
+      tile_face_phase<DIM, P, SYS, TX, TY, NB>(a, sc, sB, sW, smem + L::OFF_F, i0, j0, nx, ny);
   }
   __syncthreads();
   pdl_launch_dependents();
 
   // ---- one thread per cell from here on (no further barriers in this tile) -----------------
+  if (NB > NT && threadIdx.x >= NT) return;
   const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
   const int gi = i0 + tx, gj = j0 + ty;
   const bool active = gi < nx && gj < ny;
@@ -952,7 +956,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   const bool need_sc = troubled && gam < 1.0f;
   if (!(a.lambda_const > 0.0f) || need_sc) {
     float s1 = 0.0f, s2 = 0.0f;
-#pragma unroll 1
+#pragma unroll (DIM == 1 ? N : 1)
     for (int qx = 0; qx < N; ++qx) {
       float tb[NY1], td[NY1];
 #pragma unroll
@@ -1158,7 +1162,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     }
   }
   // volume: flux deviation and alpha-weighted viscous term, projected by sum factorisation
-#pragma unroll 1
+#pragma unroll (DIM == 1 ? N : 1)
   for (int qx = 0; qx < N; ++qx) {
     float tb[NY1], td[NY1];
 #pragma unroll
@@ -1250,21 +1254,53 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   if (bad) atomicOr(a.status, kStatNonfinite);
 }
 
-template <int DIM, int P, int SYS, int TX, int TY, bool SURR>
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR, int NB = TX * TY>
 __device__ __forceinline__ void stage_body(const StageArgs& a, const DgTables<DIM, P>& T) {
   extern __shared__ __align__(16) float smem[];
-  stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);  // lands with the tile's first wait
+  stage_tables_to_smem<DIM, P, TX, TY, NB>(a.tab_img, smem);  // lands with the tile's first wait
   pdl_wait();  // everything below reads or writes what earlier kernels write
   if constexpr (SURR && DIM == 2) {
     if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY>(a.mlp, smem);
   }
-  scalar_tile<DIM, P, SYS, TX, TY, SURR>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
+  scalar_tile<DIM, P, SYS, TX, TY, SURR, NB>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
+}
+
+// Threads of a block of the plain stage kernel.  One warp more than the tile's cells in 1D
+// and below p = 3 in 2D, so that the tile's vertices ((TX + 1) (TY + 1) of them) take one
+// round, and the faces beside them fewer.  At p >= 3 the extra warp's registers would cost
+// a resident CTA per SM.
+template <int DIM, int P, int TX, int TY>
+__host__ __device__ constexpr int stage_block_threads() {
+  return DIM == 1 || P <= 2 ? TX * TY + 32 : TX * TY;
 }
 
 template <int DIM, int P, int SYS, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
+__global__ void __launch_bounds__(stage_block_threads<DIM, P, TX, TY>())
     dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
-  stage_body<DIM, P, SYS, TX, TY, false>(a, T);
+  stage_body<DIM, P, SYS, TX, TY, false, stage_block_threads<DIM, P, TX, TY>()>(a, T);
+}
+
+// nsteps SSP-RK3 steps of a 1D mesh that is a single tile (nx <= TX), in one launch.  The
+// halo of a stage is this block's own output of the stage before, so a block barrier
+// (which orders the block's global writes before its later reads) stands in for the
+// kernel boundary; the tabulations are staged once.  Each stage is the stage kernel's
+// code with the same block, so the results are bitwise those of three launches per step.
+template <int P, int SYS, int TX>
+__global__ void __launch_bounds__(stage_block_threads<1, P, TX, 1>())
+    dg_scalar_steps_tile(const __grid_constant__ StepArgs s, const __grid_constant__ DgTables<1, P> T) {
+  constexpr int NB = stage_block_threads<1, P, TX, 1>();
+  extern __shared__ __align__(16) float smem[];
+  stage_tables_to_smem<1, P, TX, 1, NB>(s.st[0].tab_img, smem);
+  pdl_wait();
+#pragma unroll 1
+  for (int n = 0; n < s.nsteps; ++n) {
+    scalar_tile<1, P, SYS, TX, 1, false, NB>(s.st[0], T, 0, 0, smem);
+    __syncthreads();
+    scalar_tile<1, P, SYS, TX, 1, false, NB>(s.st[1], T, 0, 0, smem);
+    __syncthreads();
+    scalar_tile<1, P, SYS, TX, 1, false, NB>(s.st[2], T, 0, 0, smem);
+    __syncthreads();
+  }
 }
 
 // The surrogate instantiation is held to the register budget of 5 resident CTAs below
