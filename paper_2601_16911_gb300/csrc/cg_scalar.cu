@@ -54,14 +54,24 @@ __device__ __forceinline__ float ml1(const CgTables<DIM, P>& C, int a, float h) 
   return (a == 0 ? 2.0f : 1.0f) * C.wl[a] * h;
 }
 
+// Threads of a block of the CG cell kernel: one warp more than the tile's cells in 1D and
+// at p = 1, so that the tile's (TX + 1) (TY + 1) vertices take one round and the halo
+// ring's integrals fall on the extra warp (KPP 256^2 CG Q1: 0.0411 -> 0.0391 ms per step;
+// at p = 2 the same block was 19 % slower).
+template <int DIM, int P, int TX, int TY>
+__host__ __device__ constexpr int cg_block_threads() {
+  return DIM == 1 || P == 1 ? TX * TY + 32 : TX * TY;
+}
+
 template <int DIM, int P, int SYS, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__ StageArgs a,
+__global__ void __launch_bounds__(cg_block_threads<DIM, P, TX, TY>()) cg_stage_cells(const __grid_constant__ StageArgs a,
                                                           const __grid_constant__ DgTables<DIM, P> T,
                                                           const __grid_constant__ CgTables<DIM, P> C) {
   using L = TileLayout<DIM, P, TX, TY>;
   using G = CgLayout<DIM, P, TX, TY>;
   using Law = ScalarLaw<SYS, DIM>;
   constexpr int N = L::N, ND = L::ND, NT = L::NT, HX = L::HX, NH = L::NH;
+  constexpr int NB = cg_block_threads<DIM, P, TX, TY>();  // threads of the block
   constexpr int NNX = G::NNX, NNY = G::NNY, NNXP = G::NNXP;
   constexpr int NY1 = DIM == 2 ? N : 1;
   extern __shared__ __align__(16) float smem[];
@@ -83,7 +93,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
 
   // ---- nodal values of the tile and its halo (periodic lattice) -------------------------
-  stage_tables_to_smem<DIM, P, TX, TY>(a.tab_img, smem);
+  stage_tables_to_smem<DIM, P, TX, TY, NB>(a.tab_img, smem);
   pdl_wait();  // everything below reads or writes what earlier kernels write
   // Node (ix, iy) lands at snode[iy][sph[iy] + ix].  Where the tile's rows do not wrap in x
   // and the state is 16-byte aligned, each row is copied as the 16-byte chunks that cover
@@ -96,7 +106,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
     const bool rows16 = I0 >= 0 && I0 + NNX <= nnx && (reinterpret_cast<uintptr_t>(a.u_in) & 15) == 0;
     if (rows16) {
       constexpr int NCH = NNXP / 4;  // chunks per row
-      for (int f = threadIdx.x; f < NNY * NCH; f += NT) {
+      for (int f = threadIdx.x; f < NNY * NCH; f += NB) {
         const int iy = f / NCH, k = f - iy * NCH;
         const int J = DIM == 2 ? wrap_index(J0 + iy, nny) : 0;
         const int64_t g0 = (int64_t)J * nnx + I0;  // the row's first node
@@ -107,13 +117,13 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
         if (k == 0) sph[iy] = ph;
       }
     } else {
-      for (int f = threadIdx.x; f < NNX * NNY; f += NT) {
+      for (int f = threadIdx.x; f < NNX * NNY; f += NB) {
         const int ix = f % NNX, iy = f / NNX;
         const int I = wrap_index(I0 + ix, nnx);
         const int J = DIM == 2 ? wrap_index(J0 + iy, nny) : 0;
         cp_async4(snode + iy * NNXP + ix, a.u_in + (size_t)J * nnx + I, 4);
       }
-      for (int iy = threadIdx.x; iy < NNY; iy += NT) sph[iy] = 0;
+      for (int iy = threadIdx.x; iy < NNY; iy += NB) sph[iy] = 0;
     }
   }
   cp_async_wait_all();
@@ -122,7 +132,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   // The transform is applied to u_loc - u_ref (u_ref = the cell's first node): every mode
   // but the mean is unchanged (the rows of V beyond the mean sum to zero), the mean gets
   // u_ref back, and a constant cell yields exactly zero non-mean modes.
-  for (int h = threadIdx.x; h < NH; h += NT) {
+  for (int h = threadIdx.x; h < NH; h += NB) {
     const int hx = h % HX, hy = DIM == 2 ? h / HX : 0;
     float ul[ND];
 #pragma unroll
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   }
   __syncthreads();
   // ---- (a)+(b) vertex candidates (shared with DG) ---------------------------------------
-  tile_vertex_phase<DIM, P, TX, TY>(a, T, sc, st, i0, j0, nx, ny);
+  tile_vertex_phase<DIM, P, TX, TY, NB>(a, T, sc, st, i0, j0, nx, ny);
   // ---- P_h local integrals b_a = int phi_a grad u (reading A13) ------------------------------
   // For u = sum_m c_m P_mx P_my on the cell, with dx dy / 4 = hdx hdy and the factor 2/dx
   // of d/dx cancelling hdx (Em, Dm: integrals of l_a against P_m and P_m'):
@@ -166,7 +176,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   // A tile cell takes every entry; a halo cell only those of its nodes on the tile's
   // boundary, the ones that the tile's nodes gather (one row or column of nodes).
   if constexpr (DIM == 1) {
-    for (int h = threadIdx.x; h < NH; h += NT) {
+    for (int h = threadIdx.x; h < NH; h += NB) {
 #pragma unroll
       for (int aa = 0; aa < N; ++aa) {
         float acc = 0.0f;
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
     }
   } else {
     constexpr int HY = L::HY;
-    {
+    if (threadIdx.x < NT) {
       const int h = (threadIdx.x / TX + 1) * HX + threadIdx.x % TX + 1;
       float c[ND];
 #pragma unroll
@@ -215,9 +225,9 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
     // faces the tile (l = P below it, 0 above), the left and right columns the node
     // column a = l (P left of it, 0 right)
     constexpr int NR = 2 * HX + 2 * TY;
-    // from the block's last thread backwards: the vertex phase's extra round falls on the
-    // first warp, the ring on the last ones
-    for (int r = NT - 1 - threadIdx.x; r < NR; r += NT) {
+    // from the block's last thread backwards: the vertex phase's extra round (if any) falls
+    // on the first warp, the ring on the last ones
+    for (int r = NB - 1 - threadIdx.x; r < NR; r += NB) {
       const bool row = r < 2 * HX;
       int hx, hy, l;
       if (row) {
@@ -273,6 +283,7 @@ __global__ void __launch_bounds__(TX* TY) cg_stage_cells(const __grid_constant__
   pdl_launch_dependents();
 
   // ---- one thread per own cell ------------------------------------------------------------------
+  if (NB > NT && threadIdx.x >= NT) return;
   const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
   const int gi = i0 + tx, gj = j0 + ty;
   if (gi >= nx || gj >= ny) return;
@@ -891,7 +902,7 @@ cudaError_t launch_cg_t(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   dim3 grid((a.nx + TX - 1) / TX, DIM == 2 ? (a.ny + TY - 1) / TY : 1);
-  cudaError_t e = launch_pdl(k1, grid, dim3(TX * TY), smem, s, a, T, C);
+  cudaError_t e = launch_pdl(k1, grid, dim3(cg_block_threads<DIM, P, TX, TY>()), smem, s, a, T, C);
   if (e != cudaSuccess) return e;
   if (a.mode & kModeSensorOnly) return cudaGetLastError();
   kernel_mark(m, s);

@@ -472,7 +472,7 @@ __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTa
     const float* base = sc + (DIM == 2 ? vb * HX : 0) + va;
     // slots SW, SE, NW, NE: the cell right of / above the vertex touches it with its
     // left / lower corner (sign -1), the cell left of / below with its right / upper one
-#pragma unroll (DIM == 1 ? NC : 1)
+#pragma unroll (DIM == 1 || P <= 2 ? NC : 1)
     for (int s = 0; s < NC; ++s) {
       const int ex = s & 1, ey = (s >> 1) & 1;
       if (!((ex ? has_e : has_w) && (ey ? has_n : has_s))) continue;
@@ -528,7 +528,7 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
 #pragma unroll
   for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
   float osum = om0;
-#pragma unroll (DIM == 1 ? NC : 1)
+#pragma unroll (DIM == 1 || P <= 2 ? NC : 1)
   for (int l = 0; l < NC; ++l) {
     const int vi = (tx + (l & 1)) + (DIM == 2 ? (ty + ((l >> 1) & 1)) * VXT : 0);
     float tl[NSP];
@@ -956,7 +956,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   const bool need_sc = troubled && gam < 1.0f;
   if (!(a.lambda_const > 0.0f) || need_sc) {
     float s1 = 0.0f, s2 = 0.0f;
-#pragma unroll (DIM == 1 ? N : 1)
+#pragma unroll (DIM == 1 || P == 1 ? N : 1)
     for (int qx = 0; qx < N; ++qx) {
       float tb[NY1], td[NY1];
 #pragma unroll
@@ -1162,7 +1162,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     }
   }
   // volume: flux deviation and alpha-weighted viscous term, projected by sum factorisation
-#pragma unroll (DIM == 1 ? N : 1)
+#pragma unroll (DIM == 1 || P == 1 ? N : 1)
   for (int qx = 0; qx < N; ++qx) {
     float tb[NY1], td[NY1];
 #pragma unroll
@@ -1266,9 +1266,9 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const DgTables<DI
 }
 
 // Threads of a block of the plain stage kernel.  One warp more than the tile's cells in 1D
-// and below p = 3 in 2D, so that the tile's vertices ((TX + 1) (TY + 1) of them) take one
-// round, and the faces beside them fewer.  At p >= 3 the extra warp's registers would cost
-// a resident CTA per SM.
+// and below p = 3 in 2D, so that the tile's (TX + 1) (TY + 1) vertices take one round,
+// and the faces beside them fewer.  At p >= 3 the extra warp's registers would cost a
+// resident CTA per SM.
 template <int DIM, int P, int TX, int TY>
 __host__ __device__ constexpr int stage_block_threads() {
   return DIM == 1 || P <= 2 ? TX * TY + 32 : TX * TY;
