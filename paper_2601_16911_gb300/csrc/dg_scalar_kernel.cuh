@@ -251,13 +251,13 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Copies the packed surrogate weights into shared memory (uint4 copies).
-template <int DIM, int P, int TX, int TY>
+// Copies the packed surrogate weights into shared memory (uint4 copies; NB threads).
+template <int DIM, int P, int TX, int TY, int NB = TX * TY>
 __device__ __forceinline__ void stage_mlp_to_smem(const void* mlp, float* smem) {
   using L = TileLayout<DIM, P, TX, TY>;
   const uint4* src = static_cast<const uint4*>(mlp);
   uint4* dst = reinterpret_cast<uint4*>(smem + L::OFF_MLP);
-  for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 16); i += L::NT) dst[i] = __ldg(src + i);
+  for (int i = threadIdx.x; i < (int)(sizeof(MlpPacked) / 16); i += NB) dst[i] = __ldg(src + i);
 }
 
 // Surrogate inputs of one cell (2D): per corner l, the vertex candidate's cell mean minus
@@ -1260,7 +1260,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const DgTables<DI
   stage_tables_to_smem<DIM, P, TX, TY, NB>(a.tab_img, smem);  // lands with the tile's first wait
   pdl_wait();  // everything below reads or writes what earlier kernels write
   if constexpr (SURR && DIM == 2) {
-    if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY>(a.mlp, smem);
+    if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY, NB>(a.mlp, smem);
   }
   scalar_tile<DIM, P, SYS, TX, TY, SURR, NB>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
 }
@@ -1303,13 +1303,13 @@ __global__ void __launch_bounds__(stage_block_threads<1, P, TX, 1>())
   }
 }
 
-// The surrogate instantiation is held to the register budget of 5 resident CTAs below
-// p = 3 (its shared memory allows 5), 4 at p = 3 and 3 at p = 4, which the network's
-// fragments would otherwise exceed.
+// The surrogate instantiation takes the plain kernel's block and is held to the register
+// budget of 4 resident CTAs up to p = 3 and 3 at p = 4, which the network's fragments
+// would otherwise exceed.
 template <int DIM, int P, int SYS, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, (P >= 4 ? 3 : P == 3 ? 4 : 5) * (128 / (TX * TY)))
+__global__ void __launch_bounds__(stage_block_threads<DIM, P, TX, TY>(), (P >= 4 ? 3 : 4) * (128 / (TX * TY)))
     dg_scalar_stage_surrogate(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
-  stage_body<DIM, P, SYS, TX, TY, true>(a, T);
+  stage_body<DIM, P, SYS, TX, TY, true, stage_block_threads<DIM, P, TX, TY>()>(a, T);
 }
 
 }  // namespace cvw

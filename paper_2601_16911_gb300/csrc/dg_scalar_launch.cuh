@@ -26,7 +26,7 @@ cudaError_t launch_scalar(const cvweno_mesh_s* m, const StageArgs& a, cudaStream
   }
   if (m->tables_bytes != sizeof(Tb)) return cudaErrorInvalidValue;
   dim3 grid((a.nx + TX - 1) / TX, DIM == 2 ? (a.ny + TY - 1) / TY : 1);
-  const int threads = SURR ? TX * TY : stage_block_threads<DIM, P, TX, TY>();
+  const int threads = stage_block_threads<DIM, P, TX, TY>();
   return launch_pdl(kern, grid, dim3(threads), smem, s, a, *static_cast<const Tb*>(m->tables));
 }
 
