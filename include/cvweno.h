@@ -241,6 +241,17 @@ cvweno_status cvweno_positivity(cvweno_mesh m, const float* u, float* out, float
 cvweno_status cvweno_mesh_set_kernel_timing(cvweno_mesh m, int enable);
 cvweno_status cvweno_kernel_times(cvweno_mesh m, float* ms, int capacity, int* count);
 
+/* Contraction form of the stage kernel.  enable = 1 runs the sensor's corner products
+ * (stage (c): the four vertex candidates mapped into the cell's semi-norm coordinates,
+ * Sec. 3.2 eq. finalweno with the semi-norm of Sec. 2.2 eq. snorm) on the tensor cores
+ * (tcgen05, split TF32: hi*hi + hi*lo + lo*hi, FP32 accumulation), on 8 x 16 tiles;
+ * enable = 0 (the default) runs them as FP32 FMAs on 16 x 8 tiles.  Both forms compute
+ * the same stage to FP32 rounding.  2D DG scalar meshes of degree 3 only: returns
+ * CVWENO_ERR_UNSUPPORTED for any other mesh when enable = 1, CVWENO_ERR_ARG for enable
+ * other than 0 or 1.  A bounded wait for the tensor cores that gives up raises status
+ * bit 4, reported as CVWENO_ERR_TIMEOUT at the next status check. */
+cvweno_status cvweno_mesh_set_tensor_cores(cvweno_mesh m, int enable);
+
 /* ---- batches of independent problems ------------------------------------------------
  * Many independent 2D DG meshes of uneven size and degree advanced together: each
  * SSP-RK3 stage of the whole batch is one persistent launch (or one per degree present),

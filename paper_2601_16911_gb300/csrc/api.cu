@@ -267,6 +267,7 @@ cvweno_status read_status(cvweno_mesh m, cudaStream_t s) {
   }
   if (st & kStatPositivity) return CVWENO_ERR_POSITIVITY;
   if (st & kStatNonfinite) return CVWENO_ERR_NONFINITE;
+  if (st & kStatTimeout) return CVWENO_ERR_TIMEOUT;
   return CVWENO_OK;
 }
 
@@ -758,6 +759,14 @@ cvweno_status cvweno_mesh_set_kernel_timing(cvweno_mesh m, int enable) {
       if (cudaEventCreate(&m->tev[i]) != cudaSuccess) return CVWENO_ERR_CUDA;
   m->timing = enable ? 1 : 0;
   if (enable) m->tcount = 0;  // disabling keeps the last step's events readable
+  return CVWENO_OK;
+}
+
+cvweno_status cvweno_mesh_set_tensor_cores(cvweno_mesh m, int enable) {
+  if (!m || (enable != 0 && enable != 1)) return CVWENO_ERR_ARG;
+  if (enable && !(m->dim == 2 && m->kind == CVWENO_DG && m->p == 3 && m->desc.system != CVWENO_EULER))
+    return CVWENO_ERR_UNSUPPORTED;
+  m->tensor_cores = enable;
   return CVWENO_OK;
 }
 

@@ -12,7 +12,7 @@ constexpr int kMaxP = 4;
 constexpr int kMaxMarks = 24;  // timing events per step: 3 stages x (up to 6 kernels + 1) + 1
 
 // Status bits raised by kernels in the mesh's device status word.
-enum : int { kStatNonfinite = 1, kStatPositivity = 2 };
+enum : int { kStatNonfinite = 1, kStatPositivity = 2, kStatTimeout = 4 };
 
 // Reference-cell tabulations of one (dim, p) pair, FP64 on the host rounded once to
 // FP32, passed to the kernels by value (__grid_constant__), so that every warp reads
@@ -61,19 +61,27 @@ struct TabImage {
   static constexpr int BD = B + N * N;         // [N][N]
   static constexpr int BK = BD + N * N;        // [N][N][N]
   static constexpr int W = BK + N * N * N;     // [N]
-  static constexpr int FLOATS = (W + N + 3) / 4 * 4;  // whole 16-byte chunks
+  static constexpr int FLOATS = (W + N + 3) / 4 * 4;  // whole 16-byte chunks (the CUDA-core kernels' part)
+  // The tensor-core form of the sensor's corner products (2D, p = 3): A[l] split into TF32
+  // hi and lo parts, zero-padded to TCK x TCK, in the canonical K-major operand layout
+  // [part][corner l][K chunk of 4][row i][4] (tc_tf32.cuh).
+  static constexpr bool HAS_TC = DIM == 2 && P == 3;
+  static constexpr int TCK = (NS + 15) / 16 * 16;
+  static constexpr int TC = FLOATS;
+  static constexpr int FLOATS_ALL = FLOATS + (HAS_TC ? 2 * NC * TCK * TCK : 0);
 };
-constexpr int kMaxTabImage = TabImage<2, kMaxP>::FLOATS;
+constexpr int imax(int a, int b) { return a > b ? a : b; }
+constexpr int kMaxTabImage = imax(TabImage<2, kMaxP>::FLOATS_ALL, TabImage<2, 3>::FLOATS_ALL);
 inline int tab_image_floats(int dim, int p) {
   switch (dim * 10 + p) {
-    case 11: return TabImage<1, 1>::FLOATS;
-    case 12: return TabImage<1, 2>::FLOATS;
-    case 13: return TabImage<1, 3>::FLOATS;
-    case 14: return TabImage<1, 4>::FLOATS;
-    case 21: return TabImage<2, 1>::FLOATS;
-    case 22: return TabImage<2, 2>::FLOATS;
-    case 23: return TabImage<2, 3>::FLOATS;
-    case 24: return TabImage<2, 4>::FLOATS;
+    case 11: return TabImage<1, 1>::FLOATS_ALL;
+    case 12: return TabImage<1, 2>::FLOATS_ALL;
+    case 13: return TabImage<1, 3>::FLOATS_ALL;
+    case 14: return TabImage<1, 4>::FLOATS_ALL;
+    case 21: return TabImage<2, 1>::FLOATS_ALL;
+    case 22: return TabImage<2, 2>::FLOATS_ALL;
+    case 23: return TabImage<2, 3>::FLOATS_ALL;
+    case 24: return TabImage<2, 4>::FLOATS_ALL;
     default: return 0;
   }
 }
@@ -210,6 +218,8 @@ struct cvweno_mesh_s {
   const void* surrogate;
   float surrogate_conf_min;
   unsigned int* surrogate_fallbacks;
+  // cvweno_mesh_set_tensor_cores: 1 = the stage kernel's tcgen05 variant (2D DG scalar Q3)
+  int tensor_cores;
   // optional per-launch timing (cvweno_mesh_set_kernel_timing): events recorded
   // between the kernels of one step, read back by cvweno_kernel_times
   int timing;

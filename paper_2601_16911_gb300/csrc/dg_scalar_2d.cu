@@ -10,6 +10,14 @@ cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_
   if (m->dim == 1) return launch_stage_1d(m, a, s);
   if ((a.mlp && !(a.mode & kModeLimit)) || (a.mode & kModeFeatures)) return launch_stage_surrogate(m, a, s);
   constexpr int TX = 16, TY = 8;
+  if (m->tensor_cores && m->p == 3) {
+    switch (m->desc.system) {
+      case CVWENO_BURGERS: return launch_scalar_tc<CVWENO_BURGERS>(m, a, s);
+      case CVWENO_KPP: return launch_scalar_tc<CVWENO_KPP>(m, a, s);
+      case CVWENO_LINADV: return launch_scalar_tc<CVWENO_LINADV>(m, a, s);
+      default: return cudaErrorNotSupported;
+    }
+  }
   switch (m->p * 10 + m->desc.system) {
     case 10 + CVWENO_BURGERS: return launch_scalar<2, 1, CVWENO_BURGERS, TX, TY>(m, a, s);
     case 20 + CVWENO_BURGERS: return launch_scalar<2, 2, CVWENO_BURGERS, TX, TY>(m, a, s);

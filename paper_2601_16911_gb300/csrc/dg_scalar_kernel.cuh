@@ -32,6 +32,7 @@
 
 #include "cvweno_internal.cuh"
 #include "mlp_mma.cuh"
+#include "tc_tf32.cuh"
 
 namespace cvw {
 
@@ -205,7 +206,15 @@ __device__ __forceinline__ void corner_taylor(const DgTables<DIM, P>& T, const f
 // Shared-memory layout of the tile: halo coefficients, vertex candidates, the corner
 // matrices (rows padded to a multiple of 4 floats for 16-byte broadcast loads), the
 // 1D tabulations read with run-time node indices, and per-thread alpha~ storage.
-template <int DIM, int P, int TX, int TY>
+// TC: the tensor-core form of the sensor (2D, p = 3, 8 x 16 tiles).  The vertex
+// candidates are kept only as the split TF32 MMA operand [part][K chunk][vertex][4]
+// (16-byte rows, vertex-major within a chunk), which for every corner l is a canonical
+// operand over the tile's cells as it stands: the cells of a tile row (8, one core-matrix
+// group) meet 8 consecutive vertices, and the next tile row starts VXT vertices further
+// on (the descriptor's 8-row-group stride).  The image is staged from B on, with its
+// tensor-core section (the split corner matrices); the alpha~ storage reuses the operand
+// once the MMAs have completed.
+template <int DIM, int P, int TX, int TY, bool TC = false>
 struct TileLayout {
   using Tb = DgTables<DIM, P>;
   static constexpr int N = P + 1, ND = Tb::ND, NS = Tb::NS, NC = Tb::NC;
@@ -214,17 +223,28 @@ struct TileLayout {
   static constexpr int NT = TX * TY;
   static constexpr int HX = TX + 2, HY = DIM == 2 ? TY + 2 : 1, NH = HX * HY;
   static constexpr int VXT = TX + 1, VYT = DIM == 2 ? TY + 1 : 1, NVT = VXT * VYT;
+  static_assert(!TC || (Img::HAS_TC && TX == 8 && NT == 128), "tensor-core form: 2D p = 3, 8 x 16 tiles");
+  static constexpr int TCK = Img::TCK, TCCH = TCK / 4;            // K of the corner products, its 16-byte chunks
+  static constexpr int TSA_PART = TCCH * NVT * 4;                 // floats of one part (hi or lo) of the operand
   static constexpr int OFF_SC = 0;                                // [ND][NH]
   static constexpr int OFF_ST = OFF_SC + ND * NH;                 // [ND][NVT]
+  static constexpr int OFF_TSA = (OFF_SC + ND * NH + 3) / 4 * 4;  // TC: [2][TCCH][NVT][4]
   // the staged TabImage (16-byte aligned): A [NC][NS][NSP], B[q][m], Bd[q][m],
-  // Bk[k][q][m], w[q]
-  static constexpr int OFF_A = (OFF_ST + ND * NVT + 3) / 4 * 4;
+  // Bk[k][q][m], w[q] (TC: from B on, then the tensor-core section); image float f sits
+  // at OFF_A + f
+  static constexpr int IMG0 = TC ? Img::B : 0;
+  static constexpr int IMG1 = TC ? Img::FLOATS_ALL : Img::FLOATS;
+  static constexpr int OFF_A = (TC ? OFF_TSA + 2 * TSA_PART : (OFF_ST + ND * NVT + 3) / 4 * 4) - IMG0;
   static constexpr int OFF_B = OFF_A + Img::B;
   static constexpr int OFF_BD = OFF_A + Img::BD;
   static constexpr int OFF_BK = OFF_A + Img::BK;
   static constexpr int OFF_W = OFF_A + Img::W;
-  static constexpr int OFF_NQ = OFF_A + Img::FLOATS;              // [ND][NT] pointwise indicators
-  static constexpr int OFF_UN = OFF_NQ + ND * NT;                 // u_n of the tile's cells, [ND][NT] or [NT][ND]
+  static constexpr int OFF_ATC = OFF_A + Img::TC;                 // TC: [2][NC][TCCH][TCK][4]
+  static constexpr int OFF_NQ = TC ? OFF_TSA : OFF_A + Img::FLOATS;  // [ND][NT] pointwise indicators
+  static constexpr int OFF_UN = TC ? OFF_A + IMG1 : OFF_NQ + ND * NT;  // u_n of the tile's cells, [ND][NT] or [NT][ND]
+  // the tile's loads are staged over the indicator and u_n regions (TC: over the operand)
+  static constexpr int STAGING = TC ? 2 * TSA_PART : 2 * ND * NT;
+  static_assert(!TC || ND * NT <= 2 * TSA_PART, "alpha~ storage must fit the operand region");
   // face fluxes of the tile, projected on the tangential modes: x-faces ((TX+1) per tile
   // row), then y-faces (TX per row, TY+1 rows)
   // (degrees 2 and 3, from measurements: at p = 1 the face work per cell is too small to
@@ -421,10 +441,10 @@ __device__ __forceinline__ void stage_rows16(float* dst, int* ph, const float* s
 
 // Starts the copy of the tabulation image img (device, TabImage<DIM, P>) into shared
 // memory; it lands with the tile's first cp.async wait.  NB: threads of the block.
-template <int DIM, int P, int TX, int TY, int NB = TX * TY>
+template <int DIM, int P, int TX, int TY, int NB = TX * TY, bool TC = false>
 __device__ __forceinline__ void stage_tables_to_smem(const float* img, float* smem) {
-  using L = TileLayout<DIM, P, TX, TY>;
-  for (int f = threadIdx.x; f < TabImage<DIM, P>::FLOATS / 4; f += NB) cp_async16(smem + L::OFF_A + 4 * f, img + 4 * f);
+  using L = TileLayout<DIM, P, TX, TY, TC>;
+  for (int f = L::IMG0 / 4 + threadIdx.x; f < L::IMG1 / 4; f += NB) cp_async16(smem + L::OFF_A + 4 * f, img + 4 * f);
 }
 
 // Writes TabImage<DIM, P> of T to img (one block; run once per mesh, off the stage path).
@@ -432,9 +452,17 @@ template <int DIM, int P>
 __global__ void tab_image_kernel(const __grid_constant__ DgTables<DIM, P> T, float* __restrict__ img) {
   using I = TabImage<DIM, P>;
   constexpr int N = I::N, NS = I::NS, NSP = I::NSP;
-  for (int f = threadIdx.x; f < I::FLOATS; f += blockDim.x) {
+  for (int f = threadIdx.x; f < I::FLOATS_ALL; f += blockDim.x) {
     float v = 0.0f;
-    if (f < I::B) {
+    if (f >= I::TC) {  // split corner matrix: [part][l][K chunk j][row i][e], K index 4 j + e
+      constexpr int TCK = I::TCK, NC = I::NC;
+      const int g = f - I::TC, part = g / (NC * TCK * TCK), r = g - part * (NC * TCK * TCK);
+      const int l = r / (TCK * TCK), r2 = r - l * (TCK * TCK), j = r2 / (4 * TCK), r3 = r2 - j * (4 * TCK);
+      const int i = r3 / 4, k = 4 * j + (r3 & 3);
+      const float x = (i < NS && k < NS) ? (&T.A[0][0][0])[(l * NS + i) * NS + k] : 0.0f;
+      const float hi = tc::tf32_rna(x);
+      v = part == 0 ? hi : tc::tf32_rna(x - hi);
+    } else if (f < I::B) {
       const int l = f / (NS * NSP), rem = f - l * (NS * NSP), i = rem / NSP, j = rem - i * NSP;
       v = j < NS ? T.A[l][i][j] : 0.0f;
     } else if (f < I::BD) {
@@ -453,10 +481,10 @@ __global__ void tab_image_kernel(const __grid_constant__ DgTables<DIM, P> T, flo
 // Stages (a)+(b) for the tile's vertices, from the halo coefficients sc (mode-major):
 // vertex candidates t* into st, and (optionally) the physical vertex data to tstar_out.
 // NB threads of the block share the vertices.
-template <int DIM, int P, int TX, int TY, int NB = TX * TY>
+template <int DIM, int P, int TX, int TY, int NB = TX * TY, bool TC = false>
 __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTables<DIM, P>& T, const float* sc,
                                                   float* st, int i0, int j0, int nx, int ny) {
-  using L = TileLayout<DIM, P, TX, TY>;
+  using L = TileLayout<DIM, P, TX, TY, TC>;
   constexpr int ND = L::ND, NC = L::NC, HX = L::HX, NH = L::NH, VXT = L::VXT, NVT = L::NVT;
   const int act_x = min(TX, nx - i0), act_y = DIM == 2 ? min(TY, ny - j0) : 1;
   for (int v = threadIdx.x; v < NVT; v += NB) {
@@ -487,8 +515,23 @@ __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTa
       for (int k = 0; k < ND; ++k) acc[k] = fmaf(wt, t[k], acc[k]);
     }
     const float inv = 1.0f / wsum;
+    if constexpr (TC) {
+      // t*_1 .. t*_NS, zero-padded to TCK, split into TF32 hi and lo: row v of the operand
 #pragma unroll
-    for (int k = 0; k < ND; ++k) st[k * NVT + v] = acc[k] * inv;
+      for (int j = 0; j < L::TCCH; ++j) {
+        float hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 4 * j + e + 1;
+          tc::split_tf32(k < ND ? acc[k < ND ? k : 0] * inv : 0.0f, hi[e], lo[e]);
+        }
+        *reinterpret_cast<float4*>(st + (j * NVT + v) * 4) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4*>(st + L::TSA_PART + (j * NVT + v) * 4) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < ND; ++k) st[k * NVT + v] = acc[k] * inv;
+    }
     if (a.tstar_out) {
       int I = i0 + va, J = j0 + vb;
       bool own_x = (va < TX || I == nx) && I < a.vx;
@@ -565,6 +608,120 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
     d2 = fmaf(df, df, d2);
   }
   // the limiter, the surrogate's inputs and its fallback always use the computed sensor
+  const bool forced = !(a.mode & (kModeLimit | kModeFeatures));
+  if (forced && a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
+  if (forced && a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
+  if (n0 <= 1e-30f) return 1.0f;
+  return 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
+}
+
+// Tensor memory and completion barrier of the tensor-core form of the sensor (one
+// allocation per CTA, made before the tile and freed inside it).
+struct TcCtx {
+  const uint32_t* slot;  // shared: TMEM base address (lane 0, first of kTcCols columns)
+  uint32_t mbar;         // shared-memory address of the MMA completion mbarrier
+  uint32_t* done;        // shared: warps that have read their corner products
+};
+constexpr uint32_t kTcCols = 64;          // 4 corners x 16 FP32 columns
+constexpr uint32_t kTcPolls = 1u << 22;   // bounded wait for the corner products
+
+// Issued by one thread once the tile's vertex candidates (the split operand) are in
+// shared memory: w_l = A[l] t*_l for the four corners l of all 128 cells, into TMEM
+// columns 16 l .. 16 l + 15 of the cell's lane, as A_hi B_hi + A_hi B_lo + A_lo B_hi.
+template <int P, int TX, int TY>
+__device__ __forceinline__ void issue_corner_products(const float* smem, const TcCtx& tcx) {
+  using L = TileLayout<2, P, TX, TY, true>;
+  constexpr int TCK = L::TCK, NC = L::NC;
+  constexpr uint32_t ALBO = L::NVT * 16, ASBO = L::VXT * 16, APART = L::TSA_PART * 4;
+  constexpr uint32_t BLBO = TCK * 16, BSBO = 8 * 16, BCORNER = TCK * TCK * 4, BPART = NC * BCORNER;
+  const uint32_t id = tc::idesc_tf32(128, TCK);
+  const uint32_t tsa = tc::smem_u32(smem + L::OFF_TSA), atc = tc::smem_u32(smem + L::OFF_ATC);
+  tc::fence_after();
+  const uint32_t tmem = *tcx.slot;
+#pragma unroll
+  for (int l = 0; l < NC; ++l) {
+    const uint32_t a0 = tsa + (((l >> 1) & 1) * L::VXT + (l & 1)) * 16, b0 = atc + l * BCORNER;
+    const uint32_t d = tmem + 16 * l;
+#pragma unroll
+    for (int s = 0; s < TCK / 8; ++s) {
+      const uint64_t ah = tc::smem_desc(a0 + 2 * s * ALBO, ALBO, ASBO);
+      const uint64_t al = tc::smem_desc(a0 + APART + 2 * s * ALBO, ALBO, ASBO);
+      const uint64_t bh = tc::smem_desc(b0 + 2 * s * BLBO, BLBO, BSBO);
+      const uint64_t bl = tc::smem_desc(b0 + BPART + 2 * s * BLBO, BLBO, BSBO);
+      tc::mma_tf32(d, ah, bh, id, s > 0);
+      tc::mma_tf32(d, ah, bl, id, 1u);
+      tc::mma_tf32(d, al, bh, id, 1u);
+    }
+  }
+  tc::commit(tcx.mbar);
+}
+
+// Stage (c) as cell_sensor, with the corner products A[l] t*_l read from tensor memory
+// (issue_corner_products).  Every thread of the CTA calls it (the TMEM loads are
+// warp-collective), cells outside the mesh included; the last warp to have read its
+// products frees the TMEM.  overlap() runs between the cell's own part and the wait for
+// the tensor cores: work of the cell that does not depend on the sensor.
+template <int DIM, int P, int TX, int TY, class Overlap>
+__device__ __forceinline__ float cell_sensor_tc(const StageArgs& a, const DgTables<DIM, P>& T, const TcCtx& tcx,
+                                                const float* c, float& n0, float* wstar, Overlap&& overlap) {
+  using L = TileLayout<DIM, P, TX, TY, true>;
+  constexpr int NS = L::NS, NC = L::NC;
+  float w0[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = i; j < NS; ++j) acc = fmaf(T.R[i][j], c[j + 1], acc);
+    w0[i] = acc;
+  }
+  float n0sq = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) n0sq = fmaf(w0[i], w0[i], n0sq);
+  n0 = sqrtf(n0sq);
+  const float om0 = (1.0f - NC * a.gamma_vertex) / ipowf(a.eps + powq(n0, a.q), a.r);
+  float S[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
+  float osum = om0;
+  overlap();
+  if (!tc::mbar_wait(tcx.mbar, 0, kTcPolls)) atomicOr(a.status, kStatTimeout);
+  tc::fence_after();
+  const uint32_t tmem = *tcx.slot;
+  const uint32_t trow = tmem + ((threadIdx.x & ~31u) << 16);
+#pragma unroll 1
+  for (int l = 0; l < NC; ++l) {
+    float wl[16];
+    tc::tmem_ld16(trow + 16 * l, wl);
+    float b2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) b2 = fmaf(wl[i], wl[i], b2);
+    const float om = a.gamma_vertex / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+    osum += om;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) S[i] = fmaf(om, wl[i], S[i]);
+  }
+  // this warp is done with the TMEM; the last of the CTA's warps frees it
+  tc::fence_before();
+  __syncwarp();
+  uint32_t arrived = 0;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence_block();
+    arrived = atomicAdd(tcx.done, 1u);
+  }
+  arrived = __shfl_sync(0xffffffffu, arrived, 0);
+  if (arrived == TX * TY / 32 - 1) {
+    __threadfence_block();
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, kTcCols);
+  }
+  const float inv = 1.0f / osum;
+  float d2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    float df = w0[i] - S[i] * inv;
+    wstar[i] = S[i] * inv;
+    d2 = fmaf(df, df, d2);
+  }
   const bool forced = !(a.mode & (kModeLimit | kModeFeatures));
   if (forced && a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
   if (forced && a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
@@ -667,6 +824,51 @@ __device__ __forceinline__ void tile_face_phase(const StageArgs& a, const float*
   }
 }
 
+// Stage (e), the faces' part of a cell's residual from the tile's face phase (sF): a lower
+// face (left/bottom) was projected relative to the neighbour's mean, so this cell adds
+// f(ubar_nb) - f(ubar) (mode 0: the integral of P_j over the face is 2 delta_j0) where that
+// neighbour is present.  r is accumulated.
+template <int DIM, int P, int SYS, int TX, int TY, bool TC>
+__device__ __forceinline__ void shared_face_residual(const StageArgs& a, const ScalarLaw<SYS, DIM>& law,
+                                                     const float* smem, const float* sc, float ubar, int tx, int ty,
+                                                     int gi, int gj, int hc, float* r) {
+  using L = TileLayout<DIM, P, TX, TY, TC>;
+  constexpr int N = L::N, HX = L::HX;
+  const float* sF = smem + L::OFF_F;
+  if constexpr (DIM == 1) {
+    const bool hasL = a.perx || gi > 0;
+    const float FR = sF[tx + 1];
+    const float FL = sF[tx] + (hasL ? law.flux_dev_dir(sc[hc - 1] - ubar, 0) : 0.0f);
+#pragma unroll
+    for (int m = 0; m < N; ++m) r[m] += -a.two_dx * (FR - ((m & 1) ? -FL : FL));
+  } else {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int dirn = f >> 1;          // 0: x-face, 1: y-face
+      const bool upper = (f & 1) == 0;  // right / top
+      const int fi = dirn == 0 ? ty * (TX + 1) + tx + (upper ? 1 : 0) : L::NFX + (ty + (upper ? 1 : 0)) * TX + tx;
+      float h[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) h[j] = sF[fi * N + j];
+      if (!upper && (dirn == 0 ? (a.perx || gi > 0) : (a.pery || gj > 0)))
+        h[0] = fmaf(2.0f, law.flux_dev_dir(sc[hc + (dirn == 0 ? -1 : -HX)] - ubar, dirn), h[0]);
+      // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
+      const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
+#pragma unroll
+      for (int my = 0; my < N; ++my)
+#pragma unroll
+        for (int mx = 0; mx < N; ++mx) {
+          const int nrm = dirn == 0 ? mx : my;  // mode index along the normal
+          const float hv = dirn == 0 ? h[my] : h[mx];
+          if (upper)
+            r[mx + N * my] = fmaf(-s2d, hv, r[mx + N * my]);
+          else
+            r[mx + N * my] = fmaf(s2d, (nrm & 1) ? -hv : hv, r[mx + N * my]);
+        }
+    }
+  }
+}
+
 // One tile of one stage: the whole path (a)-(e) for the cells [i0, i0+TX) x [j0, j0+TY)
 // (SURR: the instantiation that also runs the surrogate sensor and the features mode; the
 // plain instantiation carries none of that code, so its registers are unaffected)
@@ -676,16 +878,19 @@ __device__ __forceinline__ void tile_face_phase(const StageArgs& a, const float*
 // thread of the CTA.  A block of NB > TX * TY threads shares the loads, the vertices and
 // the faces among all of them; its threads beyond the cells leave before the per-cell
 // stages.
-template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false, int NB = TX * TY>
+// TC: the tensor-core form of stage (c) (2D, p = 3, 8 x 16 tiles; TileLayout), with the
+// CTA's TMEM allocation and MMA barrier in tcx; the TMEM is freed inside the tile.
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR = false, int NB = TX * TY, bool TC = false>
 __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<DIM, P>& T, int i0, int j0,
-                                            float* smem) {
-  using L = TileLayout<DIM, P, TX, TY>;
+                                            float* smem, TcCtx tcx = {}) {
+  using L = TileLayout<DIM, P, TX, TY, TC>;
   using Law = ScalarLaw<SYS, DIM>;
   constexpr int N = L::N, ND = L::ND, NT = L::NT;
   constexpr int HX = L::HX, NH = L::NH;
   constexpr int NY1 = DIM == 2 ? N : 1;  // tensor extent in y (1 in 1D)
+  static_assert(!TC || (DIM == 2 && !SURR && NB == NT), "tensor-core form: plain 2D kernel, one thread per cell");
   float* sc = smem + L::OFF_SC;
-  float* st = smem + L::OFF_ST;
+  float* st = smem + (TC ? L::OFF_TSA : L::OFF_ST);
   float* sA = smem + L::OFF_A;
   float* sB = smem + L::OFF_B;
   float* sBd = smem + L::OFF_BD;
@@ -702,9 +907,9 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   //  - a cell of whole 16-byte chunks (Q1, Q3): 16-byte copies per cell, cell-major;
   //  - otherwise each halo row by stage_rows16, at the row's phase sph[r];
   //  - a state that is not 16-byte aligned: 4-byte copies straight into sc.
-  static_assert(NH * ND <= 2 * ND * NT, "halo staging must fit the indicator and u_n regions");
+  static_assert(NH * ND <= L::STAGING, "halo staging must fit the indicator and u_n regions");
   constexpr int HY = L::HY, RSP = (HX * ND + 6) / 4 * 4;  // staging row stride (floats)
-  static_assert(ND % 4 == 0 || HY * RSP <= 2 * ND * NT, "halo row staging must fit the indicator and u_n regions");
+  static_assert(ND % 4 == 0 || HY * RSP <= L::STAGING, "halo row staging must fit the indicator and u_n regions");
   __shared__ int sph[HY];
   const bool aligned = (reinterpret_cast<uintptr_t>(a.u_in) & 15) == 0;
   const bool in16 = ND % 4 == 0 && aligned;
@@ -789,30 +994,38 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   }
 
   // ---- (a)+(b): vertex candidates of the tile's vertices ------------------------------
-  tile_vertex_phase<DIM, P, TX, TY, NB>(a, T, sc, st, i0, j0, nx, ny);
+  tile_vertex_phase<DIM, P, TX, TY, NB, TC>(a, T, sc, st, i0, j0, nx, ny);
   constexpr bool kSharedFaces = L::SHARED_FACES && !(SURR && P == 2);
   if constexpr (kSharedFaces) {
     if (!(a.mode & (kModeSensorOnly | kModeLimit | kModeFeatures)))
       tile_face_phase<DIM, P, SYS, TX, TY, NB>(a, sc, sB, sW, smem + L::OFF_F, i0, j0, nx, ny);
   }
+  if constexpr (TC) tc::fence_proxy_async();  // the operand, for the tensor cores
   __syncthreads();
+  if constexpr (TC) {
+    if (threadIdx.x == 0) issue_corner_products<P, TX, TY>(smem, tcx);
+  }
   pdl_launch_dependents();
 
-  // ---- one thread per cell from here on (no further barriers in this tile) -----------------
+  // ---- one thread per cell from here on (TC: one more barrier, after the sensor) -----------
   if (NB > NT && threadIdx.x >= NT) return;
   const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
-  const int gi = i0 + tx, gj = j0 + ty;
+  const int gi = i0 + tx, gj = DIM == 2 ? j0 + ty : 0;
   const bool active = gi < nx && gj < ny;
   // the surrogate runs warp-wide on the tensor cores: cells outside the mesh take part
-  // (on the tile's zero-filled halo data) and leave after it
+  // (on the tile's zero-filled halo data) and leave after it; so do they in the TC form,
+  // whose TMEM loads are warp-collective
   bool use_mlp = false;
   if constexpr (DIM == 2 && SURR) use_mlp = a.mlp != nullptr && !(a.mode & (kModeLimit | kModeFeatures));
-  if (!active && !use_mlp) return;
+  if (!TC && !active && !use_mlp) return;
   const int hc = (DIM == 2 ? (ty + 1) * HX : 0) + tx + 1;
   const size_t cell = (size_t)gj * nx + gi;
   float c[ND];
 #pragma unroll
   for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + hc];
+  float r[ND];  // the residual (TC: its faces' part is taken while the tensor cores run)
+#pragma unroll
+  for (int m = 0; m < ND; ++m) r[m] = 0.0f;
 
   // ---- (c) cell-vertex reconstruction and sensor --------------------------------------
   float n0;
@@ -855,6 +1068,12 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
     } else {
       gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
     }
+  } else if constexpr (TC) {
+    const bool faces_now = active && !(a.mode & (kModeSensorOnly | kModeLimit));
+    gam = cell_sensor_tc<DIM, P, TX, TY>(a, T, tcx, c, n0, wstar, [&] {
+      if (faces_now) shared_face_residual<DIM, P, SYS, TX, TY, TC>(a, Law(a, c[0]), smem, sc, c[0], tx, ty, gi, gj, hc, r);
+    });
+    if (!active) return;
   } else {
     gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
   }
@@ -1036,47 +1255,9 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   }
 
   // ---- (e) residual, deviation form ----------------------------------------------------------
-  float r[ND];
-#pragma unroll
-  for (int m = 0; m < ND; ++m) r[m] = 0.0f;
   const float mu = (1.0f - gam) * nu;
   if constexpr (kSharedFaces) {
-    // faces, from the tile's face phase: a lower face (left/bottom) was projected relative to
-    // the neighbour's mean, so this cell adds f(ubar_nb) - f(ubar) (mode 0: the integral of
-    // P_j over the face is 2 delta_j0) where that neighbour is present
-    const float* sF = smem + L::OFF_F;
-    if constexpr (DIM == 1) {
-      const bool hasL = a.perx || gi > 0;
-      const float FR = sF[tx + 1];
-      const float FL = sF[tx] + (hasL ? law.flux_dev_dir(sc[hc - 1] - ubar, 0) : 0.0f);
-  #pragma unroll
-      for (int m = 0; m < N; ++m) r[m] = -a.two_dx * (FR - ((m & 1) ? -FL : FL));
-    } else {
-  #pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const int dirn = f >> 1;          // 0: x-face, 1: y-face
-        const bool upper = (f & 1) == 0;  // right / top
-        const int fi = dirn == 0 ? ty * (TX + 1) + tx + (upper ? 1 : 0) : L::NFX + (ty + (upper ? 1 : 0)) * TX + tx;
-        float h[N];
-  #pragma unroll
-        for (int j = 0; j < N; ++j) h[j] = sF[fi * N + j];
-        if (!upper && (dirn == 0 ? (a.perx || gi > 0) : (a.pery || gj > 0)))
-          h[0] = fmaf(2.0f, law.flux_dev_dir(sc[hc + (dirn == 0 ? -1 : -HX)] - ubar, dirn), h[0]);
-        // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
-        const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
-  #pragma unroll
-        for (int my = 0; my < N; ++my)
-  #pragma unroll
-          for (int mx = 0; mx < N; ++mx) {
-            const int nrm = dirn == 0 ? mx : my;  // mode index along the normal
-            const float hv = dirn == 0 ? h[my] : h[mx];
-            if (upper)
-              r[mx + N * my] = fmaf(-s2d, hv, r[mx + N * my]);
-            else
-              r[mx + N * my] = fmaf(s2d, (nrm & 1) ? -hv : hv, r[mx + N * my]);
-          }
-      }
-    }
+    if constexpr (!TC) shared_face_residual<DIM, P, SYS, TX, TY, TC>(a, law, smem, sc, ubar, tx, ty, gi, gj, hc, r);
   } else {
     // faces: neighbour traces relative to this cell's mean (ghost = own trace on a
     // transmissive side)
@@ -1254,15 +1435,30 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   if (bad) atomicOr(a.status, kStatNonfinite);
 }
 
-template <int DIM, int P, int SYS, int TX, int TY, bool SURR, int NB = TX * TY>
+template <int DIM, int P, int SYS, int TX, int TY, bool SURR, int NB = TX * TY, bool TC = false>
 __device__ __forceinline__ void stage_body(const StageArgs& a, const DgTables<DIM, P>& T) {
   extern __shared__ __align__(16) float smem[];
-  stage_tables_to_smem<DIM, P, TX, TY, NB>(a.tab_img, smem);  // lands with the tile's first wait
+  TcCtx tcx = {};
+  if constexpr (TC) {
+    // published by the tile's first barrier (after its loads)
+    __shared__ uint32_t tmem_slot, tc_done;
+    __shared__ uint64_t mma_bar;
+    if (threadIdx.x < 32) {
+      tc::tmem_alloc(&tmem_slot, kTcCols);
+      tc::fence_before();
+    }
+    if (threadIdx.x == 0) {
+      tc::mbar_init(&mma_bar, 1);
+      tc_done = 0;
+    }
+    tcx = TcCtx{&tmem_slot, tc::smem_u32(&mma_bar), &tc_done};
+  }
+  stage_tables_to_smem<DIM, P, TX, TY, NB, TC>(a.tab_img, smem);  // lands with the tile's first wait
   pdl_wait();  // everything below reads or writes what earlier kernels write
   if constexpr (SURR && DIM == 2) {
     if (a.mlp) stage_mlp_to_smem<DIM, P, TX, TY, NB>(a.mlp, smem);
   }
-  scalar_tile<DIM, P, SYS, TX, TY, SURR, NB>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem);
+  scalar_tile<DIM, P, SYS, TX, TY, SURR, NB, TC>(a, T, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, smem, tcx);
 }
 
 // Threads of a block of the plain stage kernel.  One warp more than the tile's cells in 1D
@@ -1278,6 +1474,14 @@ template <int DIM, int P, int SYS, int TX, int TY>
 __global__ void __launch_bounds__(stage_block_threads<DIM, P, TX, TY>())
     dg_scalar_stage(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<DIM, P> T) {
   stage_body<DIM, P, SYS, TX, TY, false, stage_block_threads<DIM, P, TX, TY>()>(a, T);
+}
+
+// The tensor-core form of the 2D Q3 stage kernel: 8 x 16 tiles, the sensor's corner
+// products on tcgen05 in split TF32 (TileLayout, issue_corner_products); 4 CTAs per SM.
+template <int SYS>
+__global__ void __launch_bounds__(128, 4)
+    dg_scalar_stage_tc(const __grid_constant__ StageArgs a, const __grid_constant__ DgTables<2, 3> T) {
+  stage_body<2, 3, SYS, 8, 16, false, 128, true>(a, T);
 }
 
 // nsteps SSP-RK3 steps of a 1D mesh that is a single tile (nx <= TX), in one launch.  The

@@ -92,6 +92,7 @@ _SIGNATURES = {
     "cvweno_positivity": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "cvweno_mesh_set_kernel_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cvweno_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _IP]),
+    "cvweno_mesh_set_tensor_cores": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cvweno_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_VP)]),
     "cvweno_mlp_destroy": (ctypes.c_int, [_VP]),
     "cvweno_mlp_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -327,6 +328,10 @@ class Mesh:
     def set_kernel_timing(self, enable: bool = True):
         _check(load().cvweno_mesh_set_kernel_timing(self._h, 1 if enable else 0), "cvweno_mesh_set_kernel_timing")
 
+    def set_tensor_cores(self, enable: bool = True):
+        """Stage (c)'s corner products on the tensor cores (split TF32) or as FP32 FMAs."""
+        _check(load().cvweno_mesh_set_tensor_cores(self._h, 1 if enable else 0), "cvweno_mesh_set_tensor_cores")
+
     def kernel_times(self):
         """Durations (ms) of the kernels of the most recent step, in launch order."""
         buf = (ctypes.c_float * 64)()
@@ -547,6 +552,10 @@ def cvweno_mesh_set_kernel_timing(mesh: Mesh, enable: bool = True):
 
 def cvweno_kernel_times(mesh: Mesh):
     return mesh.kernel_times()
+
+
+def cvweno_mesh_set_tensor_cores(mesh: Mesh, enable: bool = True):
+    mesh.set_tensor_cores(enable)
 
 
 def cvweno_limit(mesh: Mesh, u, out, all_cells: bool = False, troubled=None, stream=None):
