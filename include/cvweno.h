@@ -380,15 +380,22 @@ cvweno_status cvweno_mlp_fallbacks(cvweno_mlp n, uint64_t* count, int reset, voi
  * state layout of desc), that allocates nothing -- for callers that cannot allocate
  * device or host memory (a library running inside an arena or memory pool it does not
  * own, or an embedding that forbids cudaMalloc after start-up).  It needs no mesh
- * handle: the tabulations are built on the host stack, and the two RK stage buffers, the
- * status word and the device copy of the tabulations live in file-scope __device__
- * storage that the library holds on every GPU that loads it until the process exits
- * (2 x 4,194,304 floats = 32 MiB, plus under 10 KiB).
+ * handle: the tabulations are built on the host stack (by the same builder that
+ * cvweno_mesh_create uses, so the step equals cvweno_step on that mesh bit for bit), and
+ * the two RK stage buffers, the status word and the device copy of the tabulations live
+ * in file-scope __device__ storage of fixed size (2 x 4,194,304 floats = 32 MiB, plus
+ * under 16 KiB), held on every GPU where it has been created until the process exits.
  * The paper has no counterpart; this is a deployment variant of cvweno_step.
- *   - States larger than 4,194,304 floats (ncells x (p+1)^dim x nvars) return
- *     CVWENO_ERR_ARG; other argument checks and codes are those of cvweno_mesh_create.
+ *   - Argument checks and codes are those of cvweno_mesh_create, in its order.  Beyond
+ *     them this variant returns CVWENO_ERR_UNSUPPORTED for CG meshes and for
+ *     hweno_limiter = 1 or positivity = 1, and CVWENO_ERR_ARG for states larger than
+ *     4,194,304 floats (ncells x (p+1)^dim x nvars).
  *   - The first call on a device looks up the device addresses of that storage with
- *     the device current; make that first call before any stream capture.
+ *     the device current.  Under CUDA's lazy module loading (the default) that first
+ *     call is also when the 32 MiB come into existence on the device: make it at
+ *     start-up, before reserving an arena of all free memory and before any stream
+ *     capture (or set CUDA_MODULE_LOADING=EAGER).  The addresses are kept for the
+ *     process: do not call it across a cudaDeviceReset of the device.
  *   - Every call shares the same storage: calls that overlap on the GPU (different
  *     streams, or different host threads) race and corrupt each other's stages.
  *   - status_out (host, may be NULL): when given, the call synchronises the stream and

@@ -592,8 +592,9 @@ cvweno_status cvweno_project(cvweno_mesh m, int ic_type, const double* ic_params
   // Gauss nodes/weights of the 12-point projection rule and Legendre values there.
   ProjTables T;
   {
+    static_assert(kProjN <= kMaxGaussRule, "projection rule larger than the Gauss rule builder");
     double x[kProjN], w[kProjN], pv[kMaxP + 1];
-    gauss_rule(kProjN, x, w);
+    if (!gauss_rule(kProjN, x, w)) return CVWENO_ERR_ARG;
     for (int q = 0; q < kProjN; ++q) {
       T.x[q] = (float)x[q];
       T.w[q] = (float)w[q];

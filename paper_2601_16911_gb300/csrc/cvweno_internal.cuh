@@ -231,7 +231,11 @@ struct cvweno_mesh_s {
 namespace cvw {
 // tables.cpp
 cvweno_status build_tables(cvweno_mesh m);
-void gauss_rule(int n, double* x, double* w);         // Gauss-Legendre on [-1,1], ascending
+// The reference-cell tabulations DgTables<dim, p> of a dx x dy cell into out (host, at
+// least capacity bytes; *bytes receives their size), with no allocation.
+cvweno_status fill_dg_tables(int dim, int p, double dx, double dy, void* out, size_t capacity, size_t* bytes);
+constexpr int kMaxGaussRule = 16;                    // largest rule gauss_rule builds
+bool gauss_rule(int n, double* x, double* w);         // Gauss-Legendre on [-1,1], ascending; false unless 1 <= n <= 16
 void legendre_values(double x, int mmax, double* out);  // P_0..P_mmax at x
 // dg_scalar.cu / dg_euler.cu
 cudaError_t launch_stage(const cvweno_mesh_s* m, const StageArgs& a, cudaStream_t s);

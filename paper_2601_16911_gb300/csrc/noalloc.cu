@@ -9,8 +9,16 @@
 //     (kStaticStateFloats floats per buffer, 2 buffers, 32 MiB in total), which every
 //     GPU that loads the library holds until the process exits;
 //   - its device status word is a second file-scope __device__ variable;
-//   - the reference-cell tabulations are built on the host stack.
+//   - the reference-cell tabulations are built on the host stack by the library's one
+//     tabulation builder (fill_dg_tables, tables.cpp), the same that meshes use.
 // It calls no cudaMalloc, cudaFree, malloc or other allocating routine.
+//
+// The device addresses of that storage are looked up once per device (static_slots), with
+// the device current, by the first call on it.  Under CUDA's lazy module loading (the
+// default) that lookup also loads this module, which is when the storage comes into
+// existence on the device: make the first call at start-up, before reserving an arena
+// of all free memory and before any stream capture.  The cached addresses belong to the
+// device's current context: do not call it across a cudaDeviceReset of that device.
 #include <math.h>
 #include <string.h>
 
@@ -37,7 +45,8 @@ bool g_ready[kMaxDevices];
 std::mutex g_mutex;
 
 // Device addresses of the static scratch, looked up once per device with that device
-// current (host code must not pass the symbols themselves to a kernel).
+// current (in host code the symbols are host-side stand-ins: passed to a kernel they
+// would fault or, where the GPU can reach host memory, silently use the wrong memory).
 cudaError_t static_slots(DeviceSlots* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -59,174 +68,6 @@ cudaError_t static_slots(DeviceSlots* out) {
   return cudaSuccess;
 }
 
-// ---- host tabulations on the stack (FP64, rounded once) ------------------------------------
-
-constexpr int kMaxN = cvw::kMaxP + 1;
-
-void sym_eigen(int n, double a[8][8], double lam[8], double v[8][8]) {
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) v[i][j] = i == j ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = i + 1; j < n; ++j) off += a[i][j] * a[i][j];
-    if (off < 1e-300) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        if (fabs(a[p][q]) < 1e-300) continue;
-        double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
-        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {
-          double akp = a[k][p], akq = a[k][q];
-          a[k][p] = c * akp - s * akq;
-          a[k][q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          double apk = a[p][k], aqk = a[q][k];
-          a[p][k] = c * apk - s * aqk;
-          a[q][k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          double vkp = v[k][p], vkq = v[k][q];
-          v[k][p] = c * vkp - s * vkq;
-          v[k][q] = s * vkp + c * vkq;
-        }
-      }
-  }
-  for (int i = 0; i < n; ++i) lam[i] = a[i][i];
-}
-
-// Gauss-Legendre rule (n <= 8) from the Legendre Jacobi matrix, ascending nodes.
-void gauss(int n, double* x, double* w) {
-  double J[8][8] = {}, lam[8], V[8][8];
-  for (int k = 1; k < n; ++k) J[k - 1][k] = J[k][k - 1] = k / sqrt(4.0 * k * k - 1.0);
-  sym_eigen(n, J, lam, V);
-  int idx[8];
-  for (int i = 0; i < n; ++i) idx[i] = i;
-  for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j)
-      if (lam[idx[j]] < lam[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
-  for (int i = 0; i < n; ++i) {
-    x[i] = lam[idx[i]];
-    w[i] = 2.0 * V[0][idx[i]] * V[0][idx[i]];
-  }
-  for (int i = 0; i < n / 2; ++i) {
-    double xm = 0.5 * (x[n - 1 - i] - x[i]), wm = 0.5 * (w[i] + w[n - 1 - i]);
-    x[i] = -xm;
-    x[n - 1 - i] = xm;
-    w[i] = w[n - 1 - i] = wm;
-  }
-  if (n % 2) x[n / 2] = 0.0;
-}
-
-// out[k][m] = D^k P_m(x) for m, k < kMaxN
-void leg(double x, double out[kMaxN][kMaxN]) {
-  for (int k = 0; k < kMaxN; ++k)
-    for (int m = 0; m < kMaxN; ++m) out[k][m] = 0.0;
-  out[0][0] = 1.0;
-  out[0][1] = x;
-  for (int m = 1; m + 1 < kMaxN; ++m) out[0][m + 1] = ((2.0 * m + 1.0) * x * out[0][m] - m * out[0][m - 1]) / (m + 1.0);
-  for (int k = 1; k < kMaxN; ++k) {
-    out[k][1] = k == 1 ? 1.0 : 0.0;
-    for (int m = 1; m + 1 < kMaxN; ++m) out[k][m + 1] = out[k][m - 1] + (2.0 * m + 1.0) * out[k - 1][m];
-  }
-}
-
-template <int DIM, int P>
-bool fill_tables(cvw::DgTables<DIM, P>& t, double dx, double dy, double h) {
-  using T = cvw::DgTables<DIM, P>;
-  constexpr int N = T::N, ND = T::ND, NS = T::NS, NC = T::NC;
-  memset(&t, 0, sizeof(t));
-  double gx[N], gw[N], L[kMaxN][kMaxN];
-  gauss(N, gx, gw);
-  leg(1.0, L);
-  for (int k = 0; k < N; ++k)
-    for (int m = 0; m < N; ++m) t.E[k][m] = (float)L[k][m];
-  for (int q = 0; q < N; ++q) {
-    leg(gx[q], L);
-    for (int m = 0; m < N; ++m) {
-      t.B[q][m] = (float)L[0][m];
-      t.Bd[q][m] = (float)L[1][m];
-      for (int k = 0; k < N; ++k) t.Bk[k][q][m] = (float)L[k][m];
-    }
-    t.w[q] = (float)gw[q];
-  }
-  // scalings as functions of h/dx and h/dy only (h = sqrt(dx^2 + dy^2) in 2D, dx in 1D)
-  (void)h;
-  const double ax = DIM == 2 ? sqrt(1.0 + (dy / dx) * (dy / dx)) : 1.0;
-  const double ay = DIM == 2 ? sqrt((dx / dy) * (dx / dy) + 1.0) : 1.0;
-  for (int k = 0; k < ND; ++k) {
-    int kx = k % N, ky = DIM == 2 ? k / N : 0;
-    t.sigma[k] = k == 0 ? 0.0f : (float)(pow(2.0 * ax, 2 * kx) * (DIM == 2 ? pow(2.0 * ay, 2 * ky) : 1.0));
-    t.tscale[k] = (float)(pow(2.0 / dx, kx) * (DIM == 2 ? pow(2.0 / dy, ky) : 1.0));
-  }
-  const int NG = 8;
-  double qx[NG], qw[NG];
-  gauss(NG, qx, qw);
-  double g[kMaxN][kMaxN][kMaxN] = {};
-  for (int q = 0; q < NG; ++q) {
-    leg(qx[q], L);
-    for (int k = 0; k < N; ++k)
-      for (int a = 0; a < N; ++a)
-        for (int b = 0; b < N; ++b) g[k][a][b] += qw[q] * L[k][a] * L[k][b];
-  }
-  double G[ND][ND] = {};
-  for (int k = 1; k < ND; ++k) {
-    int kx = k % N, ky = DIM == 2 ? k / N : 0;
-    // h^(2|k| - dim) (2/dx)^(2kx) (2/dy)^(2ky) |J|
-    double rho = pow(2.0 * ax, 2 * kx) * (DIM == 2 ? pow(2.0 * ay, 2 * ky) : 1.0) /
-                 (DIM == 2 ? 4.0 * ax * ay : 2.0 * ax);
-    for (int a = 0; a < ND; ++a)
-      for (int b = 0; b < ND; ++b) {
-        double v = g[kx][a % N][b % N];
-        if (DIM == 2) v *= g[ky][a / N][b / N];
-        G[a][b] += rho * v;
-      }
-  }
-  double R[NS][NS] = {};
-  for (int j = 0; j < NS; ++j) {
-    double s = G[j + 1][j + 1];
-    for (int k = 0; k < j; ++k) s -= R[k][j] * R[k][j];
-    if (!(s > 0.0)) return false;
-    R[j][j] = sqrt(s);
-    for (int i = j + 1; i < NS; ++i) {
-      double v = G[j + 1][i + 1];
-      for (int k = 0; k < j; ++k) v -= R[k][j] * R[k][i];
-      R[j][i] = v / R[j][j];
-    }
-  }
-  for (int i = 0; i < NS; ++i)
-    for (int j = 0; j < NS; ++j) t.R[i][j] = (float)R[i][j];
-  double Gs[2][kMaxN][kMaxN] = {};
-  for (int si = 0; si < 2; ++si)
-    for (int a = 0; a < N; ++a)
-      for (int k = 0; k < N; ++k) {
-        double acc = 0.0, fk = 1.0;
-        for (int i = 2; i <= k; ++i) fk *= i;
-        for (int q = 0; q < NG; ++q) {
-          leg(qx[q], L);
-          acc += qw[q] * L[0][a] * pow(qx[q] - (si ? 1.0 : -1.0), k) / fk;
-        }
-        Gs[si][a][k] = 0.5 * (2 * a + 1) * acc;
-      }
-  for (int l = 0; l < NC; ++l) {
-    int sxi = l & 1, syi = (l >> 1) & 1;
-    for (int i = 0; i < NS; ++i)
-      for (int j = 0; j < NS; ++j) {
-        double acc = 0.0;
-        for (int k = i; k < NS; ++k) {
-          int a = k + 1, b = j + 1;
-          double c = Gs[sxi][a % N][b % N];
-          if (DIM == 2) c *= Gs[syi][a / N][b / N];
-          acc += R[i][k] * c;
-        }
-        t.A[l][i][j] = (float)acc;
-      }
-  }
-  return true;
-}
-
 // Large enough for every DgTables<DIM, P> instance.
 union AnyTables {
   cvw::DgTables<1, 1> t11;
@@ -245,8 +86,10 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
                                             void* stream) {
   using namespace cvw;
   if (!d || !u || !(dt > 0.0)) return CVWENO_ERR_ARG;
+  // the checks of cvweno_mesh_create, in its order and with its codes
   if (d->dim != 1 && d->dim != 2) return CVWENO_ERR_ARG;
   if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return CVWENO_ERR_ARG;
+  if (d->nx > (1 << 24) || (d->dim == 2 && d->ny > (1 << 20))) return CVWENO_ERR_ARG;
   if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0))) return CVWENO_ERR_ARG;
   for (int i = 0; i < 4; ++i)
     if (d->bc[i] != CVWENO_PERIODIC && d->bc[i] != CVWENO_TRANSMISSIVE) return CVWENO_ERR_ARG;
@@ -257,10 +100,14 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   if (!(p.eps > 0.0) || !(p.q >= 1.0) || !(p.gamma_vertex > 0.0) || (1 << d->dim) * p.gamma_vertex >= 1.0)
     return CVWENO_ERR_ARG;
   if (p.sensor_mode < 0 || p.sensor_mode > 2) return CVWENO_ERR_ARG;
-  if (p.hweno_limiter || p.positivity) return CVWENO_ERR_UNSUPPORTED;  // limited steps are not in this variant
-  if (d->kind != CVWENO_DG || d->degree < 1 || d->degree > kMaxP) return CVWENO_ERR_UNSUPPORTED;
+  if (p.hweno_limiter != 0 && p.hweno_limiter != 1) return CVWENO_ERR_ARG;
+  if (p.positivity != 0 && p.positivity != 1) return CVWENO_ERR_ARG;
+  if (d->kind != CVWENO_DG && d->kind != CVWENO_CG) return CVWENO_ERR_ARG;
+  if (d->degree < 1 || d->degree > kMaxP) return CVWENO_ERR_UNSUPPORTED;
   if (p.r != floor(p.r) || p.r < 1.0 || p.r > 8.0) return CVWENO_ERR_UNSUPPORTED;
   if ((d->system == CVWENO_KPP || d->system == CVWENO_EULER) && d->dim != 2) return CVWENO_ERR_UNSUPPORTED;
+  // what this variant leaves out: CG meshes and the limited steps
+  if (d->kind != CVWENO_DG || p.hweno_limiter || p.positivity) return CVWENO_ERR_UNSUPPORTED;
 
   // the mesh description this step needs, on the stack
   cvweno_mesh_s m;
@@ -286,19 +133,8 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   m.h = d->dim == 2 ? sqrt(m.dx * m.dx + m.dy * m.dy) : m.dx;
 
   AnyTables tabs;
-  bool ok = false;
-  switch (m.dim * 10 + m.p) {
-    case 11: ok = fill_tables(tabs.t11, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t11); break;
-    case 12: ok = fill_tables(tabs.t12, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t12); break;
-    case 13: ok = fill_tables(tabs.t13, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t13); break;
-    case 14: ok = fill_tables(tabs.t14, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t14); break;
-    case 21: ok = fill_tables(tabs.t21, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t21); break;
-    case 22: ok = fill_tables(tabs.t22, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t22); break;
-    case 23: ok = fill_tables(tabs.t23, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t23); break;
-    case 24: ok = fill_tables(tabs.t24, m.dx, m.dy, m.h); m.tables_bytes = sizeof(tabs.t24); break;
-    default: return CVWENO_ERR_UNSUPPORTED;
-  }
-  if (!ok) return CVWENO_ERR_ARG;
+  const cvweno_status tst = fill_dg_tables(m.dim, m.p, m.dx, m.dy, &tabs, sizeof(tabs), &m.tables_bytes);
+  if (tst != CVWENO_OK) return tst;
   m.tables = &tabs;
 
   DeviceSlots slots;

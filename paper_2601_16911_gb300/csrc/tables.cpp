@@ -5,74 +5,78 @@
 // of the Legendre Jacobi matrix (cyclic Jacobi rotations), Legendre derivatives by
 // the recurrence D^k P_{m+1} = D^k P_{m-1} + (2m+1) D^{k-1} P_m, the Taylor->Legendre
 // corner maps by exact quadrature of the Taylor monomials, and the element semi-norm
-// (eq. snorm) as a Gram matrix reduced by Cholesky factorisation.
+// (eq. snorm) as a Gram matrix reduced by Cholesky factorisation.  The reference-cell
+// tabulations are built in fixed-size stack arrays and written into a caller-provided
+// DgTables (fill_dg_tables), with no allocation: the mesh path and the allocation-free
+// step (noalloc.cu) share this one builder.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
-
-#include <vector>
 
 #include "cvweno_internal.cuh"
 
 namespace cvw {
 namespace {
 
-// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi rotations.
-// a (n x n, row-major) is destroyed; eigenvalues to lam, eigenvectors as columns of v.
-void jacobi_eigen(int n, std::vector<double>& a, std::vector<double>& lam, std::vector<double>& v) {
-  v.assign(n * n, 0.0);
-  for (int i = 0; i < n; ++i) v[i * n + i] = 1.0;
+constexpr int kMaxEig = kMaxGaussRule;  // largest eigenproblem: the largest Gauss rule
+
+// Eigen-decomposition of a small symmetric matrix (n <= kMaxEig) by cyclic Jacobi
+// rotations.  a is destroyed; eigenvalues to lam, eigenvectors as columns of v.
+void jacobi_eigen(int n, double a[kMaxEig][kMaxEig], double lam[kMaxEig], double v[kMaxEig][kMaxEig]) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) v[i][j] = i == j ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 100; ++sweep) {
     double off = 0.0;
     for (int i = 0; i < n; ++i)
-      for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
+      for (int j = i + 1; j < n; ++j) off += a[i][j] * a[i][j];
     if (off < 1e-300) break;
     for (int pi = 0; pi < n; ++pi) {
       for (int qi = pi + 1; qi < n; ++qi) {
-        double apq = a[pi * n + qi];
+        double apq = a[pi][qi];
         if (fabs(apq) < 1e-300) continue;
-        double theta = (a[qi * n + qi] - a[pi * n + pi]) / (2.0 * apq);
+        double theta = (a[qi][qi] - a[pi][pi]) / (2.0 * apq);
         double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
         double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
         for (int k = 0; k < n; ++k) {  // columns p, q
-          double akp = a[k * n + pi], akq = a[k * n + qi];
-          a[k * n + pi] = c * akp - s * akq;
-          a[k * n + qi] = s * akp + c * akq;
+          double akp = a[k][pi], akq = a[k][qi];
+          a[k][pi] = c * akp - s * akq;
+          a[k][qi] = s * akp + c * akq;
         }
         for (int k = 0; k < n; ++k) {  // rows p, q
-          double apk = a[pi * n + k], aqk = a[qi * n + k];
-          a[pi * n + k] = c * apk - s * aqk;
-          a[qi * n + k] = s * apk + c * aqk;
+          double apk = a[pi][k], aqk = a[qi][k];
+          a[pi][k] = c * apk - s * aqk;
+          a[qi][k] = s * apk + c * aqk;
         }
         for (int k = 0; k < n; ++k) {
-          double vkp = v[k * n + pi], vkq = v[k * n + qi];
-          v[k * n + pi] = c * vkp - s * vkq;
-          v[k * n + qi] = s * vkp + c * vkq;
+          double vkp = v[k][pi], vkq = v[k][qi];
+          v[k][pi] = c * vkp - s * vkq;
+          v[k][qi] = s * vkp + c * vkq;
         }
       }
     }
   }
-  lam.resize(n);
-  for (int i = 0; i < n; ++i) lam[i] = a[i * n + i];
+  for (int i = 0; i < n; ++i) lam[i] = a[i][i];
 }
 
 // Golub-Welsch: nodes = eigenvalues of the symmetric Jacobi matrix of the Legendre
-// recurrence, weights = 2 * (first eigenvector component)^2.  Ascending nodes.
-void gauss_golub_welsch(int n, double* x, double* w) {
-  std::vector<double> J(n * n, 0.0), lam, V;
+// recurrence, weights = 2 * (first eigenvector component)^2.  Ascending nodes; returns
+// false (writing nothing) unless 1 <= n <= kMaxEig.
+bool gauss_golub_welsch(int n, double* x, double* w) {
+  if (n < 1 || n > kMaxEig) return false;
+  double J[kMaxEig][kMaxEig] = {}, lam[kMaxEig], V[kMaxEig][kMaxEig];
   for (int k = 1; k < n; ++k) {
     double b = k / sqrt(4.0 * k * k - 1.0);
-    J[(k - 1) * n + k] = J[k * n + k - 1] = b;
+    J[k - 1][k] = J[k][k - 1] = b;
   }
   jacobi_eigen(n, J, lam, V);
-  std::vector<int> idx(n);
+  int idx[kMaxEig];
   for (int i = 0; i < n; ++i) idx[i] = i;
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j)
       if (lam[idx[j]] < lam[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
   for (int i = 0; i < n; ++i) {
     x[i] = lam[idx[i]];
-    double v0 = V[0 * n + idx[i]];
+    double v0 = V[0][idx[i]];
     w[i] = 2.0 * v0 * v0;
   }
   // symmetrise (the rule is symmetric about 0)
@@ -83,6 +87,7 @@ void gauss_golub_welsch(int n, double* x, double* w) {
     w[i] = w[n - 1 - i] = wm;
   }
   if (n % 2) x[n / 2] = 0.0;
+  return true;
 }
 
 // D^k P_m(x) for m <= mmax, k <= kmax: out[k][m] (row stride mmax+1).
@@ -106,13 +111,12 @@ double factorial(int k) {
   return f;
 }
 
+// The reference-cell tabulations of a dx x dy cell into *t (no allocation).
 template <int DIM, int P>
-cvweno_status fill(cvweno_mesh m) {
+cvweno_status fill_into(DgTables<DIM, P>* t, double dx, double dy) {
   using T = DgTables<DIM, P>;
   constexpr int N = T::N, ND = T::ND, NS = T::NS, NC = T::NC;
-  T* t = (T*)calloc(1, sizeof(T));
-  if (!t) return CVWENO_ERR_NOMEM;
-  const double dx = m->dx, dy = m->dy;
+  memset(t, 0, sizeof(T));
   // h/dx and h/dy (h = sqrt(dx^2 + dy^2) in 2D, dx in 1D) from the aspect ratio alone:
   // every scaling below is a function of these two ratios, so square cells of any size
   // get bitwise the same tabulations (except tscale)
@@ -145,7 +149,7 @@ cvweno_status fill(cvweno_mesh m) {
   const int NG = 8;
   double qx[NG], qw[NG];
   gauss_golub_welsch(NG, qx, qw);
-  std::vector<double> g((size_t)N * N * N, 0.0);  // [k][a][b]
+  double g[N * N * N] = {};  // [k][a][b]
   double tq[N * N];
   for (int q = 0; q < NG; ++q) {
     legendre_derivs(qx[q], P, P, tq);
@@ -156,7 +160,7 @@ cvweno_status fill(cvweno_mesh m) {
   // element semi-norm Gram matrix on modes (eq. snorm), physical scaling folded in:
   // h^(2|k| - dim) (2/dx)^(2kx) (2/dy)^(2ky) |J| = (2h/dx)^(2kx) (2h/dy)^(2ky) |J| / h^dim
   // with |J| / h^dim = 1 / (4 ax ay) in 2D and 1 / (2 ax) in 1D
-  std::vector<double> G((size_t)ND * ND, 0.0);
+  double G[ND * ND] = {};
   for (int k = 1; k < ND; ++k) {
     int kx = k % N, ky = DIM == 2 ? k / N : 0;
     double rho = pow(2.0 * ax, 2 * kx) * (DIM == 2 ? pow(2.0 * ay, 2 * ky) : 1.0) /
@@ -170,11 +174,11 @@ cvweno_status fill(cvweno_mesh m) {
       }
   }
   // Cholesky G[1:,1:] = R^T R, R upper triangular
-  std::vector<double> R((size_t)NS * NS, 0.0);
+  double R[NS * NS] = {};
   for (int j = 0; j < NS; ++j) {
     double s = G[(j + 1) * ND + (j + 1)];
     for (int k = 0; k < j; ++k) s -= R[k * NS + j] * R[k * NS + j];
-    if (!(s > 0.0)) { free(t); return CVWENO_ERR_ARG; }
+    if (!(s > 0.0)) return CVWENO_ERR_ARG;
     R[j * NS + j] = sqrt(s);
     for (int i = j + 1; i < NS; ++i) {
       double v = G[(j + 1) * ND + (i + 1)];
@@ -201,7 +205,7 @@ cvweno_status fill(cvweno_mesh m) {
   for (int l = 0; l < NC; ++l) {
     int sxi = l & 1, syi = (l >> 1) & 1;
     // C[a][k] for a, k in 1..ND-1, then A = R C
-    std::vector<double> C((size_t)NS * NS);
+    double C[NS * NS];
     for (int a = 1; a < ND; ++a)
       for (int k = 1; k < ND; ++k) {
         int ax = a % N, ay = DIM == 2 ? a / N : 0, kx = k % N, ky = DIM == 2 ? k / N : 0;
@@ -215,6 +219,20 @@ cvweno_status fill(cvweno_mesh m) {
         for (int k = i; k < NS; ++k) acc += R[i * NS + k] * C[k * NS + j];
         t->A[l][i][j] = (float)acc;
       }
+  }
+  return CVWENO_OK;
+}
+
+// The mesh's own copy of its tabulations (owned by the mesh).
+template <int DIM, int P>
+cvweno_status fill(cvweno_mesh m) {
+  using T = DgTables<DIM, P>;
+  T* t = (T*)calloc(1, sizeof(T));
+  if (!t) return CVWENO_ERR_NOMEM;
+  cvweno_status st = fill_into<DIM, P>(t, m->dx, m->dy);
+  if (st != CVWENO_OK) {
+    free(t);
+    return st;
   }
   m->tables = t;
   m->tables_bytes = sizeof(T);
@@ -230,13 +248,14 @@ void gll_nodes(int p, double* x) {
   x[p] = 1.0;
   const int n = p - 1;
   if (n <= 0) return;
-  std::vector<double> J((size_t)n * n, 0.0), lam, V;
+  double J[kMaxEig][kMaxEig] = {}, lam[kMaxEig], V[kMaxEig][kMaxEig];
   for (int k = 1; k < n; ++k) {
     const double b = sqrt(k * (k + 2.0) / ((2.0 * k + 1.0) * (2.0 * k + 3.0)));
-    J[(k - 1) * n + k] = J[k * n + k - 1] = b;
+    J[k - 1][k] = J[k][k - 1] = b;
   }
   jacobi_eigen(n, J, lam, V);
-  std::vector<double> srt(lam);
+  double srt[kMaxEig];
+  for (int i = 0; i < n; ++i) srt[i] = lam[i];
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j)
       if (srt[j] < srt[i]) { double t = srt[i]; srt[i] = srt[j]; srt[j] = t; }
@@ -331,7 +350,21 @@ cvweno_status fill_cg(cvweno_mesh m) {
 
 }  // namespace
 
-void gauss_rule(int n, double* x, double* w) { gauss_golub_welsch(n, x, w); }
+bool gauss_rule(int n, double* x, double* w) { return gauss_golub_welsch(n, x, w); }
+
+cvweno_status fill_dg_tables(int dim, int p, double dx, double dy, void* out, size_t capacity, size_t* bytes) {
+  switch (dim * 10 + p) {
+#define CVW_FILL(D, Q)                                                               \
+  case D * 10 + Q:                                                                   \
+    if (capacity < sizeof(DgTables<D, Q>)) return CVWENO_ERR_ARG;                    \
+    *bytes = sizeof(DgTables<D, Q>);                                                 \
+    return fill_into<D, Q>(static_cast<DgTables<D, Q>*>(out), dx, dy);
+    CVW_FILL(1, 1) CVW_FILL(1, 2) CVW_FILL(1, 3) CVW_FILL(1, 4)
+    CVW_FILL(2, 1) CVW_FILL(2, 2) CVW_FILL(2, 3) CVW_FILL(2, 4)
+#undef CVW_FILL
+    default: return CVWENO_ERR_UNSUPPORTED;
+  }
+}
 
 void legendre_values(double x, int mmax, double* out) { legendre_derivs(x, mmax, 0, out); }
 
