@@ -121,27 +121,34 @@ typedef struct {
 void cvweno_default_params(cvweno_params* p);
 
 /* Build the mesh: host tables (vertex patches, colouring), basis tabulations in
- * FP64 rounded once to FP32, device scratch.  desc and out are host pointers.
+ * FP64 rounded once to FP32, device scratch.  The discretisation is that of Sec. 2
+ * (the uniform partition of Sec. 2 eq. pde's domain into cells K_e of diameter h_e,
+ * Sec. 2.1 DG space V_h of tensor polynomials Q_p; Sec. 2.2 for the CG space) with the
+ * vertex patches C(x_i) of Sec. 3.2 (the cells meeting at vertex x_i).  desc and out are host pointers.
  * Returns ERR_ARG for inconsistent sizes/sides, ERR_UNSUPPORTED for degree > 4, 1D
  * Euler/KPP, CG with Euler or a transmissive side, or a non-integer r.  Records the
  * current device as the mesh's device. */
 cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* desc, cvweno_mesh* out);
 
-/* Free everything the mesh owns (synchronises its device).  NULL is accepted. */
+/* Free everything the mesh owns (synchronises its device).  NULL is accepted.  (Resource
+ * management; no passage of the paper.) */
 cvweno_status cvweno_mesh_destroy(cvweno_mesh m);
 
 /* Sizes (host out-pointers, each may be NULL): cells, DOFs per cell per variable
- * ((p+1)^dim), conserved variables (1 or 4), vertices (periodic sides identify
- * their vertices), quadrature points per cell ((p+1)^dim Gauss-Legendre). */
+ * ((p+1)^dim, the dimension of Q_p on one cell, Sec. 2.1), conserved variables (1 or 4;
+ * Sec. 5.4 for Euler), vertices x_i (Sec. 3.2; periodic sides identify their vertices),
+ * quadrature points per cell ((p+1)^dim Gauss-Legendre, the nodes x_q of Sec. 4). */
 cvweno_status cvweno_mesh_info(cvweno_mesh m, int64_t* ncells, int64_t* ndof_per_var, int* nvars,
                                int64_t* nverts, int* nquad);
 
-/* Number of floats of one state (host out-pointer): nvars * ncells * (p+1)^dim for DG,
+/* Number of floats of one state (host out-pointer; Sec. 2.1 DG, Sec. 2.2 CG spaces):
+ * nvars * ncells * (p+1)^dim for DG,
  * nvars * (p nx) * (p ny) nodal values for CG (GLL nodes of the periodic lattice,
  * node I + (p nx) J). */
 cvweno_status cvweno_state_size(cvweno_mesh m, int64_t* nstate);
 
-/* Host copies of the integer mesh tables (host arrays, each may be NULL):
+/* Host copies of the integer mesh tables (host arrays, each may be NULL), the vertex
+ * patches C(x_i) of Sec. 3.2 (eq. taylorcand averages over them):
  *   cell_vertices[ncells][2^dim]  vertex of corner c = cx + 2 cy of each cell
  *   vertex_cells[nverts][2^dim]   cells around each vertex in the fixed slot order
  *                                 SW, SE, NW, NE (1D: W, E); -1 where a transmissive
@@ -179,30 +186,39 @@ cvweno_status cvweno_sensor(cvweno_mesh m, const float* u, float* gamma, float* 
 cvweno_status cvweno_residual_ex(cvweno_mesh m, const float* u, const int32_t* troubled_override, float* dudt,
                                  float* gamma, float* nu, float* alpha, int32_t* troubled, void* stream);
 
-/* Stages (a)-(e): dudt = M^{-1} r (device, state layout). */
+/* Stages (a)-(e): dudt = M^{-1} r (device, state layout): r is the stabilised residual of
+ * Sec. 2.1 eq. convop plus the dissipation of Sec. 2.2 eq. stab / eq. lostab, with the
+ * sensor of Sec. 3.2 eq. finalweno and Sec. 2.2 eq. gamma and the quadrature weights of
+ * Sec. 4 eq. alphaq; M is the (diagonal, Legendre) mass matrix. */
 cvweno_status cvweno_residual(cvweno_mesh m, const float* u, float* dudt, void* stream);
 
-/* One SSP-RK3 step (Shu-Osher form) in place on u (device).  dt > 0: that step size,
+/* One SSP-RK3 step (Shu-Osher form) in place on u (device): the explicit third-order
+ * strong-stability-preserving Runge-Kutta scheme of Sec. 5 applied to the semi-discrete
+ * system of Sec. 2.2 eq. sdstab, each stage a cvweno_residual evaluation.  dt > 0: that step size,
  * no synchronisation.  dt <= 0: dt = cfl * min(dx, dy) / (dim * max lambda_e), which
  * reads the FP64 maximum back (synchronises) and also checks the status word.
  * dt_used (host, may be NULL) receives the step size. */
 cvweno_status cvweno_step(cvweno_mesh m, float* u, double dt, double cfl, double* dt_used, void* stream);
 
-/* nsteps SSP-RK3 steps of fixed size dt > 0, enqueued without synchronisation.  A 1D
+/* nsteps SSP-RK3 steps (Sec. 5, as cvweno_step) of fixed size dt > 0, enqueued without
+ * synchronisation.  A 1D
  * scalar DG mesh of at most 128 cells without a limiter (one tile) runs all the steps of
  * the call in one kernel launch (cvweno_step: its one step), unless kernel timing is on;
  * the results are bitwise those of one launch per stage. */
 cvweno_status cvweno_advance(cvweno_mesh m, float* u, double dt, int nsteps, void* stream);
 
 /* FP64 totals sum_e int_{K_e} u_h of every conserved variable into totals[nvars]
- * (host).  Synchronises. */
+ * (host): the totals the scheme conserves (Sec. 4: the stabilisation keeps the zero-sum
+ * property s_h^e(u_h, 1) = 0, which gives discrete conservation).  Synchronises. */
 cvweno_status cvweno_mass_total(cvweno_mesh m, const float* u, double* totals, void* stream);
 
-/* FP64 maximum over cells of lambda_e (the CFL wave speed) into *lam (host).
- * Synchronises and checks the status word. */
+/* FP64 maximum over cells of lambda_e (the wave speed of Sec. 2.2 eq. lostab, read as
+ * max |f'(u_h)| over the cell's nodes; the CFL time step of cvweno_step follows from it)
+ * into *lam (host).  Synchronises and checks the status word. */
 cvweno_status cvweno_max_wavespeed(cvweno_mesh m, const float* u, double* lam, void* stream);
 
-/* Synchronise the stream, read and clear the mesh's device status word. */
+/* Synchronise the stream, read and clear the mesh's device status word.  (Error
+ * reporting; no passage of the paper.) */
 cvweno_status cvweno_status_check(cvweno_mesh m, void* stream);
 
 /* HWENO limiter (Sec. 3): out = u, except that every cell whose computed sensor gamma_e
@@ -405,7 +421,7 @@ cvweno_status cvweno_mlp_fallbacks(cvweno_mlp n, uint64_t* count, int reset, voi
 cvweno_status cvweno_step_static(const cvweno_mesh_desc* desc, float* u, double dt, int32_t* status_out,
                                  void* stream);
 
-/* Static description of a status code. */
+/* Static description of a status code.  (Error reporting; no passage of the paper.) */
 const char* cvweno_status_string(cvweno_status s);
 
 #ifdef __cplusplus
