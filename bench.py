@@ -39,7 +39,7 @@ WORKLOAD = ("KPP 2D, f=(sin u, cos u), [-2,2]^2 periodic, 256x256 quads, DG and 
 SEED = 0
 SURROGATE_P = 2  # degree of the surrogate workload (--surrogate-degree)
 # --impl reference: mesh size of the bounded sample each reference step runs (None: full)
-REFERENCE_SAMPLE_N = {"kpp": 16, "euler": 16, "burgers1d": None, "batched": 16, "surrogate": 16}
+REFERENCE_SAMPLE_N = {"kpp": 64, "euler": 32, "burgers1d": None, "batched": 32, "surrogate": 64}
 
 
 def problems(workload: str, n_scale: int | None = None):
@@ -199,6 +199,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fp32_alu_peak(dev, sm_mhz: float):
+    """FP32 FMA peak of the device (TFLOP/s) and its description: SMs (read from the
+    device) x 128 FP32 lanes x 2 flop x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz"
+
+
+def host_cpu():
+    """(logical cores available to this process, CPU model name) of the host."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return cores, model
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -232,18 +258,14 @@ def fma_per_cell_euler(p: int, troubled_fraction: float) -> float:
             + 4 * (14 * n**3 + 20 * n**2) + 30 * (n**2 + 8 * n))
 
 
-def fma_per_cell_cg_cells(p: int, troubled_fraction: float) -> float:
-    """The CG cell kernel: the DG count of stages (a)-(e) less the face part of (e) (a
-    continuous solution has no face fluxes), plus the nodal -> modal map of the tile and halo cells (2n^3 each; 180 halo cells per
-    128-cell tile), the local integrals int phi grad u of the tile's cells (4n^3 each, by
-    tensor factors) and of the 52 halo-ring cells on the node row or column they share
-    with the tile (4n^2 each), and P_h grad u at the cell's Gauss points (4n^3) and nodes
-    (8n^2)."""
+def fma_per_cell_cg_halo(p: int) -> float:
+    """Implementation work of the CG cell kernel beyond the method's count, per tile cell:
+    the nodal -> modal map (2n^3) of the 52 halo cells around a 128-cell tile and the
+    local integrals of the halo ring on the node row or column it shares with the tile
+    (4n^2 each) -- halo recomputation, reported beside the method's figure."""
     n = p + 1
-    halo = 180.0 / 128.0
     ring = 52.0 / 128.0
-    return (fma_per_cell(p, troubled_fraction) - fma_face_terms(p) + halo * 2 * n**3 + 4 * n**3 + ring * 4 * n**2 + 4 * n**3
-            + 8 * n**2)
+    return ring * 2 * n**3 + ring * 4 * n**2
 
 
 def bytes_per_dof_stage() -> float:
@@ -296,8 +318,13 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    cores, model = host_cpu()
+    threads = O.set_threads(cores)
+    nsamp = REFERENCE_SAMPLE_N.get(args.workload)
+    if nsamp and threads < 8:  # keep the run within minutes on a host without OpenMP threads
+        nsamp //= 2
     work = [(d, O.project(d, *ic).astype(np.float32).astype(np.float64), dt)
-            for _, d, ic, dt in problems(args.workload, REFERENCE_SAMPLE_N.get(args.workload))]
+            for _, d, ic, dt in problems(args.workload, nsamp)]
     units = sum(3 * int(np.prod(O.state_shape(d))) for d, _, _ in work)
 
     def step():
@@ -310,16 +337,18 @@ def run_reference(args):
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
+    O.set_threads(1)
     value = units * args.steps / dt
-    nsamp = REFERENCE_SAMPLE_N.get(args.workload)
     sample = ("one SSP-RK3 step of every discretisation of the workload per benchmark step"
-              + (f", at {nsamp}x{nsamp} cells" if nsamp else ""))
+              + (f", at {nsamp}x{nsamp} cells" if nsamp else "") + f", {threads} threads (OpenMP over cells)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "reference": "FP64 CPU oracle (plain C, single thread)",
+            "config": {"workload": WORKLOADS[args.workload],
+                       "reference": f"FP64 CPU oracle (plain C, OpenMP over cells, {threads} threads)",
                        "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": model, "host_cores": cores},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -334,17 +363,29 @@ def cpu_baseline_sample(workload: str):
 
     n = {"kpp": 128, "euler": 64, "burgers1d": None, "batched": 48, "surrogate": 96}[workload]
     work = [(d, O.project(d, *ic), dt) for _, d, ic, dt in problems(workload, n)]
-    t0 = time.perf_counter()
-    units = 0
-    for d, u, dt in work:
-        O.ssprk3(d, u, dt, 1)
-        units += 3 * int(np.prod(u.shape))
-    el = time.perf_counter() - t0
+    cores, model = host_cpu()
+
+    def timed(threads):
+        used = O.set_threads(threads)
+        t0 = time.perf_counter()
+        units = 0
+        for d, u, dt in work:
+            O.ssprk3(d, u, dt, 1)
+            units += 3 * int(np.prod(u.shape))
+        return units / (time.perf_counter() - t0), time.perf_counter() - t0, used
+
+    try:
+        v1, el1, _ = timed(1)
+        vn, eln, used = timed(cores)
+    finally:
+        O.set_threads(1)
     where = f"at {n}x{n} cells" if n else "at full size"
     if workload == "batched":
         where += " (one instance of each degree)"
-    return {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one SSP-RK3 step of every discretisation of the workload {where} ({el:.1f} s, 1 thread)"}
+    return {"value": vn, "unit": UNIT, "cores": used, "kind": "oracle", "cpu_model": model, "host_cores": cores,
+            "sample": f"one SSP-RK3 step of every discretisation of the workload {where}: {eln:.1f} s on {used} "
+                      f"threads (OpenMP over cells), {el1:.1f} s on 1 thread",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1}}
 
 
 def l1_vs_fp64(workload: str):
@@ -597,10 +638,14 @@ def run_gpu(args):
     out = mdom.residual_ex(states[kdom])
     troubled_frac = float(out["troubled"].float().mean().item())
     pdom = mdom.desc["degree"]
+    impl_fma = 0.0
     if args.workload == "euler":
         fma = fma_per_cell_euler(pdom, troubled_frac)
     elif mdom.desc.get("kind", 0) == I.CG:
-        fma = fma_per_cell_cg_cells(pdom, troubled_frac)
+        # the method's count of SURVEY-style stages (a)-(e) for Q_p (the same per-cell
+        # figure as DG); the kernel's halo recomputation is implementation work
+        fma = fma_per_cell(pdom, troubled_frac)
+        impl_fma = fma_per_cell_cg_halo(pdom)
     elif mdom.desc["dim"] == 1:
         n1 = pdom + 1
         fma = 3 * (2 * n1 * n1) + 4 * n1 + 2 * n1 * n1 + troubled_frac * 2 * n1 ** 3 + 6 * n1 * n1
@@ -609,7 +654,7 @@ def run_gpu(args):
     flops = 2.0 * fma * mdom.ncells * dom_stages
     peaks, peak_kind = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak_tflops, peak_desc = fp32_alu_peak(dev, sm_mhz)
     achieved_tflops = flops / (launch_ms * 1e-3) / 1e12
     hbm_gbs = bytes_per_dof_stage() * mdom.nstate * dom_stages / (launch_ms * 1e-3) / 1e9
     traffic = measured_traffic({"kpp": "cg_stage_cells_q3_kpp256", "euler": "dg_euler_stage_q3_euler512",
@@ -624,8 +669,10 @@ def run_gpu(args):
                            "the kernel (a whole SSP-RK3 step), after the metric's timed loop (L2 flushed between "
                            "steps)"),
                 "stages_per_launch": dom_stages,
-                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
-                "flops_per_launch": flops, "troubled_fraction": troubled_frac,
+                "peak_source": f"{peak_desc} ({peak_kind} sm_max_mhz)",
+                "flops_per_launch": flops, "flops_basis": "the method's FMA count per cell x 2 x cells",
+                "implementation_flops_per_launch": 2.0 * impl_fma * mdom.ncells * dom_stages,
+                "troubled_fraction": troubled_frac,
                 "hbm_algorithmic_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks.get("hbm_gbs", 6800.0)}
     if args.workload == "kpp":
         # the DG Q3 stage kernel beside it: one launch per stage, its graph's time / 3
@@ -782,14 +829,14 @@ def run_gpu_batched(args, ws, rank, local, dev):
     stage_ms = step_ms / 3.0
     peaks, peak_kind = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak, peak_desc = fp32_alu_peak(dev, sm_mhz)
     achieved = flops / (stage_ms * 1e-3) / 1e12
     nlaunch = 1 if plan["schedule"] == cv.BATCH_FUSED else len({d["degree"] for d in descs})
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                 "traffic": measured_traffic("dg_scalar_batch_burgers64"),
                 "kernel": "dg_scalar_batch<PSEL,BURGERS,TX,TY> (persistent, fused stages a-e + RK combine)",
                 "launch_ms": stage_ms / nlaunch if nlaunch == 1 else None, "stage_ms": stage_ms,
-                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
+                "peak_source": f"{peak_desc} ({peak_kind} sm_max_mhz)",
                 "flops_per_stage": flops,
                 "hbm_algorithmic_gbs": hbm_bytes / (stage_ms * 1e-3) / 1e9,
                 "hbm_frac_of_measured": hbm_bytes / (stage_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
@@ -976,14 +1023,14 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
     flops = 2.0 * fma_per_cell(SURROGATE_P, tf) * m_plain.ncells
     peaks, peak_kind = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak, peak_desc = fp32_alu_peak(dev, sm_mhz)
     achieved = flops / (launch_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                 "traffic": measured_traffic("dg_scalar_stage_q2_surrogate_kpp1024"),
                 "kernel": f"dg_scalar_stage<2,{SURROGATE_P},KPP,16,8,surrogate> (stages a-e + RK, network in stage c)",
                 "launch_ms": launch_ms, "launches_timed": len(dom_ms),
                 "timing": "CUDA events recorded as graph nodes around each launch, in a replay after the timed loop",
-                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
+                "peak_source": f"{peak_desc} ({peak_kind} sm_max_mhz)",
                 "flops_per_launch": flops, "flops_model": "the plain method's count (the work the surrogate replaces)",
                 "hbm_algorithmic_gbs": bytes_per_dof_stage() * m_plain.nstate / (launch_ms * 1e-3) / 1e9}
     # e2e through the public API

@@ -81,6 +81,12 @@
  *       p(U_bar + t (U_q - U_bar)) = eps (one root: p is concave along the line),
  *       scaling the non-mean modes of every variable.  Applied after every RK stage.
  *   P4  a cell whose mean is not admissible is left as it is and reported.
+ * Threads.  The loops over cells, vertices and rows of faces carry OpenMP pragmas (used
+ * when the file is compiled with -fopenmp; or_set_threads picks the count, 1 by default
+ * through the Python wrapper).  Each iteration writes only its own cell's (vertex's, face
+ * row's) entries and adds into them in the same order as a single thread does, so the
+ * results are bitwise the same for every thread count.  Only the timed CPU baseline uses
+ * more than one thread.
  * CG is parity-unpinned against the paper's exact values (A12, A13 are readings); its
  * pins are conservation, the sweeps' convergence to the consistent-mass solve, the
  * shared sensor's pins and the design order / Table bur2 magnitudes.
@@ -89,6 +95,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXP 4
 #define OR_MAXN (OR_MAXP + 1)
@@ -536,6 +545,7 @@ static int or_numflux(const or_mesh* m, const double* UL, const double* UR, doub
  * beta[e][c] = ||u^e||_{x_c}^q with the pointwise semi-norm of eq. pointsnorm. */
 static void or_hermite_m(const or_mesh* m, const double* u, double* T, double* beta) {
   int nk = or_nk(m);
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < m->ncell; ++e) {
     const double* c0 = or_cell(m, u, 0, e);
     for (int c = 0; c < m->ncorner; ++c) {
@@ -556,6 +566,7 @@ static void or_hermite_m(const or_mesh* m, const double* u, double* T, double* b
 /* stage (b): vertex-averaged Taylor data T*[v][k] with equal linear weights */
 static void or_vertex_average_m(const or_mesh* m, const double* T, const double* beta, double* Tstar) {
   int nk = or_nk(m);
+#pragma omp parallel for schedule(static)
   for (int v = 0; v < m->nvert; ++v) {
     double wsum = 0.0;
     double acc[OR_MAXND];
@@ -622,9 +633,17 @@ static int or_sensor_m(const or_mesh* m, const double* u, const double* Tstar, d
                        double* norm0, double* lamv, double* omega) {
   const or_desc* d = &m->d;
   int nk = or_nk(m), nq = m->nq, ncand = m->ncorner + 1;
-  double* Dv = (double*)malloc(sizeof(double) * ncand * nk * nq);
-  if (!Dv) return OR_ERR_NOMEM;
+  int err = OR_OK;
+#pragma omp parallel
+  {
+  double* Dv = (double*)malloc(sizeof(double) * ncand * nk * nq); /* this thread's scratch */
+  if (!Dv) {
+#pragma omp atomic write
+    err = OR_ERR_NOMEM;
+  }
+#pragma omp for schedule(static)
   for (int e = 0; e < m->ncell; ++e) {
+    if (!Dv) continue;
     const double* c0 = or_cell(m, u, 0, e);
     double N2[OR_MAXN + 1] = {0};
     /* derivatives of every candidate at every volume Gauss point */
@@ -686,14 +705,19 @@ static int or_sensor_m(const or_mesh* m, const double* u, const double* Tstar, d
       g = 1.0 - pow(fmin(1.0, sqrt(diff2) / nrm), d->q);
     double lam;
     int st = or_cell_lambda(m, u, e, &lam);
-    if (st) { free(Dv); return st; }
+    if (st) {
+#pragma omp atomic write
+      err = st;
+      continue;
+    }
     gamma[e] = g;
     nu[e] = lam * m->h / (2.0 * m->p);
     if (norm0) norm0[e] = nrm;
     if (lamv) lamv[e] = lam;
   }
   free(Dv);
-  return OR_OK;
+  }
+  return err;
 }
 
 /* stage (d): nonlinear quadrature weights alpha[e][var][q] and the troubled flag */
@@ -701,6 +725,7 @@ static void or_sc_weights_m(const or_mesh* m, const double* u, const double* gam
                             const int* override_troubled, double* alpha, int* troubled) {
   const or_desc* d = &m->d;
   int nq = m->nq, nk = or_nk(m);
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < m->ncell; ++e) {
     int tr = d->sc_quadrature && gamma[e] < d->c_gamma && norm0[e] > 1e-30;
     if (override_troubled && override_troubled[e] >= 0) tr = override_troubled[e] && norm0[e] > 1e-30;
@@ -754,6 +779,7 @@ static int or_residual_m(const or_mesh* m, const double* u, const double* gamma,
   size_t ntot = (size_t)nv * m->ncell * nd;
   for (size_t t = 0; t < ntot; ++t) dudt[t] = 0.0;
   /* volume terms */
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < m->ncell; ++e) {
     double mu = (1.0 - gamma[e]) * nu[e];
     for (int qi = 0; qi < nq; ++qi) {
@@ -788,6 +814,9 @@ static int or_residual_m(const or_mesh* m, const double* u, const double* gamma,
     int nfp = m->dim == 2 ? m->n : 1;
     double fw = m->dim == 2 ? (dirn == 0 ? 0.5 * m->dy : 0.5 * m->dx) : 1.0;
     double nxn = dirn == 0 ? 1.0 : 0.0, nyn = dirn == 0 ? 0.0 : 1.0;
+    int err = OR_OK;
+    /* the faces of one row (b) touch only that row's cells */
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < nb; ++b) {
       for (int a = 0; a < nface; ++a) {
         int aL = a - 1, aR = a;
@@ -806,7 +835,11 @@ static int or_residual_m(const or_mesh* m, const double* u, const double* gamma,
           if (eL < 0) memcpy(UL, UR, sizeof(UL));
           if (eR < 0) memcpy(UR, UL, sizeof(UR));
           int st = or_numflux(m, UL, UR, nxn, nyn, F);
-          if (st) return st;
+          if (st) {
+#pragma omp atomic write
+            err = st;
+            continue;
+          }
           for (int v = 0; v < nv; ++v) {
             for (int mi = 0; mi < nd; ++mi) {
               if (eL >= 0)
@@ -818,6 +851,7 @@ static int or_residual_m(const or_mesh* m, const double* u, const double* gamma,
         }
       }
     }
+    if (err) return err;
   }
   /* mass matrix: diagonal for the Legendre basis, computed by quadrature */
   for (int mi = 0; mi < nd; ++mi) {
@@ -948,23 +982,37 @@ static int or_cg_residual_m(const or_mesh* m, const double* uc, const double* ga
   double* r = (double*)calloc(nn, sizeof(double));
   double* tmp = (double*)malloc(sizeof(double) * nn);
   if (!ML || !Ph || !r || !tmp) { free(ML); free(Ph); free(r); free(tmp); return OR_ERR_NOMEM; }
+  /* every cell's terms are computed into term[e][qi][mi] (in parallel) and added into the
+   * nodes in the order (e, qi, mi), one cell after the other */
+  const size_t nterm = (size_t)nq * nd;
+  double* term = (double*)malloc(sizeof(double) * 2 * nterm * m->ncell);
+  if (!term) { free(ML); free(Ph); free(r); free(tmp); return OR_ERR_NOMEM; }
   or_cg_lumped_mass(m, ML);
   /* P_h grad u: (sum_e int phi_j d_c u) / ML_j */
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < m->ncell; ++e) {
     const double* c = uc + (size_t)e * nd;
+    double* te = term + 2 * nterm * e;
     for (int qi = 0; qi < nq; ++qi) {
       double xi, eta, W;
       or_qpoint(m, qi, &xi, &eta, &W);
       double gx = or_du(m, c, 1, 0, xi, eta), gy = m->dim == 2 ? or_du(m, c, 0, 1, xi, eta) : 0.0;
       for (int mi = 0; mi < nd; ++mi) {
-        int jn = or_cg_node(m, e, mi % m->n, mi / m->n);
         double ph = or_dphi(m, mi, 0, 0, xi, eta);
-        Ph[jn] += W * ph * gx;
-        Ph[nn + jn] += W * ph * gy;
+        te[2 * (qi * nd + mi)] = W * ph * gx;
+        te[2 * (qi * nd + mi) + 1] = W * ph * gy;
       }
     }
   }
+  for (int e = 0; e < m->ncell; ++e)
+    for (int qi = 0; qi < nq; ++qi)
+      for (int mi = 0; mi < nd; ++mi) {
+        int jn = or_cg_node(m, e, mi % m->n, mi / m->n);
+        Ph[jn] += term[2 * (nterm * e + qi * nd + mi)];
+        Ph[nn + jn] += term[2 * (nterm * e + qi * nd + mi) + 1];
+      }
   for (int j = 0; j < nn; ++j) { Ph[j] /= ML[j]; Ph[nn + j] /= ML[j]; }
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < m->ncell; ++e) {
     const double* c = uc + (size_t)e * nd;
     double gxq[OR_MAXND], gyq[OR_MAXND], pxq[OR_MAXND], pyq[OR_MAXND], Wq[OR_MAXND];
@@ -1019,10 +1067,14 @@ static int or_cg_residual_m(const or_mesh* m, const double* uc, const double* ga
       for (int mi = 0; mi < nd; ++mi) {
         double px = or_dphi(m, mi, 1, 0, xi, eta), py = m->dim == 2 ? or_dphi(m, mi, 0, 1, xi, eta) : 0.0;
         double val = W * (px * Fx + (m->dim == 2 ? py * Fy : 0.0)) - nu[e] * al[qi] * W * (px * vx + py * vy);
-        r[or_cg_node(m, e, mi % m->n, mi / m->n)] += val;
+        term[nterm * e + qi * nd + mi] = val;
       }
     }
   }
+  for (int e = 0; e < m->ncell; ++e)
+    for (int qi = 0; qi < nq; ++qi)
+      for (int mi = 0; mi < nd; ++mi) r[or_cg_node(m, e, mi % m->n, mi / m->n)] += term[nterm * e + qi * nd + mi];
+  free(term);
   /* M^{-1} r: lumped mass, then two defect-correction sweeps du += ML^{-1}(r - M_C du) */
   for (int j = 0; j < nn; ++j) dudt[j] = r[j] / ML[j];
   for (int sweep = 0; sweep < 2; ++sweep) {
@@ -1056,6 +1108,18 @@ static const double* or_local_state(const or_mesh* m, const double* u, double** 
 
 static size_t or_state_len(const or_mesh* m) {
   return m->kind == OR_CG ? (size_t)m->nvar * m->nnode : (size_t)m->nvar * m->ncell * m->nd;
+}
+
+/* Threads of the OpenMP loops (n >= 1); returns the count in effect, 1 when the file was
+ * compiled without OpenMP.  The results do not depend on it. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* number of doubles in a state: nvar * ncell * (p+1)^dim (DG) or nvar * nnode (CG) */
@@ -1431,17 +1495,20 @@ int or_ssprk3(const or_desc* d, double* u, double dt, int nsteps) {
   for (int s = 0; s < nsteps && !st; ++s) {
     st = or_residual(d, u, NULL, L, NULL, NULL, NULL, NULL);
     if (st) break;
-    for (size_t t = 0; t < N; ++t) u1[t] = u[t] + dt * L[t];
+#pragma omp parallel for schedule(static)
+    for (long t = 0; t < (long)N; ++t) u1[t] = u[t] + dt * L[t];
     OR_LIMIT_STAGE(u1)
     if (st) break;
     st = or_residual(d, u1, NULL, L, NULL, NULL, NULL, NULL);
     if (st) break;
-    for (size_t t = 0; t < N; ++t) u2[t] = 0.75 * u[t] + 0.25 * (u1[t] + dt * L[t]);
+#pragma omp parallel for schedule(static)
+    for (long t = 0; t < (long)N; ++t) u2[t] = 0.75 * u[t] + 0.25 * (u1[t] + dt * L[t]);
     OR_LIMIT_STAGE(u2)
     if (st) break;
     st = or_residual(d, u2, NULL, L, NULL, NULL, NULL, NULL);
     if (st) break;
-    for (size_t t = 0; t < N; ++t) u[t] = u[t] / 3.0 + 2.0 / 3.0 * (u2[t] + dt * L[t]);
+#pragma omp parallel for schedule(static)
+    for (long t = 0; t < (long)N; ++t) u[t] = u[t] / 3.0 + 2.0 / 3.0 * (u2[t] + dt * L[t]);
     OR_LIMIT_STAGE(u)
   }
 #undef OR_LIMIT_STAGE

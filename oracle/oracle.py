@@ -64,12 +64,14 @@ DEFAULTS = dict(
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into a shared library (plain gcc, -O2, no fast-math)."""
+    """Compile the oracle into a shared library (plain gcc, -O2, no fast-math), with
+    OpenMP where gcc supports it (the results do not depend on the thread count)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -109,8 +111,17 @@ def _load():
                 fn.restype = ctypes.c_int
             lib.or_legendre_dk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
             lib.or_legendre_dk.restype = ctypes.c_double
+            lib.or_set_threads.argtypes = [ctypes.c_int]
+            lib.or_set_threads.restype = ctypes.c_int
+            lib.or_set_threads(1)  # one thread unless a caller asks for more
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's cell loops (1 by default); returns the count in effect (1
+    when it was built without OpenMP).  Results are bitwise the same for any count."""
+    return int(_load().or_set_threads(int(n)))
 
 
 def desc(**kw) -> dict:
