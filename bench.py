@@ -388,39 +388,88 @@ def cpu_baseline_sample(workload: str):
             "single_thread": {"value": v1, "unit": UNIT, "cores": 1}}
 
 
-def l1_vs_fp64(workload: str):
-    """Final-time L1 difference of the FP32 GPU path against the FP64 oracle on a
-    reduced mesh of the workload (32x32 or the full 1D mesh, 10 SSP-RK3 steps)."""
+FINAL_TIME = {"kpp": 1.0, "euler": 0.25, "burgers1d": 0.4, "batched": 0.05, "surrogate": 1.0}
+# mesh of the final-time runs (None: the full mesh); the oracle must follow every step
+FINAL_TIME_N = {"kpp": 24, "euler": 16, "burgers1d": None, "batched": 8, "surrogate": 24}
+
+
+def _steps_to(t_end: float, dt: float):
+    """(number of steps, last step size) that end exactly at t_end."""
+    nsteps = max(1, int(math.ceil(t_end / dt - 1e-9)))
+    return nsteps, t_end - (nsteps - 1) * dt
+
+
+def final_time_l1(workload: str, n=None, surrogate=None):
+    """Every discretisation of the workload run to the workload's final time on a reduced
+    mesh of the same problem: the FP32 GPU path and the FP64 oracle from the same
+    FP32-rounded datum, and the oracle's own one-ulp envelope (reading A23): the oracle
+    restarted from that datum with every coefficient moved by one FP32 ulp up or down
+    (seeded signs; two seeds, the larger difference kept).  Returns, per discretisation,
+    the relative L1(Omega) differences from the oracle's solution; with a surrogate
+    network, also that of the GPU run with the network attached (the oracle runs the
+    plain method)."""
     import numpy as np
     import torch
 
     from oracle import oracle as O
     from paper_2601_16911_gb300 import cvweno as cv
+
+    n = n or FINAL_TIME_N[workload]
+    t_end = FINAL_TIME[workload]
+    cores, _ = host_cpu()
+    O.set_threads(cores)
     out = {}
-    work = problems(workload, 32 if workload != "burgers1d" else None)
-    if workload == "batched":
-        # through the batched path: one batch of the sampled instances
-        b = cv.Batch([d for _, d, _, _ in work])
-        us = [O.project(d, *ic).astype(np.float32).astype(np.float64) for _, d, ic, _ in work]
-        ug = torch.from_numpy(np.concatenate([u.reshape(-1) for u in us]).astype(np.float32)).cuda()
-        b.advance(ug, [dt for _, _, _, dt in work], 10)
-        b.status_check()
-        for k, (label, d, ic, dt) in enumerate(work):
-            ref = O.ssprk3(d, us[k], dt, 10)
-            got = b.view(ug, k).cpu().numpy().astype(np.float64).reshape(us[k].shape)
-            out[label] = O.l1_diff(d, got, ref) / O.l1_diff(d, ref, np.zeros_like(ref))
-        b.close()
-        return out
-    for label, d, ic, dt in work:
-        u = O.project(d, *ic).astype(np.float32).astype(np.float64)
-        ref = O.ssprk3(d, u, dt, 10)
-        mesh = cv.Mesh(d)
-        ug = torch.from_numpy(u.astype(np.float32)).cuda()
-        mesh.advance(ug, dt, 10)
-        mesh.status_check()
-        got = ug.cpu().numpy().astype(np.float64)
-        mesh.close()
-        out[label] = O.l1_diff(d, got, ref) / O.l1_diff(d, ref, np.zeros_like(ref))
+    try:
+        for label, d, ic, dt in problems(workload, n):
+            nsteps, dt_last = _steps_to(t_end, dt)
+            u32 = O.project(d, *ic).astype(np.float32)
+            u = u32.astype(np.float64)
+
+            def oracle_run(v):
+                v = O.ssprk3(d, v, dt, nsteps - 1) if nsteps > 1 else v
+                return O.ssprk3(d, v, dt_last, 1)
+
+            def one_ulp(seed):
+                up = np.random.default_rng(seed).random(u32.shape) < 0.5
+                return np.where(up, np.nextafter(u32, np.float32(np.inf)),
+                                np.nextafter(u32, np.float32(-np.inf))).astype(np.float64)
+
+            ref = oracle_run(u)
+            envs = [oracle_run(one_ulp(seed)) for seed in (1, 2)]
+            ug = torch.from_numpy(u32.copy()).cuda()
+            if workload == "batched":  # through the batched path: a batch of this one instance
+                b = cv.Batch([d])
+                flat = ug.view(-1)
+                if nsteps > 1:
+                    b.advance(flat, [dt], nsteps - 1)
+                b.advance(flat, [dt_last], 1)
+                b.status_check()
+                b.close()
+            else:
+                ug_s = ug.clone()
+                mesh = cv.Mesh(d)
+                if nsteps > 1:
+                    mesh.advance(ug, dt, nsteps - 1)
+                mesh.advance(ug, dt_last, 1)
+                mesh.status_check()
+                if surrogate is not None:
+                    mesh.set_surrogate(surrogate, 0.5)
+                    if nsteps > 1:
+                        mesh.advance(ug_s, dt, nsteps - 1)
+                    mesh.advance(ug_s, dt_last, 1)
+                    mesh.status_check()
+                mesh.close()
+            got = ug.cpu().numpy().astype(np.float64)
+            norm = O.l1_diff(d, ref, np.zeros_like(ref))
+            out[label] = {"l1_rel": O.l1_diff(d, got, ref) / norm,
+                          "envelope_l1_rel": max(O.l1_diff(d, e, ref) for e in envs) / norm,
+                          "cells": f"{d['nx']}x{d['ny']}" if d["dim"] == 2 else f"{d['nx']}",
+                          "t": t_end, "steps": nsteps}
+            if surrogate is not None and workload != "batched":
+                got_s = ug_s.cpu().numpy().astype(np.float64)
+                out[label]["l1_rel_with_surrogate"] = O.l1_diff(d, got_s, ref) / norm
+    finally:
+        O.set_threads(1)
     return out
 
 
@@ -688,7 +737,7 @@ def run_gpu(args):
     l1 = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline_sample(args.workload)
-        l1 = l1_vs_fp64(args.workload)
+        l1 = final_time_l1(args.workload)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -700,7 +749,7 @@ def run_gpu(args):
                        "parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
                        "per_variant_ms": {lb: statistics.mean(per_degree[k]) for k, lb in enumerate(labels)},
                        "wall_s_timed_region": wall,
-                       "l1_rel_vs_fp64_reduced_mesh_10steps": l1,
+                       "l1_vs_fp64_final_time": l1,
                        **({"one_call_run": one_call_run} if one_call_run else {})},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -843,7 +892,7 @@ def run_gpu_batched(args, ws, rank, local, dev):
     cpu = l1 = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline_sample("batched")
-        l1 = l1_vs_fp64("batched")
+        l1 = final_time_l1("batched")
     from collections import Counter
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -859,7 +908,7 @@ def run_gpu_batched(args, ws, rank, local, dev):
                        "batched_over_plain": value / plain_value,
                        "l2": "flushed (512 MB write) between timed steps, outside the timed events",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single GPU", "wall_s_timed_region": wall,
-                       "l1_rel_vs_fp64_reduced_mesh_10steps": l1},
+                       "l1_vs_fp64_final_time": l1},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "steps": e2e_steps, "api": "cvweno_batch_advance via the ctypes binding, pinned host buffers"},
@@ -1051,7 +1100,7 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
     if not args.no_cpu_baseline:
         cpu = cpu_baseline_sample("surrogate")
         cpu["sample"] += "; plain sensor (the oracle runs the method, not the network)"
-        l1 = surrogate_l1_vs_fp64(net)
+        l1 = final_time_l1("surrogate", surrogate=net)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -1065,7 +1114,7 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
                                         data_s=t_data, train_s=t_train),
                        "held_out_quality": quality,
                        "l1_rel_surrogate_vs_plain_gpu_after_timed_steps": l1_full,
-                       "l1_rel_vs_fp64_reduced_mesh_10steps": l1,
+                       "l1_vs_fp64_final_time": l1,
                        "l2": "flushed (512 MB write) between timed steps, outside the timed events"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
@@ -1076,31 +1125,6 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
     m_surr.close()
     net.close()
     return 0
-
-
-def surrogate_l1_vs_fp64(net):
-    """Relative L1 against the FP64 oracle (plain method) after 10 steps at 32^2 on the
-    evaluation seed: the plain FP32 path and the path with the surrogate."""
-    import numpy as np
-    import torch
-
-    from oracle import oracle as O
-    from paper_2601_16911_gb300 import cvweno as cv
-    (label, d, ic, dt), = problems("surrogate", 32)
-    u = O.project(d, *ic).astype(np.float32).astype(np.float64)
-    ref = O.ssprk3(d, u, dt, 10)
-    norm = O.l1_diff(d, ref, np.zeros_like(ref))
-    out = {}
-    for name, use in (("plain", False), ("surrogate", True)):
-        m = cv.Mesh(d)
-        if use:
-            m.set_surrogate(net, 0.5)
-        ug = torch.from_numpy(u.astype(np.float32)).cuda()
-        m.advance(ug, dt, 10)
-        m.status_check()
-        out[name] = O.l1_diff(d, ug.cpu().numpy().astype(np.float64), ref) / norm
-        m.close()
-    return out
 
 
 def main():

@@ -6,8 +6,17 @@ import torch
 from oracle import oracle as O
 from paper_2601_16911_gb300 import cvweno as cv
 
-RES_TOL = 1e-5   # per-stage residual: max |r_gpu - r_oracle| / max |r_oracle|
-GAMMA_TOL = 2e-4  # per-cell sensor (absolute; gamma in [0, 1])
+# The stated bar for every floating-point stage output is 1e-5 (the FP32 path against the
+# FP64 oracle on the same FP32-rounded input):
+RES_TOL = 1e-5    # per-stage residual: max |r_gpu - r_oracle| / max |r_oracle|
+# Per-cell sensor gamma_e in [0, 1], absolute: 1e-5 is about 170 FP32 ulps at 1.  The FP32
+# sensor is a few hundred FMAs deep (Taylor data, vertex and cell Jiang-Shu weights,
+# Gram-form semi-norms); over every parity case of both kernel forms, the largest
+# difference measured on a GB300 was 2.8e-7.
+GAMMA_TOL = 1e-5
+# SC weights alpha_q (eq. alphaq), relative to the cell's largest, on cells that both
+# sides mark troubled: the same bar; the largest measured was 3.4e-7.
+ALPHA_TOL = 1e-5
 
 
 def to_gpu(u):

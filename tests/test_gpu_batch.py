@@ -94,7 +94,8 @@ def test_batch_equals_single_mesh_path():
             torch.cuda.synchronize()
             diff = (b.view(r, k) - single.reshape(-1)).abs().max().item()
             scale = single.abs().max().item()
-            assert diff <= 1e-6 * scale, (plan, k, diff, scale)
+            # the batch runs the single-mesh tile code on every tile: bit for bit
+            assert diff == 0.0, (plan, k, diff, scale)
             m.close()
     b.close()
 
@@ -139,7 +140,7 @@ def test_batch_advance_equals_per_mesh_advance_and_replays():
     torch.cuda.synchronize()
     assert b.status_check() == -1
     diff = (u - ref).abs().max().item()
-    assert diff <= 1e-6 * ref.abs().max().item(), diff
+    assert diff == 0.0, diff  # the same tile code and RK epilogue: bit for bit
     b.close()
 
 
@@ -155,7 +156,7 @@ def test_batch_autotune_picks_a_valid_plan_and_keeps_results():
     assert b.plan()["schedule"] == best["schedule"] and b.plan()["tile"] == best["tile"]
     after = b.residual(u)
     diff = (after - before).abs().max().item()
-    assert diff <= 1e-6 * before.abs().max().item()
+    assert diff == 0.0  # every plan runs the same per-tile arithmetic
     b.close()
 
 
@@ -243,7 +244,7 @@ def test_batch_full_workload_sampled_windows():
         single = m.residual(b.view(u, k).view(m.state_shape).clone())
         torch.cuda.synchronize()
         diff = (b.view(r, k) - single.reshape(-1)).abs().max().item()
-        assert diff <= 1e-6 * single.abs().max().item(), (k, diff)
+        assert diff == 0.0, (k, diff)
         m.close()
     seen = set()
     for k, (d, _) in enumerate(probs):

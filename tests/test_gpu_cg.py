@@ -13,7 +13,7 @@ import torch
 from oracle import oracle as O
 from paper_2601_16911_gb300 import cvweno as cv
 from paper_2601_16911_gb300 import inputs as I
-from tests.gpu_common import RES_TOL, borderline_override, rel_err, rounded, to_gpu
+from tests.gpu_common import ALPHA_TOL, GAMMA_TOL, RES_TOL, borderline_override, rel_err, rounded, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +51,7 @@ def test_cg_projection_parity(name):
     got = mesh.project(*ic).cpu().numpy()
     ref = O.project(d, *ic)
     assert got.shape == ref.shape
+    # GLL interpolation of the datum in FP32 (reading A25): a few ulps; measured 9.7e-7
     assert rel_err(got, ref) < 2e-6
     mesh.close()
 
@@ -67,13 +68,13 @@ def test_cg_full_stage_parity(name):
     got = {k: v.cpu().numpy() for k, v in out.items()}
     mesh.close()
     mask = cg_nonflat(d, u)
-    assert np.abs(got["gamma"] - ref["gamma"])[mask].max() < 2e-4
+    assert np.abs(got["gamma"] - ref["gamma"])[mask].max() < GAMMA_TOL
     assert rel_err(got["nu"], ref["nu"]) < 1e-6
     dec = (np.abs(ref["gamma"] - d["c_gamma"]) >= 1e-4) & mask
     assert np.array_equal(got["troubled"][dec], ref["troubled"][dec])
     both = (got["troubled"] == 1) & (ref["troubled"] == 1) & mask
     if both.any():
-        assert np.abs(got["alpha"][both] - ref["alpha"][both]).max() / np.abs(ref["alpha"][both]).max() < 1e-4
+        assert np.abs(got["alpha"][both] - ref["alpha"][both]).max() / np.abs(ref["alpha"][both]).max() < ALPHA_TOL
     assert rel_err(got["dudt"], ref["dudt"]) < RES_TOL
 
 

@@ -18,7 +18,7 @@ import torch
 from oracle import oracle as O
 from paper_2601_16911_gb300 import cvweno as cv
 from paper_2601_16911_gb300 import inputs as I
-from tests.gpu_common import (GAMMA_TOL, RES_TOL, borderline_override, nonflat_mask, rel_err, residual_pair, rounded,
+from tests.gpu_common import (ALPHA_TOL, GAMMA_TOL, RES_TOL, borderline_override, nonflat_mask, rel_err, residual_pair, rounded,
                               to_gpu)
 
 pytestmark = pytest.mark.gpu
@@ -100,6 +100,8 @@ def test_projection_parity(name):
     mesh = cv.Mesh(d)
     got = mesh.project(*ic).cpu().numpy()
     ref = O.project(d, *ic)
+    # the 12-point projection rule (reading A17) evaluated in FP32: a few ulps of the
+    # largest coefficient
     assert rel_err(got, ref) < 2e-6
     mesh.close()
 
@@ -133,7 +135,7 @@ def test_full_stage_parity(name):
     both = (got["troubled"] == 1) & (ref["troubled"] == 1) & mask
     if both.any():
         aerr = np.abs(got["alpha"][both] - ref["alpha"][both]).max() / np.abs(ref["alpha"][both]).max()
-        assert aerr < 1e-4, aerr
+        assert aerr < ALPHA_TOL, aerr
     # the smooth Euler density wave (not one of the workloads) sits on the FP32 floor
     # of the flux evaluation: reading A26 -- the error is the same with gamma taken
     # from the GPU (pure arithmetic), bounded here by 1e-4

@@ -28,14 +28,16 @@ def test_positivity_matches_oracle(p, amp):
     mesh.status_check()
     out, th = out.cpu().numpy().astype(np.float64), th.cpu().numpy().astype(np.float64)
     mesh.close()
-    assert np.abs(th - th_ref).max() <= 1e-4
+    # theta: FP32 bisection (40 halvings) on FP32 pressures against the FP64 root (P3);
+    # the 1e-5 bar of the other stages, measured at most 2.7e-7 on a GB300
+    assert np.abs(th - th_ref).max() <= 1e-5
     if amp < 0.1:
         assert np.array_equal(out, u) and np.all(th == 1.0)
     else:
         assert (th_ref < 1).sum() > 10
     assert np.array_equal(out[:, :, 0], u[:, :, 0])
     err = np.abs(out - ref).max(axis=2) / np.abs(u).max(axis=2)
-    assert err.max() <= 1e-4, err.max()
+    assert err.max() <= 1e-5, err.max()  # limited modes, per cell relative: measured at most 2.7e-7
 
 
 def test_in_place_and_inadmissible_mean():
@@ -75,6 +77,9 @@ def test_limited_step_through_a_near_vacuum():
     got = ug.cpu().numpy().astype(np.float64)
     mesh.close()
     norm = O.l1_diff(dp, ref, np.zeros_like(ref))
+    # 40 limited steps through a near vacuum: every stage's theta (a root of a concave
+    # pressure along a segment) is re-decided on FP32 data, so the run follows the oracle
+    # to the sensitivity of those roots rather than to the per-stage 1e-5
     assert O.l1_diff(dp, got, ref) <= 1e-4 * norm
 
 

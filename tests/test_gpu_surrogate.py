@@ -11,7 +11,7 @@ from oracle import oracle as O
 from oracle import surrogate as S
 from paper_2601_16911_gb300 import cvweno as cv
 from paper_2601_16911_gb300 import inputs as I
-from tests.gpu_common import RES_TOL, rounded, to_gpu
+from tests.gpu_common import GAMMA_TOL, RES_TOL, rounded, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -34,8 +34,10 @@ def test_features_match_oracle(p):
     nonflat = nrm > 1e-6 * nrm.max()
     assert nonflat.sum() > 20
     err = np.abs(f - f_ref)[nonflat]
-    assert err.max() <= 1e-4 * (1.0 + np.abs(f_ref[nonflat]).max()), err.max()
-    assert np.abs(g - g_ref)[nonflat].max() <= 2e-4
+    # the stated 1e-5 bar (inputs are ratios of FP32 Taylor data over ||u^e||_e + eps);
+    # measured at most 5.9e-8 on a GB300
+    assert err.max() <= 1e-5 * (1.0 + np.abs(f_ref[nonflat]).max()), err.max()
+    assert np.abs(g - g_ref)[nonflat].max() <= GAMMA_TOL
 
 
 def random_training_set(seed, n):

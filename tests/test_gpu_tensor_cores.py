@@ -18,7 +18,7 @@ import torch
 from oracle import oracle as O
 from paper_2601_16911_gb300 import cvweno as cv
 from paper_2601_16911_gb300 import inputs as I
-from tests.gpu_common import GAMMA_TOL, RES_TOL, nonflat_mask, rel_err, residual_pair, rounded, to_gpu
+from tests.gpu_common import ALPHA_TOL, GAMMA_TOL, RES_TOL, nonflat_mask, rel_err, residual_pair, rounded, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +74,7 @@ def test_full_stage_parity_tensor_cores(name):
     both = (got["troubled"] == 1) & (ref["troubled"] == 1) & mask
     if both.any():
         aerr = np.abs(got["alpha"][both] - ref["alpha"][both]).max() / np.abs(ref["alpha"][both]).max()
-        assert aerr < 1e-4, aerr
+        assert aerr < ALPHA_TOL, aerr
     assert rel_err(got["dudt"], ref["dudt"]) < RES_TOL
 
 
