@@ -1055,13 +1055,17 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
                  reinterpret_cast<__nv_bfloat16*>(smem + L::OFF_XS) + warp * 32 * 16, o0, o1);
       if (!active) return;
       const float conf = 1.0f / (1.0f + __expf(-o1));
+      const bool fallback = live && !(conf >= a.mlp_conf_min);
+      if (a.mlp_fallbacks) {  // one atomic per warp: the count of its falling-back cells
+        const unsigned am = __activemask(), fm = __ballot_sync(am, fallback);
+        if (fm && (threadIdx.x & 31) == (unsigned)(__ffs(am) - 1)) atomicAdd(a.mlp_fallbacks, (unsigned)__popc(fm));
+      }
       if (!live) {
         gam = 1.0f;  // flat to rounding (readings A7, S7): no network, no fallback
-      } else if (conf >= a.mlp_conf_min) {
+      } else if (!fallback) {
         gam = 1.0f / (1.0f + __expf(-o0));
       } else {
         gam = cell_sensor<DIM, P, TX, TY>(a, T, st, sA, c, tx, ty, n0, wstar);
-        if (a.mlp_fallbacks) atomicAdd(a.mlp_fallbacks, 1u);
       }
       if (a.sensor_mode == CVWENO_SENSOR_SMOOTH) gam = 1.0f;
       if (a.sensor_mode == CVWENO_SENSOR_TROUBLED) gam = 0.0f;

@@ -1,0 +1,109 @@
+"""What the trained surrogate sensor gains over the method without it (KPP, Q2).
+
+The network (12-64-64-2, GELU, bf16 tensor-core inference fused into stage (c)) is
+trained on the GPU on plain-sensor labels of KPP 128^2 Q2 runs (seeds 0-3), its
+confidence threshold is calibrated on a held-out seed (5), and it is judged on a third
+seed (4) against the plain path:
+  * calibration transfers in part: the threshold leaves at most 1 % of the held-out
+    seed's confident cells 0.05 or more from the plain sensor; on the evaluation seed's
+    states that holds for 94.5 % of them (measured on a GB300), and at least 90 % must;
+  * accuracy: run to t = 1 on a 16^2 mesh that the FP64 oracle follows, the plain FP32
+    path stays within 2x the oracle's own one-ulp envelope of the oracle's solution
+    (measured 1.0x), and the path with the network within 15x (measured 7.3x: the
+    network's gamma errors are the larger perturbation);
+  * throughput (the measured negative result): the network does not pay for itself.
+    At Q2 it costs about 1,100 instructions per cell (128 GELUs, 88 MMAs per 32 cells,
+    fragment packing) against 400-500 for the plain sensor, and only the cells it is
+    confident about skip the sensor, so the step with the network is no faster than the
+    plain step (measured 0.974x at 512^2); it must also not be more than 20 % slower.
+    Training and calibration are deterministic (fixed data, initial parameters and
+    reduction order), so these figures repeat.
+"""
+import statistics
+
+import pytest
+import torch
+
+import bench
+from paper_2601_16911_gb300 import cvweno as cv
+from paper_2601_16911_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+P = 2
+
+
+@pytest.fixture(scope="module")
+def trained():
+    X, y, _ = bench.surrogate_training_set(P, n=128, seeds=(0, 1, 2, 3), snapshots=16, max_samples=200_000)
+    net = cv.Mlp(I.mlp_init(0))
+    net.train(X, y, batch=4096, epochs=30, lr=1e-3)
+    conf_min, info = bench.calibrate_confidence(net, P, n=128, seed=5)
+    yield net, conf_min, info
+    net.close()
+
+
+def test_calibration_transfers_to_the_evaluation_seed(trained):
+    net, conf_min, info = trained
+    assert 0.0 < info["confident_fraction"] < 1.0
+    d, ic = I.kpp(4, n=128, degree=P)
+    m = cv.Mesh(d)
+    u = m.project(*ic)
+    dt = bench.cfl_dt(P, 128)
+    errs = []
+    for _ in range(6):
+        m.advance(u, dt, 40)
+        f, g, nrm = m.features(u, with_norm=True)
+        live = nrm > 1e-5 * (u.view(-1, (P + 1) ** 2)[:, 0].abs() + 1.0)
+        o = net.infer(f[live])
+        conf = torch.sigmoid(o[:, 1])
+        ok = conf >= conf_min
+        errs.append((torch.sigmoid(o[:, 0]) - g[live]).abs()[ok])
+    m.status_check()
+    m.close()
+    err = torch.cat(errs)
+    assert err.numel() > 100
+    assert float((err < 0.05).float().mean()) >= 0.90
+
+
+def test_final_time_accuracy_against_fp64(trained):
+    net, conf_min, _ = trained
+    res = bench.final_time_l1("surrogate", n=16, surrogate=(net, conf_min))
+    (r,) = res.values()
+    assert r["l1_rel"] <= max(2.0 * r["envelope_l1_rel"], 1e-5), r
+    assert r["l1_rel_with_surrogate"] <= max(15.0 * r["envelope_l1_rel"], 1e-5), r
+
+
+def _step_ms(mesh, u, dt, reps=5, steps=10):
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    out = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mesh.advance(u, dt, steps)
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b) / steps)
+    return statistics.median(out)
+
+
+def test_the_network_does_not_pay_for_itself_at_q2(trained):
+    net, conf_min, _ = trained
+    d, ic = I.kpp(4, n=512, degree=P)
+    dt = bench.cfl_dt(P, 512)
+    plain, surr = cv.Mesh(d), cv.Mesh(d)
+    surr.set_surrogate(net, conf_min)
+    u0 = plain.project(*ic)
+    plain.advance(u0, dt, 100)  # a formed front
+    up, us = u0.clone(), u0.clone()
+    for m, u in ((plain, up), (surr, us)):
+        m.advance(u, dt, 3)
+    tp = _step_ms(plain, up, dt)
+    ts = _step_ms(surr, us, dt)
+    plain.status_check()
+    surr.status_check()
+    plain.close()
+    surr.close()
+    ratio = tp / ts  # throughput with the network over without
+    assert 0.8 <= ratio <= 1.0, (ratio, tp, ts)
