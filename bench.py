@@ -500,6 +500,8 @@ def run_gpu(args):
     meshes, states, dts, graphs, inits, labels = [], [], [], [], [], []
     for label, d, ic, dt in problems(args.workload):
         m = cv.Mesh(d)
+        if args.tensor_cores and label == "DG-Q3":
+            m.set_tensor_cores(True)  # stage (c)'s corner products on tcgen05 (split TF32)
         u = m.project(*ic)
         torch.cuda.synchronize()
         meshes.append(m)
@@ -741,9 +743,20 @@ def run_gpu(args):
         dg_ms = statistics.mean(per_degree[kdg]) / 3.0
         tf_dg = float(meshes[kdg].residual_ex(states[kdg])["troubled"].float().mean().item())
         dg_tf = 2.0 * fma_per_cell(3, tf_dg) * meshes[kdg].ncells / (dg_ms * 1e-3) / 1e12
-        roofline["dg_q3_stage"] = {"kernel": "dg_scalar_stage<2,3,KPP,16,8>", "launch_ms": dg_ms, "achieved": dg_tf,
+        roofline["dg_q3_stage"] = {"kernel": ("dg_scalar_stage_tc<KPP>" if args.tensor_cores else
+                                              "dg_scalar_stage<2,3,KPP,16,8>"), "launch_ms": dg_ms, "achieved": dg_tf,
                                    "frac": dg_tf / alu_peak_tflops,
-                                   "traffic": measured_traffic("dg_scalar_stage_q3_kpp256")}
+                                   "traffic": None if args.tensor_cores else measured_traffic("dg_scalar_stage_q3_kpp256")}
+        # the whole step: the method's flops of every discretisation over the step time
+        step_flops = 0.0
+        for m, u in zip(meshes, states):
+            tf = float(m.residual_ex(u)["troubled"].float().mean().item())
+            step_flops += 3 * 2.0 * fma_per_cell(m.desc["degree"], tf) * m.ncells
+        roofline["whole_step"] = {"flops_per_step": step_flops,
+                                  "achieved": step_flops / (step_ms * 1e-3) / 1e12,
+                                  "frac": step_flops / (step_ms * 1e-3) / 1e12 / alu_peak_tflops,
+                                  "how": "the method's count per cell of every discretisation, three stages, over the "
+                                         "metric's step time (the six discretisations overlap on the GPU)"}
 
     cpu = None
     l1 = None
@@ -754,6 +767,7 @@ def run_gpu(args):
             "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "cells": meshes[0].ncells, "variants": labels,
+                       **({"dg_q3_form": "tensor cores (tcgen05, split TF32)"} if args.tensor_cores else {}),
                        "dofs_per_step_stage": units_per_step // 3, "units_per_step": units_per_step,
                        "l2": "flushed (512 MB write) between timed steps, outside the timed events",
                        "graphs": "one CUDA graph per RK step holding every discretisation as a parallel branch "
@@ -1190,6 +1204,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="kpp: run the DG Q3 discretisation in the tensor-core form of its stage kernel")
     ap.add_argument("--surrogate-degree", type=int, default=2, choices=[1, 2, 3, 4],
                     help="degree of the surrogate workload (configs[4] is Q2)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kpp",
