@@ -382,9 +382,13 @@ def cpu_baseline_sample(workload: str):
     where = f"at {n}x{n} cells" if n else "at full size"
     if workload == "batched":
         where += " (one instance of each degree)"
-    return {"value": vn, "unit": UNIT, "cores": used, "kind": "oracle", "cpu_model": model, "host_cores": cores,
+    # the faster of the two legs is the baseline (a small sample runs faster on one thread)
+    best_v, best_cores = (vn, used) if vn >= v1 else (v1, 1)
+    return {"value": best_v, "unit": UNIT, "cores": best_cores, "kind": "oracle", "cpu_model": model,
+            "host_cores": cores,
             "sample": f"one SSP-RK3 step of every discretisation of the workload {where}: {eln:.1f} s on {used} "
-                      f"threads (OpenMP over cells), {el1:.1f} s on 1 thread",
+                      f"threads (OpenMP over cells), {el1:.1f} s on 1 thread; the faster is the value",
+            "all_cores": {"value": vn, "unit": UNIT, "cores": used},
             "single_thread": {"value": v1, "unit": UNIT, "cores": 1}}
 
 
