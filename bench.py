@@ -714,7 +714,7 @@ def run_gpu(args):
     if args.workload == "euler":
         fma = fma_per_cell_euler(pdom, troubled_frac)
     elif mdom.desc.get("kind", 0) == I.CG:
-        # the method's count of SURVEY-style stages (a)-(e) for Q_p (the same per-cell
+        # the method's count of stages (a)-(e) for Q_p (the same per-cell
         # figure as DG); the kernel's halo recomputation is implementation work
         fma = fma_per_cell(pdom, troubled_frac)
         impl_fma = fma_per_cell_cg_halo(pdom)
@@ -1216,7 +1216,7 @@ def main():
     ap.add_argument("--tensor-cores", action="store_true",
                     help="kpp: run the DG Q3 discretisation in the tensor-core form of its stage kernel")
     ap.add_argument("--surrogate-degree", type=int, default=2, choices=[1, 2, 3, 4],
-                    help="degree of the surrogate workload (configs[4] is Q2)")
+                    help="degree of the surrogate workload (quoted on Q2)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kpp",
                     help="kpp (default): the 2D KPP configuration the metric is quoted on; euler, burgers1d and "
                          "batched measure the other configurations")

@@ -299,7 +299,7 @@ typedef struct {
 } cvweno_batch_plan;
 
 /* Create a batch of count >= 1 meshes from descs[count] (host).  Every desc must be
- * 2D, DG, the same scalar system (BURGERS only in this build), degree 1..4, with
+ * 2D, DG, the same scalar system (BURGERS only), degree 1..4, with
  * square cells (dx == dy, so that one set of reference tabulations serves each
  * degree); other checks are those of cvweno_mesh_create.  Default plan: FUSED, 16x8,
  * dynamic, ctas_per_sm 0, use_graph 1.  Records the current device. */
