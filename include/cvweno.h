@@ -62,7 +62,8 @@ typedef enum {
   CVWENO_ERR_POSITIVITY = 4,   /* Euler: non-positive density or pressure at a node */
   CVWENO_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
   CVWENO_ERR_UNSUPPORTED = 6,  /* valid but not implemented (degree, kind, system) */
-  CVWENO_ERR_NOMEM = 7         /* device or host allocation failed */
+  CVWENO_ERR_NOMEM = 7,        /* device or host allocation failed */
+  CVWENO_ERR_CHECK = 8         /* a bounds check of the checked build (-DCVWENO_CHECK) failed */
 } cvweno_status;
 
 enum { CVWENO_DG = 0, CVWENO_CG = 1 };
@@ -268,6 +269,22 @@ cvweno_status cvweno_kernel_times(cvweno_mesh m, float* ms, int capacity, int* c
  * bit 4, reported as CVWENO_ERR_TIMEOUT at the next status check. */
 cvweno_status cvweno_mesh_set_tensor_cores(cvweno_mesh m, int enable);
 
+/* Bounds-checked build.  The library built with -DCVWENO_CHECK (libcvweno_check.so, same
+ * entry points) checks, before each global load or store of a stage kernel (and each
+ * shared-memory staging store whose offset follows the data's alignment), that the span
+ * lies within its array: the state arrays within the mesh's nstate floats, the per-cell
+ * outputs and work arrays within its cells.  A failed check skips the access and raises
+ * status bit 8, reported as CVWENO_ERR_CHECK at the next status check; nothing traps.
+ * This call narrows the extents those checks use for the mesh's later launches (so that
+ * the checks themselves can be exercised without an out-of-bounds access):
+ *   - state_floats: floats of u_in, u_n and u_out, 0 <= state_floats <= nstate;
+ *   - cells: cells of the per-cell outputs, 0 <= cells <= the mesh's cell count;
+ *   - both negative: back to the mesh's own extents.
+ * Errors: CVWENO_ERR_ARG for a NULL mesh or a value above the mesh's own extent (or one
+ * negative and the other not); CVWENO_ERR_UNSUPPORTED in the normal build, which has no
+ * checks. */
+cvweno_status cvweno_mesh_set_check_extents(cvweno_mesh m, int64_t state_floats, int64_t cells);
+
 /* ---- batches of independent problems ------------------------------------------------
  * Many independent 2D DG meshes of uneven size and degree advanced together: each
  * SSP-RK3 stage of the whole batch is one persistent launch (or one per degree present),
@@ -416,7 +433,8 @@ cvweno_status cvweno_mlp_fallbacks(cvweno_mlp n, uint64_t* count, int reset, voi
  *     streams, or different host threads) race and corrupt each other's stages.
  *   - status_out (host, may be NULL): when given, the call synchronises the stream and
  *     stores the device status bits of this step (1 non-finite, 2 non-positive density
- *     or pressure), returning CVWENO_ERR_NONFINITE / CVWENO_ERR_POSITIVITY accordingly;
+ *     or pressure, 8 a failed bounds check of the checked build), returning
+ *     CVWENO_ERR_NONFINITE / CVWENO_ERR_POSITIVITY / CVWENO_ERR_CHECK accordingly;
  *     when NULL the call only enqueues work. */
 cvweno_status cvweno_step_static(const cvweno_mesh_desc* desc, float* u, double dt, int32_t* status_out,
                                  void* stream);

@@ -213,6 +213,7 @@ StageArgs base_args(const cvweno_mesh_s* m) {
   memset(&a, 0, sizeof(a));
   const cvweno_params& p = m->desc.params;
   a.status = m->d_status;
+  set_check_extents(a, m->chk_state >= 0 ? m->chk_state : m->nstate, m->chk_cell >= 0 ? m->chk_cell : m->ncell);
   a.nx = m->nx;
   a.ny = m->ny;
   a.perx = m->desc.bc[0] == CVWENO_PERIODIC;
@@ -265,6 +266,7 @@ cvweno_status read_status(cvweno_mesh m, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return CVWENO_ERR_CUDA;
   }
+  if (st & kStatCheck) return CVWENO_ERR_CHECK;
   if (st & kStatPositivity) return CVWENO_ERR_POSITIVITY;
   if (st & kStatNonfinite) return CVWENO_ERR_NONFINITE;
   if (st & kStatTimeout) return CVWENO_ERR_TIMEOUT;
@@ -273,6 +275,7 @@ cvweno_status read_status(cvweno_mesh m, cudaStream_t s) {
 
 cvweno_status rk_stage(cvweno_mesh m, const float* in, const float* un, float* out, float ra, float rb, float dt,
                        cudaStream_t s) {
+  NvtxRange range("rk_stage");
   StageArgs a = base_args(m);
   a.u_in = in;
   a.u_n = un;
@@ -408,6 +411,7 @@ const char* cvweno_status_string(cvweno_status s) {
     case CVWENO_ERR_TIMEOUT: return "bounded device wait timed out";
     case CVWENO_ERR_UNSUPPORTED: return "unsupported configuration";
     case CVWENO_ERR_NOMEM: return "out of memory";
+    case CVWENO_ERR_CHECK: return "bounds check failed (checked build)";
   }
   return "unknown status";
 }
@@ -472,6 +476,7 @@ cvweno_status cvweno_mesh_create(const cvweno_mesh_desc* d, cvweno_mesh* out) {
   cvweno_mesh m = (cvweno_mesh)calloc(1, sizeof(cvweno_mesh_s));
   if (!m) return CVWENO_ERR_NOMEM;
   m->desc = *d;
+  m->chk_state = m->chk_cell = -1;
   cudaGetDevice(&m->device);
   m->dim = d->dim;
   m->p = d->degree;
@@ -616,6 +621,7 @@ cvweno_status cvweno_project(cvweno_mesh m, int ic_type, const double* ic_params
 
 cvweno_status cvweno_vertex_data(cvweno_mesh m, const float* u, float* tstar, void* stream) {
   if (!m || !u || !tstar) return CVWENO_ERR_ARG;
+  NvtxRange range("cvweno_vertex_data");
   StageArgs a = base_args(m);
   a.u_in = u;
   a.tstar_out = tstar;
@@ -625,6 +631,7 @@ cvweno_status cvweno_vertex_data(cvweno_mesh m, const float* u, float* tstar, vo
 
 cvweno_status cvweno_sensor(cvweno_mesh m, const float* u, float* gamma, float* nu, void* stream) {
   if (!m || !u) return CVWENO_ERR_ARG;
+  NvtxRange range("cvweno_sensor");
   StageArgs a = base_args(m);
   a.u_in = u;
   a.gamma_out = gamma;
@@ -646,6 +653,7 @@ cvweno_status cvweno_limit(cvweno_mesh m, const float* u, float* out, int all_ce
                            void* stream) {
   if (!m || !u || !out || u == out) return CVWENO_ERR_ARG;
   if (m->kind != CVWENO_DG || m->desc.system == CVWENO_EULER) return CVWENO_ERR_UNSUPPORTED;
+  NvtxRange range("cvweno_limit");
   StageArgs a = base_args(m);
   a.u_in = u;
   a.u_out = out;
@@ -658,6 +666,7 @@ cvweno_status cvweno_limit(cvweno_mesh m, const float* u, float* out, int all_ce
 cvweno_status cvweno_residual_ex(cvweno_mesh m, const float* u, const int32_t* troubled_override, float* dudt,
                                  float* gamma, float* nu, float* alpha, int32_t* troubled, void* stream) {
   if (!m || !u || !dudt || u == dudt) return CVWENO_ERR_ARG;
+  NvtxRange range("cvweno_residual");
   StageArgs a = base_args(m);
   a.u_in = u;
   a.u_n = u;
@@ -698,6 +707,7 @@ cvweno_status cvweno_max_wavespeed(cvweno_mesh m, const float* u, double* lam, v
 
 cvweno_status cvweno_step(cvweno_mesh m, float* u, double dt, double cfl, double* dt_used, void* stream) {
   if (!m || !u) return CVWENO_ERR_ARG;
+  NvtxRange range("cvweno_step");
   cudaStream_t s = S(stream);
   if (!(dt > 0.0)) {
     if (!(cfl > 0.0)) return CVWENO_ERR_ARG;
@@ -714,6 +724,7 @@ cvweno_status cvweno_step(cvweno_mesh m, float* u, double dt, double cfl, double
 
 cvweno_status cvweno_advance(cvweno_mesh m, float* u, double dt, int nsteps, void* stream) {
   if (!m || !u || !(dt > 0.0) || nsteps < 0) return CVWENO_ERR_ARG;
+  NvtxRange range("cvweno_advance");
   if (nsteps > 0 && steps_in_one_launch(m)) return enqueue_steps_one_launch(m, u, (float)dt, nsteps, S(stream));
   for (int i = 0; i < nsteps; ++i) {
     cvweno_status st = enqueue_step(m, u, (float)dt, S(stream));
@@ -769,6 +780,18 @@ cvweno_status cvweno_mesh_set_tensor_cores(cvweno_mesh m, int enable) {
     return CVWENO_ERR_UNSUPPORTED;
   m->tensor_cores = enable;
   return CVWENO_OK;
+}
+
+cvweno_status cvweno_mesh_set_check_extents(cvweno_mesh m, int64_t state_floats, int64_t cells) {
+  if (!m || state_floats > m->nstate || cells > m->ncell || ((state_floats < 0) != (cells < 0)))
+    return CVWENO_ERR_ARG;
+#ifdef CVWENO_CHECK
+  m->chk_state = state_floats;
+  m->chk_cell = cells;
+  return CVWENO_OK;
+#else
+  return CVWENO_ERR_UNSUPPORTED;
+#endif
 }
 
 cvweno_status cvweno_kernel_times(cvweno_mesh m, float* ms, int capacity, int* count) {

@@ -515,6 +515,7 @@ cvweno_status cvweno_batch_get_plan(cvweno_batch b, cvweno_batch_plan* plan) {
 }
 
 cvweno_status cvweno_batch_residual(cvweno_batch b, const float* u, float* dudt, void* stream) {
+  cvw::NvtxRange range("cvweno_batch_residual");
   if (!b || !u || !dudt || u == dudt) return CVWENO_ERR_ARG;
   cudaStream_t s = S(stream);
   cvweno_status st = set_slot_args(b, kSlotResidual, u, dudt, nullptr, s);
@@ -523,6 +524,7 @@ cvweno_status cvweno_batch_residual(cvweno_batch b, const float* u, float* dudt,
 }
 
 cvweno_status cvweno_batch_advance(cvweno_batch b, float* u, const double* dt, int nsteps, void* stream) {
+  cvw::NvtxRange range("cvweno_batch_advance");
   if (!b || !u || !dt || nsteps < 0) return CVWENO_ERR_ARG;
   for (int k = 0; k < b->count; ++k)
     if (!(dt[k] > 0.0)) return CVWENO_ERR_ARG;
@@ -654,8 +656,10 @@ cvweno_status cvweno_batch_status_check(cvweno_batch b, int* first_bad, void* st
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return CVWENO_ERR_CUDA;
   }
+  if (all & kStatCheck) return CVWENO_ERR_CHECK;
   if (all & kStatPositivity) return CVWENO_ERR_POSITIVITY;
   if (all & kStatNonfinite) return CVWENO_ERR_NONFINITE;
+  if (all & kStatTimeout) return CVWENO_ERR_TIMEOUT;
   return CVWENO_OK;
 }
 

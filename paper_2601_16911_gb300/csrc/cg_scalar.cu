@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(cg_block_threads<DIM, P, TX, TY>()) cg_stage_c
         const int ph = (int)(g0 & 3);
         const int64_t c0 = g0 - ph + 4 * k;
         const int64_t left = g0 + NNX - c0;  // wanted floats from the chunk's start on
-        if (left > 0) cp_async16z(snode + iy * NNXP + 4 * k, a.u_in + c0, left >= 4 ? 16 : (int)left * 4);
+        if (left > 0 && CVW_SPAN(a.status, c0, left >= 4 ? 4 : left, a.lim_in))
+          cp_async16z(snode + iy * NNXP + 4 * k, a.u_in + c0, left >= 4 ? 16 : (int)left * 4);
         if (k == 0) sph[iy] = ph;
       }
     } else {
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(cg_block_threads<DIM, P, TX, TY>()) cg_stage_c
         const int ix = f % NNX, iy = f / NNX;
         const int I = wrap_index(I0 + ix, nnx);
         const int J = DIM == 2 ? wrap_index(J0 + iy, nny) : 0;
-        cp_async4(snode + iy * NNXP + ix, a.u_in + (size_t)J * nnx + I, 4);
+        if (CVW_SPAN(a.status, (size_t)J * nnx + I, 1, a.lim_in)) cp_async4(snode + iy * NNXP + ix, a.u_in + (size_t)J * nnx + I, 4);
       }
       for (int iy = threadIdx.x; iy < NNY; iy += NB) sph[iy] = 0;
     }
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(cg_block_threads<DIM, P, TX, TY>()) cg_stage_c
   const int hcx = tx + 1, hcy = DIM == 2 ? ty + 1 : 0;
   const int hc = hcy * HX + hcx;
   const size_t cell = (size_t)gj * nx + gi;
+  if (!CVW_SPAN(a.status, cell, 1, a.lim_cell)) return;  // per-cell outputs and rloc
   float c[ND];
 #pragma unroll
   for (int m = 0; m < ND; ++m) c[m] = sc[m * NH + hc];
@@ -583,19 +585,21 @@ __device__ __forceinline__ float node_residual(const StageArgs& a, int I, int J)
   const int nx = a.nx;
   const int i = I / P, aa = I - i * P;
   const int cx0 = aa == 0 ? (i == 0 ? nx - 1 : i - 1) : i, lx0 = aa == 0 ? P : aa;
+  const int64_t lim = CVW_EXTENT(a, lim_cell) * ND;
+  auto rl = [&](size_t k) { return CVW_SPAN(a.status, k, 1, lim) ? a.rloc[k] : 0.0f; };
   if constexpr (DIM == 1) {
-    float r = a.rloc[(size_t)cx0 * ND + lx0];
-    if (aa == 0) r += a.rloc[(size_t)i * ND];
+    float r = rl((size_t)cx0 * ND + lx0);
+    if (aa == 0) r += rl((size_t)i * ND);
     return r;
   } else {
     const int j = J / P, bb = J - j * P;
     const int cy0 = bb == 0 ? (j == 0 ? a.ny - 1 : j - 1) : j, ly0 = bb == 0 ? P : bb;
     const size_t row0 = (size_t)cy0 * nx, row1 = (size_t)j * nx;
-    float r = a.rloc[(row0 + cx0) * ND + lx0 + N * ly0];
-    if (aa == 0) r += a.rloc[(row0 + i) * ND + N * ly0];
+    float r = rl((row0 + cx0) * ND + lx0 + N * ly0);
+    if (aa == 0) r += rl((row0 + i) * ND + N * ly0);
     if (bb == 0) {
-      r += a.rloc[(row1 + cx0) * ND + lx0];
-      if (aa == 0) r += a.rloc[(row1 + i) * ND];
+      r += rl((row1 + cx0) * ND + lx0);
+      if (aa == 0) r += rl((row1 + i) * ND);
     }
     return r;
   }
@@ -610,6 +614,7 @@ __global__ void cg_node_rhs(const __grid_constant__ StageArgs a, const __grid_co
     const int I = (int)(j % a.nnx), J = (int)(j / a.nnx);
     const float r = node_residual<DIM, P>(a, I, J);
     const float ml = ml1(C, I % P, hdx) * (DIM == 2 ? ml1(C, J % P, hdy) : 1.0f);
+    if (!CVW_SPAN(a.status, j, 1, a.lim_out)) continue;
     a.rnode[j] = r;
     a.du[j] = r / ml;
   }
@@ -653,6 +658,7 @@ __global__ void cg_node_sweep(const __grid_constant__ StageArgs a, const __grid_
   const int64_t nn = (int64_t)a.nnx * (DIM == 2 ? a.nny : 1);
   const float hdx = 1.0f / a.two_dx, hdy = DIM == 2 ? 1.0f / a.two_dy : 1.0f;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
+    if (!CVW_SPAN(a.status, j, 1, a.lim_out)) continue;  // nodal inputs, outputs and work arrays
     const int I = (int)(j % a.nnx), J = (int)(j / a.nnx);
     const float mc = mass_apply<DIM, P>(C, du_in, I, J, a.nnx, DIM == 2 ? a.nny : 1, hdx, hdy);
     const float ml = ml1(C, I % P, hdx) * (DIM == 2 ? ml1(C, J % P, hdy) : 1.0f);
@@ -743,8 +749,9 @@ __global__ void __launch_bounds__(kNdX* node_tile_y<P>(), 2048 / (kNdX * node_ti
     simly[ry] = iml(bb);
   }
   pdl_wait();  // everything below reads or writes what earlier kernels write
-  if (own && rk) uin = a.u_in[j];
-  if (own && with_un) un = a.u_n[j];
+  const bool own_ok = own && CVW_SPAN(a.status, j, 1, a.lim_in) && CVW_SPAN(a.status, j, 1, a.lim_out);
+  if (own_ok && rk) uin = a.u_in[j];
+  if (own_ok && with_un) un = a.u_n[j];
   __syncthreads();
   // ---- r and du0 on the window: every gather of the thread in flight before the first use -----
   constexpr int NW = (RX * RY + NT - 1) / NT;
@@ -757,11 +764,13 @@ __global__ void __launch_bounds__(kNdX* node_tile_y<P>(), 2048 / (kNdX * node_ti
       const int ry = f / RX, rx = f - ry * RX;
       const long long rA = srowA[ry], rB = srowB[ry];
       const int cA = scolA[rx], cB = scolB[rx];
-      float r = a.rloc[rA + cA];
-      if (cB >= 0) r += a.rloc[rA + cB];
+      const int64_t lim = CVW_EXTENT(a, lim_cell) * (N * N);
+      auto rl = [&](long long k) { return CVW_SPAN(a.status, k, 1, lim) ? a.rloc[k] : 0.0f; };
+      float r = rl(rA + cA);
+      if (cB >= 0) r += rl(rA + cB);
       if (rB >= 0) {
-        r += a.rloc[rB + cA];
-        if (cB >= 0) r += a.rloc[rB + cB];
+        r += rl(rB + cA);
+        if (cB >= 0) r += rl(rB + cB);
       }
       rv[k] = r;
     }
@@ -865,7 +874,7 @@ __global__ void __launch_bounds__(kNdX* node_tile_y<P>(), 2048 / (kNdX * node_ti
   }
   __syncthreads();
   pdl_launch_dependents();
-  if (!own) return;
+  if (!own_ok) return;
   // ---- second sweep: y-pass at this thread's node, and the stage output ----------------------
   const int ay = sly[ty + 2 * P], ly0 = ay == 0 ? P : ay, dy = ty + P;
   float mc = 0.0f;

@@ -2,17 +2,49 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/cvweno.h"
 
 namespace cvw {
 
+// An NVTX range over a host scope: every entry point that enqueues kernels names its
+// work (and every RK stage its launch), so that a profiler can select a call's kernels
+// (ncu --nvtx --nvtx-include "cvweno_step/").  Without an attached tool the push and
+// pop cost one predictable branch each.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 constexpr int kMaxP = 4;
 constexpr int kMaxMarks = 24;  // timing events per step: 3 stages x (up to 6 kernels + 1) + 1
 
 // Status bits raised by kernels in the mesh's device status word.
-enum : int { kStatNonfinite = 1, kStatPositivity = 2, kStatTimeout = 4 };
+enum : int { kStatNonfinite = 1, kStatPositivity = 2, kStatTimeout = 4, kStatCheck = 8 };
+
+// Bounds checks of the checked build (compiled with -DCVWENO_CHECK): before each global
+// load or store of a stage kernel, and each shared-memory store whose offset depends on
+// the data's alignment, the span [first, first + count) is checked against the extent of
+// its array; a failed check raises kStatCheck in the status word (CVWENO_ERR_CHECK at the
+// next status check) and the access is skipped.  Nothing traps.  In the normal build
+// CVW_SPAN is the constant true and costs nothing.
+#if defined(CVWENO_CHECK) && defined(__CUDACC__)
+__device__ __forceinline__ bool cvw_span(int* status, long long first, long long count, long long lim) {
+  if (first >= 0 && count >= 0 && first + count <= lim) return true;
+  atomicOr(status, kStatCheck);
+  return false;
+}
+#define CVW_SPAN(status, first, count, lim) \
+  ::cvw::cvw_span((status), (long long)(first), (long long)(count), (long long)(lim))
+#define CVW_EXTENT(a, field) ((a).field)
+#else
+#define CVW_SPAN(status, first, count, lim) true
+#define CVW_EXTENT(a, field) int64_t(0)
+#endif
 
 // Reference-cell tabulations of one (dim, p) pair, FP64 on the host rounded once to
 // FP32, passed to the kernels by value (__grid_constant__), so that every warp reads
@@ -155,7 +187,24 @@ struct StageArgs {
   float* rnode; // [nnode] assembled residual (1D)
   float* du;    // [nnode] du/dt iterate (1D)
   float* du2;   // [nnode] second defect-correction iterate (1D)
+#ifdef CVWENO_CHECK
+  // extents for the bounds checks of the checked build (absent from the normal build, whose
+  // kernels then see the same arguments as without the checks)
+  int64_t lim_in;      // floats readable at u_in and u_n
+  int64_t lim_out;     // floats writable at u_out
+  int64_t lim_cell;    // cells: the extent of the per-cell outputs and of rloc (in cells)
+#endif
 };
+
+// Sets the extents of the checked build's bounds checks (nothing in the normal build).
+inline void set_check_extents(StageArgs& a, int64_t nstate, int64_t ncell) {
+#ifdef CVWENO_CHECK
+  a.lim_in = a.lim_out = nstate;
+  a.lim_cell = ncell;
+#else
+  (void)a, (void)nstate, (void)ncell;
+#endif
+}
 
 // The three SSP-RK3 stages of a step, each a full StageArgs (kModeRK), repeated nsteps
 // times by the one-launch step kernel of a 1D mesh that is a single tile.
@@ -220,6 +269,8 @@ struct cvweno_mesh_s {
   unsigned int* surrogate_fallbacks;
   // cvweno_mesh_set_tensor_cores: 1 = the stage kernel's tcgen05 variant (2D DG scalar Q3)
   int tensor_cores;
+  // cvweno_mesh_set_check_extents: the checked build's extents (-1: nstate and ncell)
+  int64_t chk_state, chk_cell;
   // optional per-launch timing (cvweno_mesh_set_kernel_timing): events recorded
   // between the kernels of one step, read back by cvweno_kernel_times
   int timing;

@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
         if (gj < 0 || gj >= ny) {
           if (a.pery) gj = (gj + ny) % ny; else ok = false;
         }
+        ok = ok && CVW_SPAN(a.status, ((size_t)v * ncell + (size_t)gj * nx + gi) * ND + 4 * q, 4, a.lim_in);
         cp_async16z(stg + 4 * f, ok ? a.u_in + ((size_t)v * ncell + (size_t)gj * nx + gi) * ND + 4 * q : a.u_in,
                     ok ? 16 : 0);
       }
@@ -232,6 +233,7 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
     if (gj < 0 || gj >= ny) {
       if (a.pery) gj = (gj + ny) % ny; else ok = false;
     }
+    ok = ok && CVW_SPAN(a.status, ((size_t)v * ncell + (size_t)gj * nx + gi) * ND + mm, 1, a.lim_in);
     cp_async4(sc + (v * ND + mm) * NH + r * HX + cc,
               ok ? a.u_in + ((size_t)v * ncell + (size_t)gj * nx + gi) * ND + mm : a.u_in, ok ? 4 : 0);
   }
@@ -287,6 +289,10 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
   if (gi >= nx || gj >= ny) return;
   const int hc = (ty + 1) * HX + tx + 1;
   const size_t cell = (size_t)gj * nx + gi;
+  // per-cell outputs, and the cell's span of u_n and u_out in the last variable
+  if (!CVW_SPAN(a.status, cell, 1, a.lim_cell) ||
+      !CVW_SPAN(a.status, ((size_t)(NV - 1) * ncell + cell) * ND, ND, a.lim_in < a.lim_out ? a.lim_in : a.lim_out))
+    return;
   auto C = [&](int v, int m, int h) -> float { return sc[(v * ND + m) * NH + h]; };
 
   // ---- (c) sensor from the density -------------------------------------------------------
@@ -713,6 +719,9 @@ __global__ void __launch_bounds__(PosThreads<P>::value)
   const int64_t ncell = (int64_t)a.nx * a.ny;
   const int64_t cell = (int64_t)blockIdx.x * NTH + threadIdx.x;
   if (cell >= ncell) return;
+  if (!CVW_SPAN(a.status, cell, 1, a.lim_cell) ||
+      !CVW_SPAN(a.status, ((NV - 1) * ncell + cell) * ND, ND, a.lim_in < a.lim_out ? a.lim_in : a.lim_out))
+    return;
   const float g = a.gas_gamma;
 #pragma unroll 1
   for (int k = 0; k < NV * ND; ++k) {

@@ -393,7 +393,7 @@ __device__ __forceinline__ void cp_async16z(float* dst, const float* src, int sr
 // ph[] with the next barrier.
 template <int E, int W, int R, int RS, int NT>
 __device__ __forceinline__ void stage_rows16(float* dst, int* ph, const float* src, int ncol, int nrow, int c0,
-                                             int r0, bool perc, bool perr) {
+                                             int r0, bool perc, bool perr, int* status, int64_t lim) {
   static_assert(RS >= W * E + 3 && RS % 4 == 0, "staging row too short");
   constexpr int NW = NT / 32;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -416,22 +416,31 @@ __device__ __forceinline__ void stage_rows16(float* dst, int* ph, const float* s
     const int p = (int)(gbase & 3);
     if (lane == 0) ph[r] = p;
     d += p;
+    const int64_t dofs = (int64_t)r * RS + p - gbase;  // staging float of global float x: x + dofs
     // body: the whole 16-byte chunks of the in-range run [g0, g1)
     const int64_t g0 = gbase + (int64_t)c_lo * E, g1 = c_hi < c_lo ? g0 : gbase + (int64_t)(c_hi + 1) * E;
     const int64_t b0 = (g0 + 3) & ~(int64_t)3, b1 = g1 & ~(int64_t)3;
     const bool body = b0 < b1;
     if (body)
-      for (int64_t x = b0 + 4 * lane; x < b1; x += 128) cp_async16(d + (x - gbase), src + x);
+      for (int64_t x = b0 + 4 * lane; x < b1; x += 128)
+        if (CVW_SPAN(status, x, 4, lim) && CVW_SPAN(status, x + dofs, 4, R * RS)) cp_async16(d + (x - gbase), src + x);
     // head and tail of the run (or the whole run when it has no whole chunk)
     const int nh = body ? (int)(b0 - g0) : (int)(g1 - g0), nt = body ? (int)(g1 - b1) : 0;
-    if (lane < nh) cp_async4(d + (g0 + lane - gbase), src + g0 + lane, 4);
-    else if (lane < nh + nt) cp_async4(d + (b1 + lane - nh - gbase), src + b1 + lane - nh, 4);
+    if (lane < nh) {
+      if (CVW_SPAN(status, g0 + lane, 1, lim) && CVW_SPAN(status, g0 + lane + dofs, 1, R * RS))
+        cp_async4(d + (g0 + lane - gbase), src + g0 + lane, 4);
+    } else if (lane < nh + nt) {
+      if (CVW_SPAN(status, b1 + lane - nh, 1, lim) && CVW_SPAN(status, b1 + lane - nh + dofs, 1, R * RS))
+        cp_async4(d + (b1 + lane - nh - gbase), src + b1 + lane - nh, 4);
+    }
     for (int j = lane; j < nout; j += 32) {
       const int cj = j / E, e = j - cj * E;
       const int c = cj < c_lo ? cj : cr + (cj - c_lo);
       if (perc) {
         const int gc = ((c0 + c) % ncol + ncol) % ncol;
-        cp_async4(d + c * E + e, src + ((int64_t)gr * ncol + gc) * E + e, 4);
+        if (CVW_SPAN(status, ((int64_t)gr * ncol + gc) * E + e, 1, lim) &&
+            CVW_SPAN(status, (int64_t)r * RS + p + c * E + e, 1, R * RS))
+          cp_async4(d + c * E + e, src + ((int64_t)gr * ncol + gc) * E + e, 4);
       } else {
         d[c * E + e] = 0.0f;
       }
@@ -539,8 +548,9 @@ __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTa
       bool own_y = DIM == 1 || ((vb < TY || J == ny) && J < vyn);
       if (own_x && own_y) {
         size_t vi = (size_t)I + (size_t)a.vx * J;
+        if (CVW_SPAN(a.status, vi * ND, ND, (int64_t)a.vx * vyn * ND))
 #pragma unroll
-        for (int k = 0; k < ND; ++k) a.tstar_out[vi * ND + k] = acc[k] * inv * T.tscale[k];
+          for (int k = 0; k < ND; ++k) a.tstar_out[vi * ND + k] = acc[k] * inv * T.tscale[k];
       }
     }
   }
@@ -918,7 +928,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   constexpr int NQ4 = ND / 4 > 0 ? ND / 4 : 1;  // used only where ND % 4 == 0
   if (rows16) {
     stage_rows16<ND, HX, HY, RSP, NB>(stg, sph, a.u_in, nx, DIM == 2 ? ny : 1, i0 - 1, DIM == 2 ? j0 - 1 : 0, a.perx,
-                                      DIM == 2 && a.pery);
+                                      DIM == 2 && a.pery, a.status, CVW_EXTENT(a, lim_in));
   } else if (in16) {
     for (int f = threadIdx.x; f < NH * NQ4; f += NB) {
       const int h = f / NQ4, q = f - h * NQ4;
@@ -931,6 +941,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
       if (DIM == 2 && (gj < 0 || gj >= ny)) {
         if (a.pery) gj = (gj + ny) % ny; else ok = false;
       }
+      ok = ok && CVW_SPAN(a.status, ((size_t)gj * nx + gi) * ND + 4 * q, 4, a.lim_in);
       cp_async16z(stg + 4 * f, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + 4 * q : a.u_in, ok ? 16 : 0);
     }
   } else {
@@ -947,6 +958,7 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
       if (DIM == 2 && (gj < 0 || gj >= ny)) {
         if (a.pery) gj = (gj + ny) % ny; else ok = false;
       }
+      ok = ok && CVW_SPAN(a.status, ((size_t)gj * nx + gi) * ND + mm, 1, a.lim_in);
       cp_async4(sc + mm * NH + r * HX + cc, ok ? a.u_in + ((size_t)gj * nx + gi) * ND + mm : a.u_in, ok ? 4 : 0);
     }
   }
@@ -980,7 +992,8 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   const bool un16 = ND % 4 == 0 && (reinterpret_cast<uintptr_t>(a.u_n) & 15) == 0;
   {
     const int ogi = i0 + threadIdx.x % TX, ogj = DIM == 2 ? j0 + threadIdx.x / TX : 0;
-    if (pre_un && threadIdx.x < NT && ogi < nx && ogj < ny) {
+    if (pre_un && threadIdx.x < NT && ogi < nx && ogj < ny &&
+        CVW_SPAN(a.status, ((size_t)ogj * nx + ogi) * ND, ND, a.lim_in)) {
       const float* src = a.u_n + ((size_t)ogj * nx + ogi) * ND;
       float* sUn = smem + L::OFF_UN;
       if (un16) {
@@ -1011,7 +1024,10 @@ __device__ __forceinline__ void scalar_tile(const StageArgs& a, const DgTables<D
   if (NB > NT && threadIdx.x >= NT) return;
   const int tx = threadIdx.x % TX, ty = DIM == 2 ? threadIdx.x / TX : 0;
   const int gi = i0 + tx, gj = DIM == 2 ? j0 + ty : 0;
-  const bool active = gi < nx && gj < ny;
+  // (the checked build also checks the cell's span of u_out and its index in the per-cell
+  // outputs)
+  const bool active = gi < nx && gj < ny && CVW_SPAN(a.status, ((size_t)gj * nx + gi) * ND, ND, a.lim_out) &&
+                      CVW_SPAN(a.status, (size_t)gj * nx + gi, 1, a.lim_cell);
   // the surrogate runs warp-wide on the tensor cores: cells outside the mesh take part
   // (on the tile's zero-filled halo data) and leave after it; so do they in the TC form,
   // whose TMEM loads are warp-collective

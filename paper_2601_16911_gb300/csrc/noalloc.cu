@@ -86,6 +86,7 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
                                             void* stream) {
   using namespace cvw;
   if (!d || !u || !(dt > 0.0)) return CVWENO_ERR_ARG;
+  NvtxRange range("cvweno_step_static");
   // the checks of cvweno_mesh_create, in its order and with its codes
   if (d->dim != 1 && d->dim != 2) return CVWENO_ERR_ARG;
   if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return CVWENO_ERR_ARG;
@@ -152,6 +153,7 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
   StageArgs a;
   memset(&a, 0, sizeof(a));
   a.status = slots.status;
+  set_check_extents(a, m.nstate, m.ncell);
   a.nx = m.nx;
   a.ny = m.ny;
   a.perx = d->bc[0] == CVWENO_PERIODIC;
@@ -193,6 +195,7 @@ extern "C" cvweno_status cvweno_step_static(const cvweno_mesh_desc* d, float* u,
         cudaStreamSynchronize(s) != cudaSuccess)
       return CVWENO_ERR_CUDA;
     *status_out = st;
+    if (st & kStatCheck) return CVWENO_ERR_CHECK;
     if (st & kStatPositivity) return CVWENO_ERR_POSITIVITY;
     if (st & kStatNonfinite) return CVWENO_ERR_NONFINITE;
   }

@@ -19,7 +19,7 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_POSITIVITY, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM = range(8)
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_POSITIVITY, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM, ERR_CHECK = range(9)
 DG, CG = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 BURGERS, KPP, LINADV, EULER = 0, 1, 2, 3
@@ -93,6 +93,7 @@ _SIGNATURES = {
     "cvweno_mesh_set_kernel_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cvweno_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _IP]),
     "cvweno_mesh_set_tensor_cores": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "cvweno_mesh_set_check_extents": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64]),
     "cvweno_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_VP)]),
     "cvweno_mlp_destroy": (ctypes.c_int, [_VP]),
     "cvweno_mlp_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -117,18 +118,24 @@ _SIGNATURES = {
 }
 
 
+def checked() -> bool:
+    """True when CVWENO_CHECKED=1 selects the bounds-checked library (libcvweno_check.so)."""
+    return os.environ.get("CVWENO_CHECKED", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(checked())
 
 
 def load(build_if_missing: bool = False):
-    """Load libcvweno.so (optionally building it first).  Raises if unavailable."""
+    """Load libcvweno.so, or libcvweno_check.so under CVWENO_CHECKED=1 (optionally building
+    it first).  Raises if unavailable."""
     global _lib
     with _lock:
         if _lib is None:
             path = library_path()
-            if build_if_missing and _build.is_stale():
-                _build.build()
+            if build_if_missing and _build.is_stale(checked()):
+                _build.build(checked=checked())
             if not os.path.exists(path):
                 raise RuntimeError(f"CUDA library {path} is not built; run paper_2601_16911_gb300.build.build()")
             lib = ctypes.CDLL(path)
@@ -331,6 +338,12 @@ class Mesh:
     def set_tensor_cores(self, enable: bool = True):
         """Stage (c)'s corner products on the tensor cores (split TF32) or as FP32 FMAs."""
         _check(load().cvweno_mesh_set_tensor_cores(self._h, 1 if enable else 0), "cvweno_mesh_set_tensor_cores")
+
+    def set_check_extents(self, state_floats: int = -1, cells: int = -1):
+        """Narrow the extents the checked library's bounds checks use (-1, -1: the mesh's
+        own).  Raises CvwenoError(ERR_UNSUPPORTED) on the normal library."""
+        _check(load().cvweno_mesh_set_check_extents(self._h, int(state_floats), int(cells)),
+               "cvweno_mesh_set_check_extents")
 
     def kernel_times(self):
         """Durations (ms) of the kernels of the most recent step, in launch order."""
@@ -556,6 +569,10 @@ def cvweno_kernel_times(mesh: Mesh):
 
 def cvweno_mesh_set_tensor_cores(mesh: Mesh, enable: bool = True):
     mesh.set_tensor_cores(enable)
+
+
+def cvweno_mesh_set_check_extents(mesh: Mesh, state_floats: int = -1, cells: int = -1):
+    mesh.set_check_extents(state_floats, cells)
 
 
 def cvweno_limit(mesh: Mesh, u, out, all_cells: bool = False, troubled=None, stream=None):
