@@ -659,23 +659,53 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
   }
 
   // ---- M^{-1}, output ---------------------------------------------------------------------------
+  // Per variable, the cell's u_n is read in full before any of its outputs is written: only
+  // this thread reads or writes the cell's span, so u_n may alias u_out, and the reads of a
+  // variable go out together instead of one round trip per mode.  16-byte loads and stores
+  // where the cell is whole 16-byte chunks and both states are 16-byte aligned.
   bool nonfinite = false;
+  const bool rk = (a.mode & kModeRK) != 0, with_un = rk && a.rk_a != 0.0f;
+  const bool v16 = ND % 4 == 0 && ((reinterpret_cast<uintptr_t>(a.u_out) | reinterpret_cast<uintptr_t>(a.u_n)) & 15) == 0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     float* out = a.u_out + ((size_t)v * ncell + cell) * ND;
     const float* un = a.u_n + ((size_t)v * ncell + cell) * ND;
+    float o[ND];
+    if (with_un) {
+      if (v16) {
+#pragma unroll
+        for (int q = 0; q < ND / 4; ++q) {
+          const float4 x = reinterpret_cast<const float4*>(un)[q];
+          o[4 * q] = x.x;
+          o[4 * q + 1] = x.y;
+          o[4 * q + 2] = x.z;
+          o[4 * q + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < ND; ++m) o[m] = un[m];
+      }
+    }
 #pragma unroll
     for (int m = 0; m < ND; ++m) {
       const int mx = m % N, my = m / N;
       const float d = r[v][m] * (0.25f * (2 * mx + 1) * (2 * my + 1));
       nonfinite |= !isfinite(d);
-      if (a.mode & kModeRK) {
+      if (rk) {
         float val = fmaf(a.dt, d, C(v, m, hc));
-        if (a.rk_a != 0.0f) val = fmaf(a.rk_b, val - un[m], un[m]);  // plain load: u_n may alias u_out
-        out[m] = val;
+        if (with_un) val = fmaf(a.rk_b, val - o[m], o[m]);
+        o[m] = val;
       } else {
-        out[m] = d;
+        o[m] = d;
       }
+    }
+    if (v16) {
+#pragma unroll
+      for (int q = 0; q < ND / 4; ++q)
+        reinterpret_cast<float4*>(out)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < ND; ++m) out[m] = o[m];
     }
   }
   if (nonfinite) atomicOr(a.status, kStatNonfinite);
