@@ -84,31 +84,31 @@ __device__ __forceinline__ float euler_pressure(float g, const float* U) {
   return (g - 1.0f) * (U[3] - 0.5f * (U[1] * U[1] + U[2] * U[2]) / U[0]);
 }
 
-// |v| + c at a node of full state U; flags non-positive density or pressure
-__device__ __forceinline__ float euler_speed(float g, const float* U, bool& bad) {
+// |v| + c at a node of full state U, with the velocity along x (dir 0) or y (dir 1) and
+// the sound speed c; flags non-positive density or pressure
+__device__ __forceinline__ float euler_wave(float g, const float* U, int dir, float& vn, float& c, bool& bad) {
   const float rho = U[0], ir = 1.0f / rho;
   const float vx = U[1] * ir, vy = U[2] * ir;
   const float p = euler_pressure(g, U);
   bad |= !(rho > 0.0f) || !(p > 0.0f);
-  return sqrtf(vx * vx + vy * vy) + sqrtf(g * fmaxf(p, 0.0f) * fabsf(ir));
+  c = sqrtf(g * fmaxf(p, 0.0f) * fabsf(ir));
+  vn = dir == 0 ? vx : vy;
+  return sqrtf(vx * vx + vy * vy) + c;
+}
+
+// |v| + c at a node of full state U; flags non-positive density or pressure
+__device__ __forceinline__ float euler_speed(float g, const float* U, bool& bad) {
+  float vn, c;
+  return euler_wave(g, U, 0, vn, c, bad);
 }
 
 // HLL flux minus F(Ubar) . n across a face with normal +x (dir 0) or +y (dir 1), from
-// the left/lower state Ubar + dL to the right/upper state Ubar + dR (reading A14, Davis
-// wave speeds from the full states).  The constant F(Ubar) drops out of every branch:
+// the left/lower state Ubar + dL to the right/upper state Ubar + dR (reading A14), with
+// Davis wave speeds from the two node states' normal velocities vnl, vnr and sound speeds
+// cl, cr (euler_wave).  The constant F(Ubar) drops out of every branch:
 // (S_R F(Ubar) - S_L F(Ubar)) / (S_R - S_L) = F(Ubar).
-__device__ __forceinline__ void hll_dev(float g, const EulerMean& M, const float* dL, const float* dR, int dir, float* F,
-                                        bool& bad) {
-  float UL[NV], UR[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    UL[v] = M.U[v] + dL[v];
-    UR[v] = M.U[v] + dR[v];
-  }
-  const float pL = euler_pressure(g, UL), pR = euler_pressure(g, UR);
-  bad |= !(UL[0] > 0.0f) || !(UR[0] > 0.0f) || !(pL > 0.0f) || !(pR > 0.0f);
-  const float vnl = UL[1 + dir] / UL[0], vnr = UR[1 + dir] / UR[0];
-  const float cl = sqrtf(g * fmaxf(pL, 0.0f) / fabsf(UL[0])), cr = sqrtf(g * fmaxf(pR, 0.0f) / fabsf(UR[0]));
+__device__ __forceinline__ void hll_dev(float g, const EulerMean& M, const float* dL, const float* dR, float vnl,
+                                        float cl, float vnr, float cr, int dir, float* F) {
   const float sl = fminf(vnl - cl, vnr - cr), sr = fmaxf(vnl + cl, vnr + cr);
   float fxl[NV], fyl[NV], fxr[NV], fyr[NV];
   euler_dflux(g, M, dL, fxl, fyl);
@@ -134,21 +134,32 @@ struct EulerLayout {
   static constexpr int N = P + 1, ND = N * N, NT = TX * TY;
   static constexpr int HX = TX + 2, HY = TY + 2, NH = HX * HY;
   static constexpr int NVT = (TX + 1) * (TY + 1);
-  static constexpr int OFF_SC = 0;                    // [NV][ND][NH] tile + halo, mode-major
-  static constexpr int OFF_ST = OFF_SC + NV * ND * NH; // [ND][NVT] density vertex candidates
-  static constexpr int OFF_NQ = OFF_ST + ND * NVT;     // [ND][NT] pointwise density indicator
+  // the tile's faces: x-faces (TX + 1 per tile row), then y-faces (TX per row of TY + 1)
+  static constexpr int NFX = (TX + 1) * TY, NFACE = NFX + TX * (TY + 1);
+  // per face: the projected flux h[v][j] (NV x N), then the largest wave speed of the
+  // left/lower and of the right/upper cell's trace over the face nodes
+  static constexpr int FS = NV * N + 2;
+  static constexpr int OFF_SC = 0;                     // [NV][ND][NH] tile + halo, mode-major
+  static constexpr int OFF_ST = OFF_SC + NV * ND * NH;  // [ND][NVT] density vertex candidates (to the sensor)
+  static constexpr int OFF_NQ = OFF_ST;                 // [ND][NT] pointwise density indicator (after the sensor)
+  static constexpr int OFF_F = OFF_ST + ND * NVT;       // [FS][NFACE] face results, component-major
   // halo staging of two variables, cell-major (cells of whole 16-byte chunks only), over
-  // the vertex and indicator regions, which are written after the load
+  // the vertex and face regions, which are written after the load
   static constexpr int OFF_STG = OFF_ST;
   static constexpr int STG = ND % 4 == 0 ? 2 * NH * ND : 0;
-  static constexpr int FLOATS = OFF_NQ + ND * NT > OFF_STG + STG ? OFF_NQ + ND * NT : OFF_STG + STG;
+  static constexpr int FLOATS = OFF_F + FS * NFACE > OFF_STG + STG ? OFF_F + FS * NFACE : OFF_STG + STG;
   static constexpr size_t BYTES = sizeof(float) * (size_t)FLOATS;
+  static_assert(ND * NT <= ND * NVT, "the indicator must fit over the vertex candidates");
 };
 
-// One thread per cell after the vertex phase.  The work is ordered so that nothing
-// larger than one face's traces or one row of volume nodes is held at a time:
-//   faces (rolled over faces and nodes): own and neighbour traces, HLL, projection onto
-//     the tangential modes, and lambda_e over the face nodes;
+// After the vertex phase, each thread takes its cell's sensor and then a share of the
+// tile's faces, each face once (rolled over faces and nodes): both cells' traces, HLL
+// relative to the left/lower cell's mean, projection onto the tangential modes, and each
+// side's largest wave speed over the face nodes.  Then one thread per cell, ordered so
+// that nothing larger than one row of volume nodes is held at a time:
+//   faces: the four projected fluxes into r (a left/lower face was projected relative to
+//     the neighbour's mean, so the cell adds F(Ubar_nb) - F(Ubar) on the face's mean
+//     mode), lambda_e over the face nodes;
 //   volume pass A (rolled over node rows): flux deviation projected into r, lambda_e
 //     over the volume nodes, and the two sums of stage (d) per variable;
 //   volume pass B, only where the viscosity (1 - gamma_e) nu_e is non-zero: the
@@ -282,22 +293,147 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
       }
     }
   }
-  __syncthreads();
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int gi = i0 + tx, gj = j0 + ty;
-  if (gi >= nx || gj >= ny) return;
   const int hc = (ty + 1) * HX + tx + 1;
   const size_t cell = (size_t)gj * nx + gi;
-  // per-cell outputs, and the cell's span of u_n and u_out in the last variable
-  if (!CVW_SPAN(a.status, cell, 1, a.lim_cell) ||
-      !CVW_SPAN(a.status, ((size_t)(NV - 1) * ncell + cell) * ND, ND, a.lim_in < a.lim_out ? a.lim_in : a.lim_out))
-    return;
+  // (the checked build also checks the cell's index in the per-cell outputs and its span of
+  // u_n and u_out in the last variable)
+  const bool active = gi < nx && gj < ny && CVW_SPAN(a.status, cell, 1, a.lim_cell) &&
+                      CVW_SPAN(a.status, ((size_t)(NV - 1) * ncell + cell) * ND, ND,
+                               a.lim_in < a.lim_out ? a.lim_in : a.lim_out);
   auto C = [&](int v, int m, int h) -> float { return sc[(v * ND + m) * NH + h]; };
+  const bool sensor_only = (a.mode & kModeSensorOnly) != 0;
+  bool bad = false;
+
+  // ---- the tile's faces, each once: traces, HLL, projection, each side's wave speed --------------
+  // In the vertex phase's barrier interval (the face results do not overlap the vertex
+  // candidates), from the block's last thread backwards: the vertex phase's extra round
+  // falls on the first threads, the face phase's on the last.
+  float* sF = smem + L::OFF_F;
+#pragma unroll 1
+  for (int f = NT - 1 - threadIdx.x; f < L::NFACE; f += NT) {
+    int dirn, hl, hr;
+    bool hasl, hasr, needed;
+    if (f < L::NFX) {
+      const int row = f / (TX + 1), col = f - row * (TX + 1);
+      hl = (row + 1) * HX + col;
+      hr = hl + 1;
+      dirn = 0;
+      const int gl = i0 - 1 + col;
+      hasl = a.perx || gl >= 0;
+      hasr = a.perx || gl + 1 < nx;
+      needed = row < act_y && col <= act_x;  // a side of an active cell
+    } else {
+      const int h = f - L::NFX, row = h / TX, col = h - row * TX;
+      hl = row * HX + col + 1;
+      hr = hl + HX;
+      dirn = 1;
+      const int gl = j0 - 1 + row;
+      hasl = a.pery || gl >= 0;
+      hasr = a.pery || gl + 1 < ny;
+      needed = col < act_x && row <= act_y;
+    }
+    if (!needed) continue;
+    // tangential trace coefficients (non-mean modes): the left/lower cell meets the face
+    // with its upper side (+1), the right/upper cell with its lower side ((-1)^i along the
+    // normal); a missing side (transmissive boundary) is the other side's ghost
+    float tl[NV][N], tr[NV][N], UL[NV], UR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        float sl = 0.0f, sr = 0.0f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int m = dirn == 0 ? i + N * j : j + N * i;
+          if (m == 0) continue;
+          const float cl = C(v, m, hl), cr = C(v, m, hr);
+          sl += cl;
+          sr += (i & 1) ? -cr : cr;
+        }
+        tl[v][j] = sl;
+        tr[v][j] = sr;
+      }
+      UL[v] = C(v, 0, hl);
+      UR[v] = C(v, 0, hr);
+    }
+    if (!hasl) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        UL[v] = UR[v];
+#pragma unroll
+        for (int j = 0; j < N; ++j) tl[v][j] = tr[v][j];
+      }
+    }
+    if (!hasr) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        UR[v] = UL[v];
+#pragma unroll
+        for (int j = 0; j < N; ++j) tr[v][j] = tl[v][j];
+      }
+    }
+    const EulerMean ML = euler_mean(g, UL);
+    float dm[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dm[v] = UR[v] - UL[v];
+    float h[NV][N];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int j = 0; j < N; ++j) h[v][j] = 0.0f;
+    float laml = 0.0f, lamr = 0.0f;
+#pragma unroll 1
+    for (int q = 0; q < N; ++q) {
+      float dL[NV], dR[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float sl = 0.0f, sr = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const float bq = T.B[q][j];
+          sl = fmaf(bq, tl[v][j], sl);
+          sr = fmaf(bq, tr[v][j], sr);
+        }
+        dL[v] = sl;
+        dR[v] = sr;
+      }
+      float vnl, cl, vnr, cr;
+      {
+        float U[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = UL[v] + dL[v];
+        laml = fmaxf(laml, euler_wave(g, U, dirn, vnl, cl, bad));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = UR[v] + dR[v];
+        lamr = fmaxf(lamr, euler_wave(g, U, dirn, vnr, cr, bad));
+      }
+      if (sensor_only) continue;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dR[v] = dm[v] + dR[v];
+      float F[NV];
+      hll_dev(g, ML, dL, dR, vnl, cl, vnr, cr, dirn, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float wf = T.w[q] * F[v];
+#pragma unroll
+        for (int j = 0; j < N; ++j) h[v][j] = fmaf(wf, T.B[q][j], h[v][j]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int j = 0; j < N; ++j) sF[(v * N + j) * L::NFACE + f] = h[v][j];
+    sF[NV * N * L::NFACE + f] = laml;
+    sF[(NV * N + 1) * L::NFACE + f] = lamr;
+  }
+  __syncthreads();
 
   // ---- (c) sensor from the density -------------------------------------------------------
-  float gam, n0;
-  {
+  float gam = 1.0f, n0 = 0.0f;
+  if (active) {
     float c[ND];
 #pragma unroll
     for (int m = 0; m < ND; ++m) c[m] = C(0, m, hc);
@@ -356,90 +492,47 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
       gam = 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
   }
 
+  // the indicator sNq, written below, lies over the vertex candidates that the sensor reads
+  __syncthreads();
+  if (!active) {
+    if (bad) atomicOr(a.status, kStatPositivity);
+    return;
+  }
 
-  // ---- faces: traces, HLL, projection; lambda_e over the face nodes ----------------------------
-  bool bad = false;
+  // ---- faces into the residual: right, left, top, bottom; lambda_e over the face nodes ---------
   float Ubar[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) Ubar[v] = C(v, 0, hc);
   const EulerMean M = euler_mean(g, Ubar);
-  const bool sensor_only = (a.mode & kModeSensorOnly) != 0;
   float r[NV][ND];
 #pragma unroll
   for (int v = 0; v < NV; ++v)
 #pragma unroll
     for (int m = 0; m < ND; ++m) r[v][m] = 0.0f;
   float lam = 0.0f;
-  // face f: 0 right (+x), 1 left, 2 top (+y), 3 bottom
 #pragma unroll 1
-  for (int f = 0; f < 4; ++f) {
-    const int dirn = f >> 1;
-    const bool upper = (f & 1) == 0;
-    const int off = dirn == 0 ? (upper ? 1 : -1) : (upper ? HX : -HX);
-    const bool has = dirn == 0 ? (a.perx || (upper ? gi + 1 < nx : gi > 0))
-                               : (a.pery || (upper ? gj + 1 < ny : gj > 0));
-    // tangential trace coefficients of the own and the neighbouring cell along this face
-    // (non-mean modes; the neighbour meets the face with its opposite side)
-    float tro[NV][N], trn[NV][N];
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        float so = 0.0f, sn = 0.0f;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const int m = dirn == 0 ? i + N * j : j + N * i;
-          if (m == 0) continue;
-          const float co = C(v, m, hc), cn = C(v, m, hc + off);
-          so += (!upper && (i & 1)) ? -co : co;
-          sn += (upper && (i & 1)) ? -cn : cn;
-        }
-        tro[v][j] = so;
-        trn[v][j] = sn;
-      }
-    float dmean[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) dmean[v] = C(v, 0, hc + off) - Ubar[v];
+  for (int k = 0; k < 4; ++k) {
+    const int dirn = k >> 1;
+    const bool upper = (k & 1) == 0;  // this cell is the face's left/lower cell
+    const int f = dirn == 0 ? ty * (TX + 1) + tx + (upper ? 1 : 0) : L::NFX + (ty + (upper ? 1 : 0)) * TX + tx;
+    lam = fmaxf(lam, sF[(NV * N + (upper ? 0 : 1)) * L::NFACE + f]);
+    if (sensor_only) continue;
     float h[NV][N];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int j = 0; j < N; ++j) h[v][j] = 0.0f;
-#pragma unroll 1
-    for (int q = 0; q < N; ++q) {
-      float dO[NV], dN[NV];
+      for (int j = 0; j < N; ++j) h[v][j] = sF[(v * N + j) * L::NFACE + f];
+    const bool nb = dirn == 0 ? (a.perx || gi > 0) : (a.pery || gj > 0);
+    if (!upper && nb) {
+      // projected relative to the neighbour's mean: F - F(Ubar) = (F - F(Ubar_nb)) + D with
+      // D = F(Ubar_nb) - F(Ubar) constant along the face, whose projection is 2 D on mode 0
+      float d[NV], dFx[NV], dFy[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        float so = 0.0f, sn = 0.0f;
+      for (int v = 0; v < NV; ++v) d[v] = C(v, 0, hc - (dirn == 0 ? 1 : HX)) - Ubar[v];
+      euler_dflux(g, M, d, dFx, dFy);
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const float bq = T.B[q][j];
-          so = fmaf(bq, tro[v][j], so);
-          sn = fmaf(bq, trn[v][j], sn);
-        }
-        dO[v] = so;
-        dN[v] = has ? dmean[v] + sn : so;  // transmissive side: ghost = own trace
-      }
-      {
-        float U[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) U[v] = Ubar[v] + dO[v];
-        lam = fmaxf(lam, euler_speed(g, U, bad));
-      }
-      if (sensor_only) continue;
-      float F[NV];
-      if (upper)
-        hll_dev(g, M, dO, dN, dirn, F, bad);
-      else
-        hll_dev(g, M, dN, dO, dirn, F, bad);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float wf = T.w[q] * F[v];
-#pragma unroll
-        for (int j = 0; j < N; ++j) h[v][j] = fmaf(wf, T.B[q][j], h[v][j]);
-      }
+      for (int v = 0; v < NV; ++v) h[v][0] = fmaf(2.0f, dirn == 0 ? dFx[v] : dFy[v], h[v][0]);
     }
-    if (sensor_only) continue;
     // r[mx,my] -= 2/dx (hR[my] - (-1)^mx hL[my]) + 2/dy (hT[mx] - (-1)^my hB[mx])
     const float s2d = dirn == 0 ? a.two_dx : a.two_dy;
 #pragma unroll
