@@ -691,8 +691,40 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
   }
 
   // ---- volume pass B: the viscous term, where (1 - gamma_e) nu_e > 0 -----------------------------
+  // With the linear weights (alpha = 1 for every variable) the term is -mu times the
+  // stiffness form of the Legendre basis, which the Gauss rule integrates exactly and which
+  // separates: the x part of mode (mx, my) is (2/dx)^2 (2 / (2 my + 1)) sum_k S[mx][k]
+  // c[k, my], with S[m][k] = int P_m' P_k' = min(m,k) (min(m,k) + 1) where m + k is even
+  // (0 otherwise), and likewise in y.  Alpha-weighted cells take the quadrature.
   const float mu = (1.0f - gam) * nu;
-  if (mu > 0.0f) {
+  bool weighted = false;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) weighted |= afac[v] >= 0.0f;
+  if (mu > 0.0f && !weighted) {
+    const float kx = -mu * a.two_dx * a.two_dx, ky = -mu * a.two_dy * a.two_dy;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int my = 0; my < N; ++my)
+#pragma unroll
+        for (int mx = 0; mx < N; ++mx) {
+          if (mx + my == 0) continue;
+          float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+          for (int k = 1; k < N; ++k) {
+            if ((k + mx) % 2 == 0 && mx > 0) {
+              const int mn = mx < k ? mx : k;
+              sx = fmaf((float)(mn * (mn + 1)), C(v, k + N * my, hc), sx);
+            }
+            if ((k + my) % 2 == 0 && my > 0) {
+              const int mn = my < k ? my : k;
+              sy = fmaf((float)(mn * (mn + 1)), C(v, mx + N * k, hc), sy);
+            }
+          }
+          const float val = fmaf(kx * (2.0f / (2 * my + 1)), sx, r[v][mx + N * my]);
+          r[v][mx + N * my] = fmaf(ky * (2.0f / (2 * mx + 1)), sy, val);
+        }
+  } else if (mu > 0.0f) {
 #pragma unroll 1
     for (int qx = 0; qx < N; ++qx) {
       float tb[NV][N], td[NV][N];
