@@ -27,6 +27,7 @@ constexpr int NV = 4;
 struct EulerMean {
   float U[NV];      // rho, m_x, m_y, E of the cell mean
   float vx, vy, H;  // mean velocity, E + p of the mean state
+  float irho;       // 1 / rho of the mean
 };
 
 __device__ __forceinline__ EulerMean euler_mean(float g, const float* Ub) {
@@ -34,6 +35,7 @@ __device__ __forceinline__ EulerMean euler_mean(float g, const float* Ub) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) M.U[v] = Ub[v];
   const float ir = 1.0f / Ub[0];
+  M.irho = ir;
   M.vx = Ub[1] * ir;
   M.vy = Ub[2] * ir;
   const float p = (g - 1.0f) * (Ub[3] - 0.5f * (Ub[1] * M.vx + Ub[2] * M.vy));
@@ -67,7 +69,7 @@ __device__ __forceinline__ void euler_dflux(float g, const EulerMean& M, const f
   const float p2 = 0.5f * d[2] * M.U[2];
   const float e2 = fmaf(0.5f * d[2], M.U[2], -p2);
   const float x = (x1 - p2) - e2;
-  const float dEmK = x / rb - 0.5f * ((M.U[1] + d[1]) * dvx + (M.U[2] + d[2]) * dvy);
+  const float dEmK = x * M.irho - 0.5f * ((M.U[1] + d[1]) * dvx + (M.U[2] + d[2]) * dvy);
   const float dp = (g - 1.0f) * dEmK;
   const float dH = d[3] + dp;
   dFx[0] = d[1];
@@ -89,7 +91,7 @@ __device__ __forceinline__ float euler_pressure(float g, const float* U) {
 __device__ __forceinline__ float euler_wave(float g, const float* U, int dir, float& vn, float& c, bool& bad) {
   const float rho = U[0], ir = 1.0f / rho;
   const float vx = U[1] * ir, vy = U[2] * ir;
-  const float p = euler_pressure(g, U);
+  const float p = (g - 1.0f) * (U[3] - 0.5f * (U[1] * vx + U[2] * vy));
   bad |= !(rho > 0.0f) || !(p > 0.0f);
   c = sqrtf(g * fmaxf(p, 0.0f) * fabsf(ir));
   vn = dir == 0 ? vx : vy;
