@@ -23,6 +23,17 @@ namespace {
 
 constexpr int NV = 4;
 
+// The reciprocal and square root of the node-wise flux path in PTX's approximate forms
+// (relative error about 2^-22, no range check and no slow path): the wave speeds and the
+// flux deviations need FP32 precision, not correct rounding.  The cell means keep IEEE
+// division.
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Mean state of a cell and the derived quantities the deviation fluxes need.
 struct EulerMean {
   float U[NV];      // rho, m_x, m_y, E of the cell mean
@@ -61,7 +72,7 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 // dE - dK for a uniform pressure) are formed with compensated products.
 __device__ __forceinline__ void euler_dflux(float g, const EulerMean& M, const float* d, float* dFx, float* dFy) {
   const float rb = M.U[0];
-  const float ir = 1.0f / (rb * (rb + d[0]));
+  const float ir = rcp_fast(rb * (rb + d[0]));
   const float dvx = diff_of_products(d[1], rb, M.U[1], d[0]) * ir;
   const float dvy = diff_of_products(d[2], rb, M.U[2], d[0]) * ir;
   // dE rhobar - (dmx mbarx + dmy mbary) / 2, compensated
@@ -89,13 +100,13 @@ __device__ __forceinline__ float euler_pressure(float g, const float* U) {
 // |v| + c at a node of full state U, with the velocity along x (dir 0) or y (dir 1) and
 // the sound speed c; flags non-positive density or pressure
 __device__ __forceinline__ float euler_wave(float g, const float* U, int dir, float& vn, float& c, bool& bad) {
-  const float rho = U[0], ir = 1.0f / rho;
+  const float rho = U[0], ir = rcp_fast(rho);
   const float vx = U[1] * ir, vy = U[2] * ir;
   const float p = (g - 1.0f) * (U[3] - 0.5f * (U[1] * vx + U[2] * vy));
   bad |= !(rho > 0.0f) || !(p > 0.0f);
-  c = sqrtf(g * fmaxf(p, 0.0f) * fabsf(ir));
+  c = sqrt_fast(g * fmaxf(p, 0.0f) * fabsf(ir));
   vn = dir == 0 ? vx : vy;
-  return sqrtf(vx * vx + vy * vy) + c;
+  return sqrt_fast(vx * vx + vy * vy) + c;
 }
 
 // |v| + c at a node of full state U; flags non-positive density or pressure
@@ -124,7 +135,7 @@ __device__ __forceinline__ void hll_dev(float g, const EulerMean& M, const float
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = fr[v];
   } else {
-    const float inv = 1.0f / (sr - sl);
+    const float inv = rcp_fast(sr - sl);
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = (sr * fl[v] - sl * fr[v] + sl * sr * (dR[v] - dL[v])) * inv;
   }
