@@ -23,16 +23,6 @@ namespace {
 
 constexpr int NV = 4;
 
-// The reciprocal and square root of the node-wise flux path in PTX's approximate forms
-// (relative error about 2^-22, no range check and no slow path): the wave speeds and the
-// flux deviations need FP32 precision, not correct rounding.  The cell means keep IEEE
-// division.
-__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ float sqrt_fast(float x) {
-  float y;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // Mean state of a cell and the derived quantities the deviation fluxes need.
 struct EulerMean {
@@ -288,12 +278,12 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
       float b2 = 0.0f;
 #pragma unroll
       for (int k = 1; k < ND; ++k) b2 = fmaf(T.sigma[k] * t[k], t[k], b2);
-      const float wt = 1.0f / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+      const float wt = rcp_fast(ipowf(a.eps + powq(sqrt_fast(b2), a.q), a.r));
       wsum += wt;
 #pragma unroll
       for (int k = 0; k < ND; ++k) acc[k] = fmaf(wt, t[k], acc[k]);
     }
-    const float inv = 1.0f / wsum;
+    const float inv = rcp_fast(wsum);
 #pragma unroll
     for (int k = 0; k < ND; ++k) st[k * NVT + vtx] = acc[k] * inv;
     if (a.tstar_out) {
@@ -461,8 +451,8 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
     float n0sq = 0.0f;
 #pragma unroll
     for (int i = 0; i < NS; ++i) n0sq = fmaf(w0[i], w0[i], n0sq);
-    n0 = sqrtf(n0sq);
-    const float om0 = (1.0f - NC * a.gamma_vertex) / ipowf(a.eps + powq(n0, a.q), a.r);
+    n0 = sqrt_fast(n0sq);
+    const float om0 = (1.0f - NC * a.gamma_vertex) * rcp_fast(ipowf(a.eps + powq(n0, a.q), a.r));
     float S[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
@@ -483,12 +473,12 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
         wl[i] = acc;
         b2 = fmaf(acc, acc, b2);
       }
-      const float om = a.gamma_vertex / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+      const float om = a.gamma_vertex * rcp_fast(ipowf(a.eps + powq(sqrt_fast(b2), a.q), a.r));
       osum += om;
 #pragma unroll
       for (int i = 0; i < NS; ++i) S[i] = fmaf(om, wl[i], S[i]);
     }
-    const float inv = 1.0f / osum;
+    const float inv = rcp_fast(osum);
     float d2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
@@ -502,7 +492,7 @@ __global__ void __launch_bounds__(TX* TY, (euler_min_ctas<P, TX, TY>()))
     else if (n0 <= 1e-30f)
       gam = 1.0f;
     else
-      gam = 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
+      gam = 1.0f - powq(fminf(1.0f, sqrt_fast(d2) * rcp_fast(n0)), a.q);
   }
 
   // the indicator sNq, written below, lies over the vertex candidates that the sensor reads

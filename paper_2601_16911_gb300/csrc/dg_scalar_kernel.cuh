@@ -47,6 +47,16 @@ __device__ __forceinline__ float ipowf(float x, int r) {
 static __device__ __noinline__ float powf_cold(float x, float q) { return powf(x, q); }
 __device__ __forceinline__ float powq(float x, float q) { return q == 1.0f ? x : powf_cold(x, q); }
 
+// Reciprocal and square root in PTX's approximate forms (relative error about 2^-22, no
+// range check and no slow path), for the nonlinear weights and norms of stages (b)-(c)
+// and the node-wise flux paths, which need FP32 precision, not correct rounding.
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---- scalar fluxes, evaluated as deviations from the cell mean -------------------------
 // A law object is built per cell from its mean ubar.  flux_dev returns
 // f(ubar + d) - f(ubar) in forms whose rounding is relative to |d|; llf_dev returns the
@@ -518,12 +528,12 @@ __device__ __forceinline__ void tile_vertex_phase(const StageArgs& a, const DgTa
       float b2 = 0.0f;
 #pragma unroll
       for (int k = 1; k < ND; ++k) b2 = fmaf(T.sigma[k] * t[k], t[k], b2);
-      const float wt = 1.0f / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+      const float wt = rcp_fast(ipowf(a.eps + powq(sqrt_fast(b2), a.q), a.r));
       wsum += wt;
 #pragma unroll
       for (int k = 0; k < ND; ++k) acc[k] = fmaf(wt, t[k], acc[k]);
     }
-    const float inv = 1.0f / wsum;
+    const float inv = rcp_fast(wsum);
     if constexpr (TC) {
       // t*_1 .. t*_NS, zero-padded to TCK, split into TF32 hi and lo: row v of the operand
 #pragma unroll
@@ -575,8 +585,8 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
   float n0sq = 0.0f;
 #pragma unroll
   for (int i = 0; i < NS; ++i) n0sq = fmaf(w0[i], w0[i], n0sq);
-  n0 = sqrtf(n0sq);
-  const float om0 = (1.0f - NC * a.gamma_vertex) / ipowf(a.eps + powq(n0, a.q), a.r);
+  n0 = sqrt_fast(n0sq);
+  const float om0 = (1.0f - NC * a.gamma_vertex) * rcp_fast(ipowf(a.eps + powq(n0, a.q), a.r));
   float S[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
@@ -604,12 +614,12 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
       wl[i] = acc;
       b2 = fmaf(acc, acc, b2);
     }
-    const float om = a.gamma_vertex / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+    const float om = a.gamma_vertex * rcp_fast(ipowf(a.eps + powq(sqrt_fast(b2), a.q), a.r));
     osum += om;
 #pragma unroll
     for (int i = 0; i < NS; ++i) S[i] = fmaf(om, wl[i], S[i]);
   }
-  const float inv = 1.0f / osum;
+  const float inv = rcp_fast(osum);
   float d2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
@@ -622,7 +632,7 @@ __device__ __forceinline__ float cell_sensor(const StageArgs& a, const DgTables<
   if (forced && a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
   if (forced && a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
   if (n0 <= 1e-30f) return 1.0f;
-  return 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
+  return 1.0f - powq(fminf(1.0f, sqrt_fast(d2) * rcp_fast(n0)), a.q);
 }
 
 // Tensor memory and completion barrier of the tensor-core form of the sensor (one
@@ -687,8 +697,8 @@ __device__ __forceinline__ float cell_sensor_tc(const StageArgs& a, const DgTabl
   float n0sq = 0.0f;
 #pragma unroll
   for (int i = 0; i < NS; ++i) n0sq = fmaf(w0[i], w0[i], n0sq);
-  n0 = sqrtf(n0sq);
-  const float om0 = (1.0f - NC * a.gamma_vertex) / ipowf(a.eps + powq(n0, a.q), a.r);
+  n0 = sqrt_fast(n0sq);
+  const float om0 = (1.0f - NC * a.gamma_vertex) * rcp_fast(ipowf(a.eps + powq(n0, a.q), a.r));
   float S[NS];
 #pragma unroll
   for (int i = 0; i < NS; ++i) S[i] = om0 * w0[i];
@@ -705,7 +715,7 @@ __device__ __forceinline__ float cell_sensor_tc(const StageArgs& a, const DgTabl
     float b2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < NS; ++i) b2 = fmaf(wl[i], wl[i], b2);
-    const float om = a.gamma_vertex / ipowf(a.eps + powq(sqrtf(b2), a.q), a.r);
+    const float om = a.gamma_vertex * rcp_fast(ipowf(a.eps + powq(sqrt_fast(b2), a.q), a.r));
     osum += om;
 #pragma unroll
     for (int i = 0; i < NS; ++i) S[i] = fmaf(om, wl[i], S[i]);
@@ -724,7 +734,7 @@ __device__ __forceinline__ float cell_sensor_tc(const StageArgs& a, const DgTabl
     tc::fence_after();
     tc::tmem_dealloc(tmem, kTcCols);
   }
-  const float inv = 1.0f / osum;
+  const float inv = rcp_fast(osum);
   float d2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
@@ -736,7 +746,7 @@ __device__ __forceinline__ float cell_sensor_tc(const StageArgs& a, const DgTabl
   if (forced && a.sensor_mode == CVWENO_SENSOR_SMOOTH) return 1.0f;
   if (forced && a.sensor_mode == CVWENO_SENSOR_TROUBLED) return 0.0f;
   if (n0 <= 1e-30f) return 1.0f;
-  return 1.0f - powq(fminf(1.0f, sqrtf(d2) / n0), a.q);
+  return 1.0f - powq(fminf(1.0f, sqrt_fast(d2) * rcp_fast(n0)), a.q);
 }
 
 // Stage (e), faces: every face of the tile once (the cell-wise loop saw each interior face
