@@ -12,7 +12,7 @@ RES_TOL = 1e-5    # per-stage residual: max |r_gpu - r_oracle| / max |r_oracle|
 # Per-cell sensor gamma_e in [0, 1], absolute: 1e-5 is about 170 FP32 ulps at 1.  The FP32
 # sensor is a few hundred FMAs deep (Taylor data, vertex and cell Jiang-Shu weights,
 # Gram-form semi-norms); over every parity case of both kernel forms, the largest
-# difference measured on a GB300 was 2.8e-7.
+# difference measured on a GB300 was 2.6e-7.
 GAMMA_TOL = 1e-5
 # SC weights alpha_q (eq. alphaq), relative to the cell's largest, on cells that both
 # sides mark troubled: the same bar; the largest measured was 3.4e-7.
