@@ -37,6 +37,7 @@
 namespace cvw {
 
 __device__ __forceinline__ float ipowf(float x, int r) {
+  if (r == 2) return x * x;  // the paper's r
   float y = x;
   for (int i = 1; i < r; ++i) y *= x;
   return y;
