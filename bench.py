@@ -628,53 +628,83 @@ def run_gpu(args):
     value = whole_job_value(units_per_step, args.steps, ws, t_max)
 
     # ---- end to end through the public API: pinned host -> device, step, device -> host ----
-    # One step as a user's time loop would capture it: per discretisation, the copy of its
-    # input from pinned host memory (on one copy stream), its cvweno_advance (kernels one
-    # discretisation after another on the compute stream, as in the timed loop) and the
-    # copy of its result back to pinned host memory (on another copy stream), so that a
-    # discretisation's copies overlap the others' kernels.  The graph is replayed once per
-    # step: every step moves its inputs in and its results out.
-    host_in = [u0.cpu().pin_memory() for u0 in inits]
-    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
-    h2d = sum(h.numel() * h.element_size() for h in host_in)
+    # Each step as a serving loop runs it: per discretisation, the copy of its input from
+    # pinned host memory (one copy stream, small states first so the light branches start
+    # early), its cvweno_advance (one stream per discretisation, heaviest first, as in the
+    # metric's graph) and the copy of its result back to pinned host memory (another copy
+    # stream), captured as one graph.  Two lanes, each with its own meshes, device states
+    # and pinned buffers, replay alternately on two streams, so that one lane's copies
+    # overlap the other lane's kernels.  Every step moves its inputs in and its results out.
+    e2e_lanes = 2
+    h2d = sum(u0.numel() * u0.element_size() for u0 in inits)
     d2h = h2d
-    e2e_steps = max(3, min(args.steps, 20))
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    nm = len(meshes)
-    arrived = [torch.cuda.Event() for _ in range(nm)]
-    done = [torch.cuda.Event() for _ in range(nm)]
-    g_e2e = torch.cuda.CUDAGraph()
-    torch.cuda.synchronize()
-    with torch.cuda.graph(g_e2e):
-        s_run = torch.cuda.current_stream()
-        s_in.wait_stream(s_run)
-        s_out.wait_stream(s_run)
-        with torch.cuda.stream(s_in):  # small states first: the light branches start early
-            for k in range(nm):
-                states[k].copy_(host_in[k], non_blocking=True)
-                arrived[k].record(s_in)
-        for k in heavy_first:
-            bs = branch_streams[k]
-            bs.wait_event(arrived[k])
-            with torch.cuda.stream(bs):
-                cv.cvweno_advance(meshes[k], states[k], dts[k], 1)
-                done[k].record(bs)
-        with torch.cuda.stream(s_out):
-            for k in range(nm):
-                s_out.wait_event(done[k])
-                host_out[k].copy_(states[k], non_blocking=True)
-        s_run.wait_stream(s_in)
-        s_run.wait_stream(s_out)
-        for bs in branch_streams:
-            s_run.wait_stream(bs)
-    g_e2e.replay()
+    e2e_steps = e2e_lanes * max(2, min(args.steps, 20) // e2e_lanes)
+
+    def e2e_lane(lane_meshes, lane_states):
+        host_in = [u0.cpu().pin_memory() for u0 in inits]
+        host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        bstreams = [torch.cuda.Stream() for _ in lane_meshes]
+        nm = len(lane_meshes)
+        arrived = [torch.cuda.Event() for _ in range(nm)]
+        done = [torch.cuda.Event() for _ in range(nm)]
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            s_run = torch.cuda.current_stream()
+            s_in.wait_stream(s_run)
+            s_out.wait_stream(s_run)
+            with torch.cuda.stream(s_in):
+                for k in range(nm):
+                    lane_states[k].copy_(host_in[k], non_blocking=True)
+                    arrived[k].record(s_in)
+            for k in heavy_first:
+                bs = bstreams[k]
+                bs.wait_event(arrived[k])
+                with torch.cuda.stream(bs):
+                    cv.cvweno_advance(lane_meshes[k], lane_states[k], dts[k], 1)
+                    done[k].record(bs)
+            with torch.cuda.stream(s_out):
+                for k in range(nm):
+                    s_out.wait_event(done[k])
+                    host_out[k].copy_(lane_states[k], non_blocking=True)
+            s_run.wait_stream(s_in)
+            s_run.wait_stream(s_out)
+            for bs in bstreams:
+                s_run.wait_stream(bs)
+        return g, (host_in, host_out, s_in, s_out, bstreams, arrived, done)
+
+    lane_meshes = [meshes]
+    for _ in range(1, e2e_lanes):
+        extra = []
+        for m, label in zip(meshes, labels):
+            m2 = cv.Mesh(m.desc)
+            if args.tensor_cores and label == "DG-Q3":
+                m2.set_tensor_cores(True)
+            extra.append(m2)
+        lane_meshes.append(extra)
+    lane_states = [states] + [[u0.clone() for u0 in inits] for _ in range(1, e2e_lanes)]
+    for lm, ls in zip(lane_meshes[1:], lane_states[1:]):
+        for m, u, dt in zip(lm, ls, dts):
+            m.advance(u, dt, 1)  # warm the lane's kernels and tables before capture
+    e2e = [e2e_lane(lm, ls) for lm, ls in zip(lane_meshes, lane_states)]
+    e2e_streams = [torch.cuda.Stream() for _ in range(e2e_lanes)]
+    for lane in range(e2e_lanes):
+        with torch.cuda.stream(e2e_streams[lane]):
+            e2e[lane][0].replay()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        g_e2e.replay()
+    for i in range(e2e_steps):
+        lane = i % e2e_lanes
+        with torch.cuda.stream(e2e_streams[lane]):
+            e2e[lane][0].replay()
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - e0
     e2e_value = units_per_step * e2e_steps / e2e_t
+    for lm in lane_meshes[1:]:
+        for m in lm:
+            m.status_check()
+            m.close()
 
     # ---- 1D: the whole run to the workload's final time in one call (informational) ----
     # A user advances the 1D mesh many steps at a time; cvweno_advance then runs every step
@@ -789,9 +819,11 @@ def run_gpu(args):
                        **({"one_call_run": one_call_run} if one_call_run else {})},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "lanes": e2e_lanes,
                     "steps": e2e_steps, "api": "cvweno_advance via the ctypes binding, pinned host buffers; one step "
                     "captured as a CUDA graph (each discretisation's kernels on its own stream, copies in and out on "
-                    "two copy streams), replayed once per step"},
+                    "two copy streams), replayed once per step; two lanes (own meshes, states and buffers) "
+                    "alternate on two streams, so one lane's copies overlap the other's kernels"},
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     for m in meshes:
@@ -882,20 +914,37 @@ def run_gpu_batched(args, ws, rank, local, dev):
     value = whole_job_value(units_per_step, args.steps, ws, t_max)
     plain_value = units_per_step / (statistics.mean(ms_p) / 1000.0)
 
-    # end to end: pinned host state in, one batched step, state out
-    host_in = u0.cpu().pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    nbytes = host_in.numel() * host_in.element_size()
-    e2e_steps = max(3, min(args.steps, 20))
+    # end to end: pinned host state in, one batched step, state out.  Two lanes (the batch
+    # and a second batch of the same problems with the same plan, each with its own state
+    # and pinned buffers) alternate on two streams, so that one lane's copies overlap the
+    # other's kernels; every step moves its state in and out.
+    nbytes = u0.numel() * u0.element_size()
+    e2e_lanes = 2
+    e2e_steps = e2e_lanes * max(2, min(args.steps, 20) // e2e_lanes)
+    b2 = cv.Batch(descs)
+    b2.set_plan(**{k: v for k, v in plan.items() if k != "ms"})
+    lanes = []
+    for lb, lu in ((b, u), (b2, u0.clone())):
+        lanes.append((lb, lu, u0.cpu().pin_memory(), torch.empty_like(u0, device="cpu").pin_memory(),
+                      torch.cuda.Stream()))
+    for lb, lu, hin, hout, ls in lanes:
+        with torch.cuda.stream(ls):
+            lu.copy_(hin, non_blocking=True)
+            cv.cvweno_batch_advance(lb, lu, dts, 1)  # captures the lane's step graph
+            hout.copy_(lu, non_blocking=True)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        u.copy_(host_in, non_blocking=True)
-        cv.cvweno_batch_advance(b, u, dts, 1)
-        host_out.copy_(u, non_blocking=True)
-        torch.cuda.synchronize()
+    for i in range(e2e_steps):
+        lb, lu, hin, hout, ls = lanes[i % e2e_lanes]
+        with torch.cuda.stream(ls):
+            lu.copy_(hin, non_blocking=True)
+            cv.cvweno_batch_advance(lb, lu, dts, 1)
+            hout.copy_(lu, non_blocking=True)
+    torch.cuda.synchronize()
     e2e_value = units_per_step * e2e_steps / (time.perf_counter() - e0)
     b.status_check()
+    b2.status_check()
+    b2.close()
 
     if rank != 0:
         b.close()
@@ -947,7 +996,10 @@ def run_gpu_batched(args, ws, rank, local, dev):
                        "l1_vs_fp64_final_time": l1},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                    "steps": e2e_steps, "api": "cvweno_batch_advance via the ctypes binding, pinned host buffers"},
+                    "lanes": e2e_lanes, "steps": e2e_steps,
+                    "api": "cvweno_batch_advance via the ctypes binding, pinned host buffers; two lanes (own batch, "
+                           "state and buffers) alternate on two streams, so one lane's copies overlap the other's "
+                           "kernels"},
             "gpu_launches": 3 * nlaunch * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     for m in meshes:
@@ -1161,20 +1213,34 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
                 "peak_source": f"{peak_desc} ({peak_kind} sm_max_mhz)",
                 "flops_per_launch": flops, "flops_model": "the plain method's count (the work the surrogate replaces)",
                 "hbm_algorithmic_gbs": bytes_per_dof_stage() * m_plain.nstate / (launch_ms * 1e-3) / 1e9}
-    # e2e through the public API
-    host_in = u0.cpu().pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    nbytes = host_in.numel() * host_in.element_size()
-    e2e_steps = max(3, min(args.steps, 20))
+    # e2e through the public API: two lanes (the mesh with the network attached and a second
+    # one, each with its own state and pinned buffers) alternate on two streams, so that
+    # one lane's copies overlap the other's kernels; every step moves its state in and out
+    nbytes = u0.numel() * u0.element_size()
+    e2e_lanes = 2
+    e2e_steps = e2e_lanes * max(2, min(args.steps, 20) // e2e_lanes)
+    m_surr2 = cv.Mesh(d)
+    m_surr2.set_surrogate(net, conf_min)
+    lanes = [(lm, lu, u0.cpu().pin_memory(), torch.empty_like(u0, device="cpu").pin_memory(), torch.cuda.Stream())
+             for lm, lu in ((m_surr, u_s), (m_surr2, u0.clone()))]
+    for lm, lu, hin, hout, ls in lanes:
+        with torch.cuda.stream(ls):
+            lu.copy_(hin, non_blocking=True)
+            cv.cvweno_advance(lm, lu, dt, 1)
+            hout.copy_(lu, non_blocking=True)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        u_s.copy_(host_in, non_blocking=True)
-        cv.cvweno_advance(m_surr, u_s, dt, 1)
-        host_out.copy_(u_s, non_blocking=True)
-        torch.cuda.synchronize()
+    for i in range(e2e_steps):
+        lm, lu, hin, hout, ls = lanes[i % e2e_lanes]
+        with torch.cuda.stream(ls):
+            lu.copy_(hin, non_blocking=True)
+            cv.cvweno_advance(lm, lu, dt, 1)
+            hout.copy_(lu, non_blocking=True)
+    torch.cuda.synchronize()
     e2e_value = units * e2e_steps / (time.perf_counter() - e0)
     m_surr.status_check()
+    m_surr2.status_check()
+    m_surr2.close()
     cpu = l1 = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline_sample("surrogate")
@@ -1197,7 +1263,10 @@ def run_gpu_surrogate(args, ws, rank, local, dev):
                        "l2": "flushed (512 MB write) between timed steps, outside the timed events"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                    "steps": e2e_steps, "api": "cvweno_advance with the surrogate attached, pinned host buffers"},
+                    "lanes": e2e_lanes, "steps": e2e_steps,
+                    "api": "cvweno_advance with the surrogate attached, pinned host buffers; two lanes (own mesh, "
+                           "state and buffers) alternate on two streams, so one lane's copies overlap the other's "
+                           "kernels"},
             "gpu_launches": 3 * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     m_plain.close()
