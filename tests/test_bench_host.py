@@ -29,7 +29,7 @@ def test_dominant_kernel_table_matches_the_workload(workload):
         assert bench.launches_per_rk_step(probs[label]) == 3 * per_stage
 
 
-def test_method_count_is_the_survey_formula():
+def test_method_count_is_the_per_stage_formula():
     # stages (a)-(e) of 2D scalar DG Q_p, n = p + 1, troubled fraction tf:
     # (8n^3 + 4n^2) + 4n^2 + (8n^3 + 6n^4) + tf 2n^5 + 14n^3 + 20n^2; Q3 at tf = 0.0701 is
     # 4047.6 FMA per cell

@@ -78,7 +78,7 @@ def test_polynomial_data_unchanged(dim, p):
 
 
 def test_limited_ssprk3_matches_oracle():
-    """1D Burgers (configs[0] data, 128 cells, P2) with the limiter in every stage and the
+    """1D Burgers (the 128-cell P2 step datum) with the limiter in every stage and the
     viscosity off, 40 steps; the relative L1 difference stays within the oracle's own
     sensitivity to a one-ulp change of the start (and within 1e-4)."""
     d0, ic = I.burgers1d_step(0, nx=128, degree=2)
