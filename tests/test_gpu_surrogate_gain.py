@@ -6,16 +6,16 @@ confidence threshold is calibrated on a held-out seed (5), and it is judged on a
 seed (4) against the plain path:
   * calibration transfers in part: the threshold leaves at most 1 % of the held-out
     seed's confident cells 0.05 or more from the plain sensor; on the evaluation seed's
-    states that holds for 94.5 % of them (measured on a GB300), and at least 90 % must;
+    states that holds for 94.1 % of them (measured on a GB300), and at least 90 % must;
   * accuracy: run to t = 1 on a 16^2 mesh that the FP64 oracle follows, the plain FP32
     path stays within 2x the oracle's own one-ulp envelope of the oracle's solution
-    (measured 1.0x), and the path with the network within 15x (measured 7.3x: the
+    (measured 1.0x), and the path with the network within 15x (measured 8.5x: the
     network's gamma errors are the larger perturbation);
   * throughput (the measured negative result): the network does not pay for itself.
     At Q2 it costs about 1,100 instructions per cell (128 GELUs, 88 MMAs per 32 cells,
     fragment packing) against 400-500 for the plain sensor, and only the cells it is
     confident about skip the sensor, so the step with the network is no faster than the
-    plain step (measured 0.974x at 512^2); it must also not be more than 20 % slower.
+    plain step (measured 0.938x at 512^2); it must also not be more than 20 % slower.
     Training and calibration are deterministic (fixed data, initial parameters and
     reduction order), so these figures repeat.
 """
