@@ -35,7 +35,7 @@ def test_features_match_oracle(p):
     assert nonflat.sum() > 20
     err = np.abs(f - f_ref)[nonflat]
     # the stated 1e-5 bar (inputs are ratios of FP32 Taylor data over ||u^e||_e + eps);
-    # measured at most 5.9e-8 on a GB300
+    # measured at most 9.0e-8 on a GB300
     assert err.max() <= 1e-5 * (1.0 + np.abs(f_ref[nonflat]).max()), err.max()
     assert np.abs(g - g_ref)[nonflat].max() <= GAMMA_TOL
 
