@@ -100,21 +100,39 @@ __device__ __forceinline__ void sin_cosm1_small(float d, float& s, float& cm1) {
   cm1 = z * pc;
 }
 
+// sin d and cos d - 1 for the deviations beyond |d| = 1 (a few multiples of pi inside a
+// KPP cell): Cody and Waite's reduction d = k pi/2 + r, |r| <= pi/4, with pi/2 split into
+// an FP32 head and tail and the FMA products exact, then the series above for r and the
+// quadrant k mod 4.  cos d - 1 is taken from cos r - 1 where cos d = cos r (no
+// cancellation); in the other quadrants cos d is at most cos(pi/4) and c - 1 does not
+// cancel.
+__device__ __forceinline__ void sin_cosm1_reduced(float d, float& s, float& cm1) {
+  const float k = rintf(d * 0.636619772f);      // nearest multiple of pi/2
+  float r = fmaf(-k, 1.57079637f, d);            // pi/2 rounded to FP32 ...
+  r = fmaf(-k, -4.37113883e-8f, r);              // ... and the rest of pi/2
+  float sr, cr1;
+  sin_cosm1_small(r, sr, cr1);
+  switch ((int)k & 3) {
+    case 0: s = sr; cm1 = cr1; break;
+    case 1: s = cr1 + 1.0f; cm1 = -sr - 1.0f; break;
+    case 2: s = -sr; cm1 = -cr1 - 2.0f; break;
+    default: s = -(cr1 + 1.0f); cm1 = sr - 1.0f; break;
+  }
+}
+
 template <int DIM>
 struct ScalarLaw<CVWENO_KPP, DIM> {
   float sb, cb;  // sin(ubar), cos(ubar)
   __device__ __forceinline__ ScalarLaw(const StageArgs&, float ub) { sincosf(ub, &sb, &cb); }
   // sin(ub + d) - sin(ub) = sin(ub)(cos d - 1) + cos(ub) sin d, and likewise for cos.
-  // Deviations inside a cell are mostly small: the series above; otherwise sincosf with
-  // cos d - 1 = -sin^2 d / (1 + cos d), which avoids the cancellation where cos d > 0.
+  // Deviations inside a cell are mostly small: the series above; otherwise the reduced
+  // series (sin_cosm1_reduced).
   __device__ __forceinline__ void flux_dev(float d, float& fx, float& fy) const {
     float s, cm1;
     if (fabsf(d) <= 1.0f) {
       sin_cosm1_small(d, s, cm1);
     } else {
-      float c;
-      sincosf(d, &s, &c);
-      cm1 = c > 0.0f ? -(s * s) / (1.0f + c) : c - 1.0f;
+      sin_cosm1_reduced(d, s, cm1);
     }
     fx = fmaf(sb, cm1, cb * s);
     fy = fmaf(cb, cm1, -sb * s);
