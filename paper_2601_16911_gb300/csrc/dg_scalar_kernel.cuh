@@ -123,7 +123,11 @@ __device__ __forceinline__ void sin_cosm1_reduced(float d, float& s, float& cm1)
 template <int DIM>
 struct ScalarLaw<CVWENO_KPP, DIM> {
   float sb, cb;  // sin(ubar), cos(ubar)
-  __device__ __forceinline__ ScalarLaw(const StageArgs&, float ub) { sincosf(ub, &sb, &cb); }
+  __device__ __forceinline__ ScalarLaw(const StageArgs&, float ub) {
+    float cm1;
+    sin_cosm1_reduced(ub, sb, cm1);
+    cb = 1.0f + cm1;
+  }
   // sin(ub + d) - sin(ub) = sin(ub)(cos d - 1) + cos(ub) sin d, and likewise for cos.
   // Deviations inside a cell are mostly small: the series above; otherwise the reduced
   // series (sin_cosm1_reduced).
