@@ -439,6 +439,16 @@ cvweno_status cvweno_mlp_fallbacks(cvweno_mlp n, uint64_t* count, int reset, voi
 cvweno_status cvweno_step_static(const cvweno_mesh_desc* desc, float* u, double dt, int32_t* status_out,
                                  void* stream);
 
+/* The sine and cosine of the KPP flux (Sec. 5.3: f(u) = (sin u, cos u)), as the stage
+ * kernels form them from a deviation d: the Maclaurin series for |d| <= 1, beyond it a
+ * reduction d = k pi/2 + r (Cody and Waite) and the series for r.  For testing the FP32
+ * forms against a reference.
+ *   - d (device, float[n]): the arguments; out (device, float[2n]): sin d in out[0..n),
+ *     cos d - 1 in out[n..2n).  Enqueued on `stream` (NULL: the default stream).
+ * Errors: CVWENO_ERR_ARG for n < 0 or NULL pointers with n > 0; CVWENO_ERR_CUDA if the
+ * launch fails. */
+cvweno_status cvweno_kpp_sincos(const float* d, float* out, int n, void* stream);
+
 /* Static description of a status code.  (Error reporting; no passage of the paper.) */
 const char* cvweno_status_string(cvweno_status s);
 

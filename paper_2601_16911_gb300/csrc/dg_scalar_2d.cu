@@ -59,3 +59,29 @@ cudaError_t launch_tab_image(int dim, int p, const void* t, float* dst, cudaStre
 }
 
 }  // namespace cvw
+
+namespace cvw {
+namespace {
+// sin d and cos d - 1 as the KPP flux forms them: the series up to |d| = 1, the reduced
+// series beyond (ScalarLaw<KPP>::flux_dev).
+__global__ void kpp_sincos_kernel(const float* __restrict__ d, float* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float s, cm1;
+    if (fabsf(d[i]) <= 1.0f)
+      sin_cosm1_small(d[i], s, cm1);
+    else
+      sin_cosm1_reduced(d[i], s, cm1);
+    out[i] = s;
+    out[n + i] = cm1;
+  }
+}
+}  // namespace
+}  // namespace cvw
+
+extern "C" cvweno_status cvweno_kpp_sincos(const float* d, float* out, int n, void* stream) {
+  if (n < 0 || (n > 0 && (!d || !out))) return CVWENO_ERR_ARG;
+  if (n == 0) return CVWENO_OK;
+  const int threads = 256, blocks = (n + threads - 1) / threads < 1024 ? (n + threads - 1) / threads : 1024;
+  cvw::kpp_sincos_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(d, out, n);
+  return cudaGetLastError() == cudaSuccess ? CVWENO_OK : CVWENO_ERR_CUDA;
+}

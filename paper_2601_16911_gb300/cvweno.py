@@ -94,6 +94,7 @@ _SIGNATURES = {
     "cvweno_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _IP]),
     "cvweno_mesh_set_tensor_cores": (ctypes.c_int, [_VP, ctypes.c_int]),
     "cvweno_mesh_set_check_extents": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64]),
+    "cvweno_kpp_sincos": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
     "cvweno_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_VP)]),
     "cvweno_mlp_destroy": (ctypes.c_int, [_VP]),
     "cvweno_mlp_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -573,6 +574,14 @@ def cvweno_mesh_set_tensor_cores(mesh: Mesh, enable: bool = True):
 
 def cvweno_mesh_set_check_extents(mesh: Mesh, state_floats: int = -1, cells: int = -1):
     mesh.set_check_extents(state_floats, cells)
+
+
+def cvweno_kpp_sincos(d, stream=None):
+    """(sin d, cos d - 1) of a float32 CUDA tensor, in the KPP flux's FP32 forms."""
+    d = d.contiguous()
+    out = torch.empty(2 * d.numel(), dtype=torch.float32, device=d.device)
+    _check(load().cvweno_kpp_sincos(_ptr(d), _ptr(out), int(d.numel()), _stream(stream)), "cvweno_kpp_sincos")
+    return out[:d.numel()].view(d.shape), out[d.numel():].view(d.shape)
 
 
 def cvweno_limit(mesh: Mesh, u, out, all_cells: bool = False, troubled=None, stream=None):
