@@ -105,7 +105,9 @@ __device__ __forceinline__ void sin_cosm1_small(float d, float& s, float& cm1) {
 // an FP32 head and tail and the FMA products exact, then the series above for r and the
 // quadrant k mod 4.  cos d - 1 is taken from cos r - 1 where cos d = cos r (no
 // cancellation); in the other quadrants cos d is at most cos(pi/4) and c - 1 does not
-// cancel.
+// cancel.  Accurate to a few FP32 ulps while k pi/2's tail stays below half an ulp of r,
+// i.e. for |d| up to about 1e3 (a KPP state lies within [pi/4, 7 pi/2] by the maximum
+// principle); a non-finite d gives non-finite results, which the stage flags.
 __device__ __forceinline__ void sin_cosm1_reduced(float d, float& s, float& cm1) {
   const float k = rintf(d * 0.636619772f);      // nearest multiple of pi/2
   float r = fmaf(-k, 1.57079637f, d);            // pi/2 rounded to FP32 ...
